@@ -1,0 +1,353 @@
+"""Benchmark of the GCDF hot path: value + df/dq for every (waypoint, point)
+pair of a synthetic scene, fused with the per-waypoint soft-min collision cost.
+
+Workload (one step): the single-trajectory box scene — 9-DOF net (4 x 256 SiLU,
+He-uniform seed 0), 128 waypoints, 16,384 points on the surfaces of 20 seeded
+boxes in a 10 x 10 x 2 m room, soft-min temperature 0.02 — i.e. 2,097,152
+value+gradient pairs reduced to 128 costs and gradients.  Inputs are synthetic
+(`synth`); the paper's benchmark maps are not available.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on the same workload
+
+Multi-GPU: one process per GPU (torchrun); every rank runs its own replica of
+the workload (weak scaling, no collective on the data path); the time is the
+maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def flops_per_pair(shape: synth.NetShape) -> int:
+    """Algorithmic FLOPs of one value + df/dq pair (multiply-add = 2 FLOPs):
+    forward (L-1) H x H layers, the output dot product and the outer-sum add of
+    the split first layer; reverse (L-1) H x H layers and the d_q x H input
+    Jacobian."""
+    H, L, dq = shape.hidden, shape.n_layers, shape.d_q
+    fwd = (L - 1) * 2 * H * H + 2 * H + H
+    rev = (L - 1) * 2 * H * H + 2 * dq * H
+    return fwd + rev
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK, sm_max_mhz=2070.0), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join("/tmp", f"gcdf_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                if self.uuid and parts[1] != self.uuid:
+                    continue
+                try:
+                    sm.append(float(parts[2]))
+                    smax.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[6:10]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload():
+    return synth.box_scene(n_waypoints=128, n_points=16384)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (the only place this script runs oracle/)
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_leg(wl, budget_s: float = 12.0, gpu_result=None):
+    """Time the FP64 oracle on a bounded sample of the workload: whole waypoints
+    (all 16,384 points each, evenly spread over the trajectory) until about
+    `budget_s` seconds have elapsed (at least one waypoint)."""
+    from oracle import metrics, reduce as red
+    s = wl.shape
+    N, M = wl.q.shape[0], wl.p.shape[0]
+    order = [int(i) for i in np.argsort(np.arange(N) * 0.61803398875 % 1.0)]
+    done, costs, grads = [], [], []
+    t0 = time.perf_counter()
+    for i in order:
+        c, g, _ = red.collision_cost(s.n_dof, s.hidden, s.n_layers, wl.weights, wl.q, wl.p,
+                                     wl.reduction, wl.param, waypoints=[i])
+        done.append(i)
+        costs.append(c[0])
+        grads.append(g[0])
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    pairs = len(done) * M
+    try:
+        import threadpoolctl
+        cores = max([d.get("num_threads", 1) for d in threadpoolctl.threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    out = {"value": pairs / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+           "sample": f"{len(done)} of {N} waypoints x {M} points ({pairs} pairs), FP64 NumPy, {dt:.1f} s",
+           "pairs": pairs, "seconds": dt}
+    if gpu_result is not None:
+        c_gpu, g_gpu = gpu_result
+        out["sample_err_cost_max"] = float(metrics.rel_err_scalar(c_gpu[done], np.array(costs)).max())
+        out["sample_err_grad_max"] = float(metrics.rel_err_vector(g_gpu[done], np.array(grads)).max())
+    return out
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on this host's cores, one bounded sample
+    per step; only rank 0 works."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = make_workload()
+    per_step = min(args.ref_budget, 150.0 / (args.steps + args.warmup))
+    rs = [cpu_oracle_leg(wl, budget_s=per_step) for _ in range(args.warmup + args.steps)][args.warmup:]
+    pairs = sum(r["pairs"] for r in rs)
+    secs = sum(r["seconds"] for r in rs)
+    value = pairs / secs
+    line = {
+        "impl": "reference", "metric": "GCDF value+grad pairs/s (soft-min collision cost)", "value": value,
+        "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / len(rs), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name + "_softmin_T0.02", "n_waypoints": 128, "n_points": 16384,
+                   "net": "9-DOF 4x256 SiLU", "sample": "whole waypoints, bounded time per step"},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": rs[-1]["cores"], "kind": "oracle",
+                         "sample": rs[-1]["sample"]},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    import paper_2601_18548_gb300 as g
+    import __graft_entry__
+    __graft_entry__.build()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    wl = make_workload()
+    s = wl.shape
+    P = wl.n_pairs
+    net = g.create_net(s.n_dof, s.hidden, s.n_layers, wl.weights, args.precision)
+    q = torch.from_numpy(wl.q).to(dev)
+    p = torch.from_numpy(wl.p).to(dev)
+    out = (torch.empty(q.shape[0], device=dev), torch.empty(q.shape[0], s.n_dof, device=dev),
+           torch.empty(q.shape[0], device=dev, dtype=torch.int32))
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)  # 256 MiB > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g.collision_cost(net, q, p, wl.reduction, wl.param, out=out)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+
+    k_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k_stop = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    s_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    s_stop = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = "GPU-" + uuid if not uuid.startswith("GPU-") else uuid
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        flush.fill_(float(k))  # evict the previous step's lines from L2 (not timed)
+        g.set_profile_events(net, k_start[k], k_stop[k])
+        s_start[k].record(stream)
+        step()
+        s_stop[k].record(stream)
+    torch.cuda.synchronize()
+    g.set_profile_events(net)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(s_start, s_stop)]
+    kern_ms = [a.elapsed_time(b) for a, b in zip(k_start, k_stop)]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        dist.barrier()
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    q_h = torch.from_numpy(wl.q).pin_memory()
+    p_h = torch.from_numpy(wl.p).pin_memory()
+    c_h = torch.empty(q.shape[0]).pin_memory()
+    g_h = torch.empty(q.shape[0], s.n_dof).pin_memory()
+    a_h = torch.empty(q.shape[0], dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q.copy_(q_h, non_blocking=True)
+        p.copy_(p_h, non_blocking=True)
+        step()
+        c_h.copy_(out[0], non_blocking=True)
+        g_h.copy_(out[1], non_blocking=True)
+        a_h.copy_(out[2], non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_s = sum(e2e_ms) / 1e3
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    peaks, peak_src = load_peaks()
+    fpp = flops_per_pair(s)
+    kern_avg_s = statistics.mean(kern_ms) / 1e3
+    achieved_tflops = fpp * P / kern_avg_s / 1e12
+    if args.precision == "bf16":
+        peak = float(peaks["bf16_tflops"])
+        bound, punit = "tensor", "TFLOP/s"
+        peak_note = f"bf16 dense burst, {peak_src}"
+    else:
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        bound, punit = "alu", "TFLOP/s"
+        peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock (derived)"
+    value = world * P * args.steps / total_s
+    cb = None
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_oracle_leg(wl, budget_s=args.ref_budget,
+                            gpu_result=(out[0].cpu().numpy(), out[1].cpu().numpy()))
+    line = {
+        "metric": "GCDF value+grad pairs/s (soft-min collision cost)",
+        "value": value,
+        "unit": "pairs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16" if args.precision == "bf16" else "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name + "_softmin_T0.02", "n_waypoints": int(q.shape[0]),
+                   "n_points": int(p.shape[0]), "pairs_per_step": P, "net": "9-DOF 4x256 SiLU",
+                   "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": bound, "achieved": achieved_tflops, "peak": peak, "unit": punit,
+                     "frac": achieved_tflops / peak, "traffic": args.traffic, "peak_source": peak_note,
+                     "kernel_ms": 1e3 * kern_avg_s, "flops_per_pair": fpp},
+        "cpu_baseline": cb,
+        "e2e": {"value": world * P * args.steps / e2e_s, "unit": "pairs/s",
+                "h2d_bytes_per_step": int(q_h.numel() * 4 + p_h.numel() * 4),
+                "d2h_bytes_per_step": int(c_h.numel() * 4 + g_h.numel() * 4 + a_h.numel() * 4)},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--ref-budget", type=float, default=12.0, help="seconds of oracle work per sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch from ncu")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

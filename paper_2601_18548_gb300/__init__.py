@@ -1,0 +1,131 @@
+"""GB300-native neural GCDF hot path (arXiv 2601.18548).
+
+Python binding of libgcdf: the functions below have the names of the C entry
+points in include/gcdf.h and only marshal arguments (PyTorch tensors -> device
+pointers, the current CUDA stream).  Every step of the computation runs in the
+library's CUDA kernels; if the library is not built, the first call raises.
+
+    net = create_net(n_dof=9, hidden=256, n_layers=4, weights=w, precision="bf16")
+    f, g = query(net, q, p)                       # per-pair f and df/dq (Eq. 14, 15)
+    c, g, a = collision_cost(net, q, p, "softmin", 0.02)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import GcdfError  # noqa: F401
+
+_PREC = {"fp32": _lib.GCDF_FP32, "bf16": _lib.GCDF_BF16}
+_RED = {"min": _lib.GCDF_RED_MIN, "softmin": _lib.GCDF_RED_SOFTMIN, "hinge": _lib.GCDF_RED_HINGE}
+
+
+def _desc(n_dof, hidden, n_layers, precision):
+    return _lib.NetDesc(int(n_dof), int(hidden), int(n_layers), _PREC[precision])
+
+
+def weight_count(n_dof: int, hidden: int, n_layers: int) -> int:
+    d = _desc(n_dof, hidden, n_layers, "fp32")
+    return int(_lib.load().gcdf_weight_count(ctypes.byref(d)))
+
+
+class Net:
+    """Owner of a gcdf_net handle (device weights on the current device)."""
+
+    def __init__(self, handle, n_dof, hidden, n_layers, precision):
+        self.handle = handle
+        self.n_dof, self.hidden, self.n_layers, self.precision = n_dof, hidden, n_layers, precision
+
+    def __del__(self):
+        destroy_net(self)
+
+
+def create_net(n_dof: int, hidden: int, n_layers: int, weights, precision: str = "fp32") -> Net:
+    """gcdf_create_net: weights is a flat FP32 host array (numpy or CPU tensor)."""
+    lib = _lib.load()
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
+    d = _desc(n_dof, hidden, n_layers, precision)
+    out = ctypes.c_void_p()
+    _lib.check(lib.gcdf_create_net(ctypes.byref(d), w.ctypes.data, w.size, ctypes.byref(out)))
+    return Net(out, n_dof, hidden, n_layers, precision)
+
+
+def destroy_net(net: Net) -> None:
+    """gcdf_destroy_net."""
+    if getattr(net, "handle", None) and net.handle.value:
+        _lib.load().gcdf_destroy_net(net.handle)
+        net.handle = ctypes.c_void_p()
+
+
+def _ptr(t, dtype=torch.float32, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def query(net: Net, q: torch.Tensor, p: torch.Tensor, part_offsets=None, part_idx=None,
+          shift=None, with_grad: bool = True, out=None, stream=None):
+    """gcdf_query: per-pair f (P,) and df/dq (P, n) in stacked order (Eq. 14)."""
+    lib = _lib.load()
+    N, M = q.shape[0], p.shape[0]
+    P = N * M if part_offsets is None else int(part_idx.numel())
+    if out is None:
+        f = torch.empty(P, device=q.device, dtype=torch.float32)
+        g = torch.empty(P, net.n_dof, device=q.device, dtype=torch.float32) if with_grad else None
+    else:
+        f, g = out
+    _lib.check(lib.gcdf_query(net.handle, _ptr(q, name="q"), N, _ptr(p, name="p"), M,
+                              _ptr(part_offsets, torch.int32, "part_offsets"),
+                              _ptr(part_idx, torch.int32, "part_idx"), P,
+                              _ptr(shift, name="shift"), _ptr(f, name="f"),
+                              _ptr(g, name="grad"), _stream(stream)))
+    return f, g
+
+
+def collision_cost(net: Net, q: torch.Tensor, p: torch.Tensor, reduction: str = "softmin",
+                   param: float = 0.02, part_offsets=None, part_idx=None, shift=None,
+                   out=None, stream=None):
+    """gcdf_collision_cost: per-waypoint cost (N,), grad (N, n), argmin (N,)."""
+    lib = _lib.load()
+    N, M = q.shape[0], p.shape[0]
+    P = N * M if part_offsets is None else int(part_idx.numel())
+    if out is None:
+        cost = torch.empty(N, device=q.device, dtype=torch.float32)
+        grad = torch.empty(N, net.n_dof, device=q.device, dtype=torch.float32)
+        amin = torch.empty(N, device=q.device, dtype=torch.int32)
+    else:
+        cost, grad, amin = out
+    _lib.check(lib.gcdf_collision_cost(net.handle, _ptr(q, name="q"), N, _ptr(p, name="p"), M,
+                                       _ptr(part_offsets, torch.int32, "part_offsets"),
+                                       _ptr(part_idx, torch.int32, "part_idx"), P,
+                                       _ptr(shift, name="shift"), _RED[reduction], float(param),
+                                       _ptr(cost, name="cost"), _ptr(grad, name="grad"),
+                                       _ptr(amin, torch.int32, "argmin"), _stream(stream)))
+    return cost, grad, amin
+
+
+def set_profile_events(net: Net, start=None, stop=None) -> None:
+    """gcdf_set_profile_events: torch.cuda.Event pair (enable_timing=True) or None."""
+    a = None if start is None else ctypes.c_void_p(start.cuda_event)
+    b = None if stop is None else ctypes.c_void_p(stop.cuda_event)
+    _lib.check(_lib.load().gcdf_set_profile_events(net.handle, a, b))
+
+
+def last_error() -> str:
+    """gcdf_last_error."""
+    m = _lib.load().gcdf_last_error()
+    return m.decode() if m else ""

@@ -1,0 +1,374 @@
+// C ABI of libgcdf (include/gcdf.h): argument checks, net construction
+// (weight layouts for each path), temporaries and launch sequence.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gcdf_internal.cuh"
+
+using namespace gcdf;
+
+namespace gcdf {
+int fp32_tile_pairs(int H);
+int tc_tile_pairs();
+bool tc_supported(int H, int L, int n_dof);
+}  // namespace gcdf
+
+struct gcdf_net {
+  int n_dof, H, L, precision, d_q, d_in;
+  int device, num_sms;
+  float* w_dev;      // original FP32 weights (layout of gcdf_weight_count)
+  // FP32 path images
+  float* BF;
+  float* BB;
+  float* bias_p;
+  float* wout_p;
+  // BF16 tensor-core path images
+  __nv_bfloat16* slabs;
+  float* tc_bias;
+  float* tc_w1p;
+  float bout;
+  size_t off_W1, off_b1, off_wout;
+  cudaEvent_t prof_start, prof_stop;  // optional events around the fused kernel
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? GCDF_ENOMEM : GCDF_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int shape_check(const gcdf_net_desc* d) {
+  if (!d) return fail(GCDF_EINVAL, "desc is NULL");
+  if (d->n_dof < 3 || d->n_dof > kMaxDof) return fail(GCDF_EINVAL, "n_dof %d outside [3, %d]", d->n_dof, kMaxDof);
+  if (d->n_hidden_layers < 2) return fail(GCDF_EINVAL, "n_hidden_layers %d < 2", d->n_hidden_layers);
+  if (d->precision != GCDF_FP32 && d->precision != GCDF_BF16)
+    return fail(GCDF_EINVAL, "unknown precision %d", d->precision);
+  if (d->hidden <= 0 || d->hidden > 512 || d->hidden % 32)
+    return fail(GCDF_EINVAL, "hidden %d must be a positive multiple of 32, at most 512", d->hidden);
+  return GCDF_OK;
+}
+
+size_t weight_count(int n_dof, int H, int L) {
+  const size_t d_in = 3 + 2 + 2 * (size_t)(n_dof - 2);
+  return H * d_in + H + (size_t)(L - 1) * ((size_t)H * H + H) + H + 1;
+}
+
+template <class T>
+int dev_alloc_copy(T** dst, const T* src, size_t count) {
+  cudaError_t e = cudaMalloc((void**)dst, count * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  e = cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  return GCDF_OK;
+}
+
+// Column permutation of the FP32 path: feature c = fg + G f  ->  column 8 fg + f.
+inline int perm_col(int c, int H) {
+  const int G = H / 8;
+  return (c % G) * 8 + c / G;
+}
+
+int build_fp32_images(gcdf_net* net, const float* w) {
+  const int H = net->H, L = net->L;
+  std::vector<float> BF((size_t)(L - 1) * H * H), BB((size_t)(L - 1) * H * H);
+  std::vector<float> bias((size_t)(L - 1) * H), wout(H);
+  size_t off = (size_t)H * net->d_in + H;
+  for (int l = 0; l < L - 1; ++l) {
+    const float* W = w + off;
+    const float* b = W + (size_t)H * H;
+    for (int o = 0; o < H; ++o) {
+      for (int i = 0; i < H; ++i) {
+        const float v = W[(size_t)o * H + i];
+        BF[(size_t)l * H * H + (size_t)i * H + perm_col(o, H)] = v;  // row = input, col = output
+        BB[(size_t)l * H * H + (size_t)o * H + perm_col(i, H)] = v;  // row = output, col = input
+      }
+      bias[(size_t)l * H + perm_col(o, H)] = b[o];
+    }
+    off += (size_t)H * H + H;
+  }
+  for (int c = 0; c < H; ++c) wout[perm_col(c, H)] = w[off + c];
+  int rc;
+  if ((rc = dev_alloc_copy(&net->BF, BF.data(), BF.size()))) return rc;
+  if ((rc = dev_alloc_copy(&net->BB, BB.data(), BB.size()))) return rc;
+  if ((rc = dev_alloc_copy(&net->bias_p, bias.data(), bias.size()))) return rc;
+  if ((rc = dev_alloc_copy(&net->wout_p, wout.data(), wout.size()))) return rc;
+  return GCDF_OK;
+}
+
+int build_tc_images(gcdf_net* net, const float* w) {
+  const int H = net->H, L = net->L;
+  std::vector<__nv_bfloat16> slabs(tc_slab_elems(H, L, net->d_q));
+  tc_build_slabs(w, H, L, net->d_q, net->d_in, slabs.data());
+  std::vector<float> bias((size_t)(L - 1) * H), w1p((size_t)H * 3);
+  size_t off = (size_t)H * net->d_in + H;
+  for (int l = 0; l < L - 1; ++l) {
+    memcpy(&bias[(size_t)l * H], w + off + (size_t)H * H, H * sizeof(float));
+    off += (size_t)H * H + H;
+  }
+  for (int c = 0; c < H; ++c)
+    for (int d = 0; d < 3; ++d) w1p[(size_t)c * 3 + d] = w[(size_t)c * net->d_in + d];
+  int rc;
+  if ((rc = dev_alloc_copy(&net->slabs, slabs.data(), slabs.size()))) return rc;
+  if ((rc = dev_alloc_copy(&net->tc_bias, bias.data(), bias.size()))) return rc;
+  if ((rc = dev_alloc_copy(&net->tc_w1p, w1p.data(), w1p.size()))) return rc;
+  return GCDF_OK;
+}
+
+void free_net(gcdf_net* n) {
+  if (!n) return;
+  cudaFree(n->w_dev);
+  cudaFree(n->BF);
+  cudaFree(n->BB);
+  cudaFree(n->bias_p);
+  cudaFree(n->wout_p);
+  cudaFree(n->slabs);
+  cudaFree(n->tc_bias);
+  cudaFree(n->tc_w1p);
+  delete n;
+}
+
+// Common validation of the per-call arrays.  Returns GCDF_OK and fills `w`.
+int check_call(gcdf_net* net, const float* q, int N, const float* p, int M, const int* offsets,
+               const int* idx, int n_pairs, const float* shift, WorkDesc& w) {
+  if (!net) return fail(GCDF_EINVAL, "net is NULL");
+  if (N < 0 || M < 0) return fail(GCDF_EINVAL, "negative size (n_waypoints %d, n_points %d)", N, M);
+  if ((offsets == nullptr) != (idx == nullptr))
+    return fail(GCDF_EINVAL, "part_offsets and part_idx must both be NULL or both be set");
+  long long P = offsets ? (long long)n_pairs : (long long)N * M;
+  if (offsets && n_pairs < 0) return fail(GCDF_EINVAL, "n_pairs %d < 0", n_pairs);
+  if (P > 0x7fffffffLL) return fail(GCDF_EINVAL, "pair count %lld exceeds 2^31-1", P);
+  if (N > 0 && (!q || !aligned16(q))) return fail(GCDF_EINVAL, "q is NULL or not 16-byte aligned");
+  if (P > 0 && M > 0 && (!p || !aligned16(p))) return fail(GCDF_EINVAL, "p is NULL or not 16-byte aligned");
+  if (offsets && (!aligned16(offsets) || (n_pairs > 0 && !aligned16(idx))))
+    return fail(GCDF_EINVAL, "part_offsets / part_idx not 16-byte aligned");
+  if (shift && !aligned16(shift)) return fail(GCDF_EINVAL, "shift not 16-byte aligned");
+  if (offsets && n_pairs > 0 && M == 0) return fail(GCDF_EINVAL, "point lists given but n_points == 0");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != net->device) return fail(GCDF_EINVAL, "net belongs to device %d, current device is %d", net->device, dev);
+  memset(&w, 0, sizeof(w));
+  w.q = q;
+  w.p = p;
+  w.offsets = offsets;
+  w.idx = idx;
+  w.N = N;
+  w.M = M;
+  w.n_pairs = (int)P;
+  w.n_dof = net->n_dof;
+  w.n_ang = net->n_dof - 2;
+  w.tile = net->precision == GCDF_FP32 ? fp32_tile_pairs(net->H) : tc_tile_pairs();
+  if (offsets) {
+    w.tiles_per_wp = 0;
+    w.n_tiles = (int)(((long long)n_pairs + w.tile - 1) / w.tile + N);
+  } else {
+    w.tiles_per_wp = (M + w.tile - 1) / w.tile;
+    w.n_tiles = w.tiles_per_wp * N;
+  }
+  return GCDF_OK;
+}
+
+struct Temps {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Temps(cudaStream_t st) : s(st) {}
+  cudaError_t get(void** out, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(out, bytes < 16 ? 16 : bytes, s);
+    if (e == cudaSuccess) ptrs.push_back(*out);
+    return e;
+  }
+  ~Temps() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+};
+
+int run(gcdf_net* net, WorkDesc& w, const float* shift, Temps& tmp, cudaStream_t s) {
+  cudaError_t e;
+  float *A = nullptr, *trig = nullptr;
+  if ((e = tmp.get((void**)&A, (size_t)w.N * net->H * sizeof(float)))) return cuda_fail(e, "cudaMallocAsync");
+  if ((e = tmp.get((void**)&trig, (size_t)w.N * 2 * w.n_ang * sizeof(float)))) return cuda_fail(e, "cudaMallocAsync");
+  w.A = A;
+  w.trig = trig;
+  if (w.offsets) {
+    int* ts = nullptr;
+    if ((e = tmp.get((void**)&ts, (size_t)(w.N + 1) * sizeof(int)))) return cuda_fail(e, "cudaMallocAsync");
+    if ((e = launch_tile_map(w.offsets, w.N, w.tile, ts, s))) return cuda_fail(e, "tile map launch");
+    w.tile_start = ts;
+  }
+  if ((e = launch_prep(w, net->w_dev + net->off_W1, net->w_dev + net->off_b1, net->H, net->d_in, shift, A, trig, s)))
+    return cuda_fail(e, "prep launch");
+  if (net->prof_start && (e = cudaEventRecord(net->prof_start, s))) return cuda_fail(e, "cudaEventRecord");
+  if (net->precision == GCDF_FP32) {
+    Fp32Weights fw;
+    fw.BF = net->BF;
+    fw.BB = net->BB;
+    fw.bias = net->bias_p;
+    fw.W1 = net->w_dev + net->off_W1;
+    fw.wout = net->wout_p;
+    fw.bout = net->bout;
+    fw.H = net->H;
+    fw.L = net->L;
+    fw.d_in = net->d_in;
+    fw.d_q = net->d_q;
+    if ((e = launch_fp32(w, fw, net->num_sms, s))) return cuda_fail(e, "fp32 kernel launch");
+  } else {
+    TcWeights tw;
+    tw.slabs = net->slabs;
+    tw.bias = net->tc_bias;
+    tw.W1p = net->tc_w1p;
+    tw.wout = net->w_dev + net->off_wout;
+    tw.bout = net->bout;
+    tw.H = net->H;
+    tw.L = net->L;
+    tw.d_q = net->d_q;
+    if ((e = launch_tc(w, tw, net->num_sms, s))) return cuda_fail(e, "tensor-core kernel launch");
+  }
+  if (net->prof_stop && (e = cudaEventRecord(net->prof_stop, s))) return cuda_fail(e, "cudaEventRecord");
+  return GCDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gcdf_weight_count(const gcdf_net_desc* desc) {
+  if (shape_check(desc) != GCDF_OK) return 0;
+  return weight_count(desc->n_dof, desc->hidden, desc->n_hidden_layers);
+}
+
+int gcdf_create_net(const gcdf_net_desc* desc, const float* weights_host, size_t n_weights, gcdf_net** out) {
+  int rc = shape_check(desc);
+  if (rc) return rc;
+  if (!weights_host || !out) return fail(GCDF_EINVAL, "weights_host or out is NULL");
+  const size_t need = weight_count(desc->n_dof, desc->hidden, desc->n_hidden_layers);
+  if (n_weights != need) return fail(GCDF_EINVAL, "n_weights %zu, shape needs %zu", n_weights, need);
+  if (desc->precision == GCDF_FP32) {
+    const int H = desc->hidden;
+    if (H != 64 && H != 128 && H != 256 && H != 512)
+      return fail(GCDF_EUNSUPPORTED, "FP32 path: hidden must be 64, 128, 256 or 512 (got %d)", H);
+    if (fp32_smem_bytes(H, desc->n_hidden_layers) > 227 * 1024)
+      return fail(GCDF_EUNSUPPORTED, "FP32 path: %d layers of width %d exceed shared memory", desc->n_hidden_layers, H);
+  } else if (!tc_supported(desc->hidden, desc->n_hidden_layers, desc->n_dof)) {
+    return fail(GCDF_EUNSUPPORTED, "BF16 path: shape (hidden %d, layers %d, n_dof %d) not built",
+                desc->hidden, desc->n_hidden_layers, desc->n_dof);
+  }
+  gcdf_net* n = new (std::nothrow) gcdf_net();
+  if (!n) return fail(GCDF_ENOMEM, "host allocation failed");
+  memset(n, 0, sizeof(*n));
+  n->n_dof = desc->n_dof;
+  n->H = desc->hidden;
+  n->L = desc->n_hidden_layers;
+  n->precision = desc->precision;
+  n->d_q = 2 + 2 * (desc->n_dof - 2);
+  n->d_in = 3 + n->d_q;
+  cudaError_t e = cudaGetDevice(&n->device);
+  if (e != cudaSuccess) { free_net(n); return cuda_fail(e, "cudaGetDevice"); }
+  e = cudaDeviceGetAttribute(&n->num_sms, cudaDevAttrMultiProcessorCount, n->device);
+  if (e != cudaSuccess) { free_net(n); return cuda_fail(e, "cudaDeviceGetAttribute"); }
+  n->off_W1 = 0;
+  n->off_b1 = (size_t)n->H * n->d_in;
+  n->off_wout = need - 1 - n->H;
+  n->bout = weights_host[need - 1];
+  if ((rc = dev_alloc_copy(&n->w_dev, weights_host, need))) { free_net(n); return rc; }
+  rc = (n->precision == GCDF_FP32) ? build_fp32_images(n, weights_host) : build_tc_images(n, weights_host);
+  if (rc) { free_net(n); return rc; }
+  *out = n;
+  g_err[0] = 0;
+  return GCDF_OK;
+}
+
+int gcdf_destroy_net(gcdf_net* net) {
+  if (!net) return GCDF_OK;
+  cudaDeviceSynchronize();
+  free_net(net);
+  return GCDF_OK;
+}
+
+int gcdf_query(gcdf_net* net, const float* q, int N, const float* p, int M, const int* part_offsets,
+               const int* part_idx, int n_pairs, const float* shift, float* f, float* grad,
+               gcdf_stream_t stream) {
+  WorkDesc w;
+  int rc = check_call(net, q, N, p, M, part_offsets, part_idx, n_pairs, shift, w);
+  if (rc) return rc;
+  if (N == 0 || w.n_pairs == 0) return GCDF_OK;
+  if (!f || !aligned16(f)) return fail(GCDF_EINVAL, "f is NULL or not 16-byte aligned");
+  if (grad && !aligned16(grad)) return fail(GCDF_EINVAL, "grad not 16-byte aligned");
+  w.mode = kQuery;
+  w.f_out = f;
+  w.g_out = grad;
+  cudaStream_t s = (cudaStream_t)stream;
+  Temps tmp(s);
+  rc = run(net, w, shift, tmp, s);
+  if (rc) return rc;
+  g_err[0] = 0;
+  return GCDF_OK;
+}
+
+int gcdf_collision_cost(gcdf_net* net, const float* q, int N, const float* p, int M, const int* part_offsets,
+                        const int* part_idx, int n_pairs, const float* shift, int reduction, float param,
+                        float* cost, float* grad, int* argmin, gcdf_stream_t stream) {
+  WorkDesc w;
+  int rc = check_call(net, q, N, p, M, part_offsets, part_idx, n_pairs, shift, w);
+  if (rc) return rc;
+  if (reduction != GCDF_RED_MIN && reduction != GCDF_RED_SOFTMIN && reduction != GCDF_RED_HINGE)
+    return fail(GCDF_EINVAL, "unknown reduction %d", reduction);
+  if (reduction == GCDF_RED_SOFTMIN && !(param > 0.f)) return fail(GCDF_EINVAL, "soft-min temperature must be > 0");
+  if (reduction == GCDF_RED_HINGE && !(param == param)) return fail(GCDF_EINVAL, "hinge margin is NaN");
+  if (N == 0) return GCDF_OK;
+  if (!cost || !aligned16(cost) || !grad || !aligned16(grad))
+    return fail(GCDF_EINVAL, "cost / grad NULL or not 16-byte aligned");
+  if (argmin && !aligned16(argmin)) return fail(GCDF_EINVAL, "argmin not 16-byte aligned");
+  w.mode = reduction;
+  w.param = param;
+  cudaStream_t s = (cudaStream_t)stream;
+  Temps tmp(s);
+  cudaError_t e;
+  Partial* parts = nullptr;
+  if ((e = tmp.get((void**)&parts, (size_t)(w.n_tiles > 0 ? w.n_tiles : 1) * sizeof(Partial))))
+    return cuda_fail(e, "cudaMallocAsync");
+  w.partials = parts;
+  if (w.n_pairs > 0) {
+    rc = run(net, w, shift, tmp, s);
+    if (rc) return rc;
+  } else if (part_offsets) {
+    // every list is empty: the merge sees no tiles
+    int* ts = nullptr;
+    if ((e = tmp.get((void**)&ts, (size_t)(N + 1) * sizeof(int)))) return cuda_fail(e, "cudaMallocAsync");
+    if ((e = launch_tile_map(part_offsets, N, w.tile, ts, s))) return cuda_fail(e, "tile map launch");
+    w.tile_start = ts;
+  } else {
+    w.tiles_per_wp = 0;
+  }
+  if ((e = launch_merge(w, N, cost, grad, argmin, s))) return cuda_fail(e, "merge launch");
+  g_err[0] = 0;
+  return GCDF_OK;
+}
+
+int gcdf_set_profile_events(gcdf_net* net, void* start_event, void* stop_event) {
+  if (!net) return fail(GCDF_EINVAL, "net is NULL");
+  if ((start_event == nullptr) != (stop_event == nullptr))
+    return fail(GCDF_EINVAL, "give both profile events or neither");
+  net->prof_start = (cudaEvent_t)start_event;
+  net->prof_stop = (cudaEvent_t)stop_event;
+  g_err[0] = 0;
+  return GCDF_OK;
+}
+
+const char* gcdf_last_error(void) { return g_err; }
+
+}  // extern "C"

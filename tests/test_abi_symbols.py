@@ -1,0 +1,48 @@
+"""The C ABI library loads on a CPU-only host and exports every entry point
+that include/gcdf.h declares; the Python binding declares the same set."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gcdf.h")).read()
+    return sorted(set(re.findall(r"GCDF_API\s+[\w\s\*]+?\b(gcdf_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("gcdf_create_net", "gcdf_destroy_net", "gcdf_query", "gcdf_collision_cost",
+                 "gcdf_last_error", "gcdf_weight_count"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_18548_gb300 import _lib
+    lib = ctypes.CDLL(_lib.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(_lib.SIGNATURES) == declared_functions()
+
+
+def test_weight_count_and_argument_errors_without_gpu():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2601_18548_gb300 as g
+    import synth
+    for (n, H, L) in ((9, 256, 4), (10, 512, 5), (3, 64, 2)):
+        assert g.weight_count(n, H, L) == synth.NetShape(n, H, L).n_params()
+    lib = g._lib.load()
+    # invalid shapes are rejected before any CUDA call
+    d = g._lib.NetDesc(2, 256, 4, 0)
+    assert lib.gcdf_weight_count(ctypes.byref(d)) == 0
+    out = ctypes.c_void_p()
+    rc = lib.gcdf_create_net(ctypes.byref(d), None, 0, ctypes.byref(out))
+    assert rc == g._lib.GCDF_EINVAL
+    assert "n_dof" in g.last_error()
+    rc = lib.gcdf_query(None, None, 1, None, 1, None, None, 0, None, None, None, None)
+    assert rc == g._lib.GCDF_EINVAL
