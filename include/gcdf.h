@@ -67,7 +67,9 @@ enum gcdf_status {
 
 enum gcdf_precision {
   GCDF_FP32 = 0, /* FP32 weights and activations on CUDA cores */
-  GCDF_BF16 = 1  /* BF16 weights and activations, FP32 accumulation, tcgen05 tensor cores */
+  GCDF_BF16 = 1, /* BF16 weights and activations, FP32 accumulation, tcgen05 tensor cores */
+  GCDF_FP16 = 2  /* FP16 weights and activations, FP32 accumulation, same tensor-core kernel;
+                    three more mantissa bits than BF16 at the same throughput, range +-65504 */
 };
 
 enum gcdf_reduction {
@@ -78,8 +80,8 @@ enum gcdf_reduction {
 
 typedef struct gcdf_net_desc {
   int n_dof;           /* n: x, y, then n - 2 angles; 3 <= n <= 12 */
-  int hidden;          /* H: hidden width; FP32: multiple of 32, <= 512; BF16: 256 */
-  int n_hidden_layers; /* L: number of SiLU layers, >= 2 (FP32: <= 5) */
+  int hidden;          /* H: hidden width; FP32: 64, 128, 256 or 512; BF16/FP16: 256 */
+  int n_hidden_layers; /* L: number of SiLU layers, >= 2 (FP32: <= 5, BF16/FP16: <= 4) */
   int precision;       /* enum gcdf_precision */
 } gcdf_net_desc;
 
@@ -94,7 +96,7 @@ GCDF_API size_t gcdf_weight_count(const gcdf_net_desc *desc);
 
 /*
  * Build a net from HOST weights (layout of gcdf_weight_count).  The weights
- * are copied (and, for GCDF_BF16, rounded to BF16 and re-laid out for the
+ * are copied (and, for GCDF_BF16 / GCDF_FP16, rounded to 16 bits and re-laid out for the
  * tensor cores) onto the current CUDA device; the host buffer may be freed
  * on return.  Synchronous.  *out receives the net; it is bound to the device
  * that was current at creation and must be used with that device current.
@@ -159,6 +161,16 @@ GCDF_API int gcdf_collision_cost(gcdf_net *net, const float *q, int n_waypoints,
                         const int *part_idx, int n_pairs, const float *shift,
                         int reduction, float param, float *cost, float *grad,
                         int *argmin, gcdf_stream_t stream);
+
+/*
+ * Device-side status of a net's kernels since the last call: 0 when every
+ * bounded wait inside the tensor-core kernel completed; bit 0 set when a wait
+ * gave up (the kernel then stopped issuing work, drained its copies, released
+ * its tensor memory and returned; that call's outputs are not valid); bit 1
+ * set when the drain itself timed out.  Synchronises the device, then clears
+ * the word.  Errors: EINVAL (NULL argument), ECUDA.
+ */
+GCDF_API int gcdf_device_status(gcdf_net *net, int *status);
 
 /*
  * Profiling hook: while set, every gcdf_query / gcdf_collision_cost call on

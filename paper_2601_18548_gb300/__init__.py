@@ -19,7 +19,7 @@ import torch
 from . import _lib
 from ._lib import GcdfError  # noqa: F401
 
-_PREC = {"fp32": _lib.GCDF_FP32, "bf16": _lib.GCDF_BF16}
+_PREC = {"fp32": _lib.GCDF_FP32, "bf16": _lib.GCDF_BF16, "fp16": _lib.GCDF_FP16}
 _RED = {"min": _lib.GCDF_RED_MIN, "softmin": _lib.GCDF_RED_SOFTMIN, "hinge": _lib.GCDF_RED_HINGE}
 
 
@@ -116,6 +116,13 @@ def collision_cost(net: Net, q: torch.Tensor, p: torch.Tensor, reduction: str = 
                                        _ptr(cost, name="cost"), _ptr(grad, name="grad"),
                                        _ptr(amin, torch.int32, "argmin"), _stream(stream)))
     return cost, grad, amin
+
+
+def device_status(net: Net) -> int:
+    """gcdf_device_status: 0, or the bits of a bounded device wait that gave up."""
+    v = ctypes.c_int(0)
+    _lib.check(_lib.load().gcdf_device_status(net.handle, ctypes.byref(v)))
+    return v.value
 
 
 def set_profile_events(net: Net, start=None, stop=None) -> None:

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgcdf.so")
 
 GCDF_OK, GCDF_EINVAL, GCDF_ENOMEM, GCDF_ECUDA, GCDF_EUNSUPPORTED = 0, 1, 2, 3, 4
-GCDF_FP32, GCDF_BF16 = 0, 1
+GCDF_FP32, GCDF_BF16, GCDF_FP16 = 0, 1, 2
 GCDF_RED_MIN, GCDF_RED_SOFTMIN, GCDF_RED_HINGE = 0, 1, 2
 
 # Every function the header declares, with (restype, argtypes).
@@ -31,6 +31,7 @@ SIGNATURES = {
     "gcdf_destroy_net": (_i, [_vp]),
     "gcdf_query": (_i, [_vp, _vp, _i, _vp, _i, _vp, _vp, _i, _vp, _vp, _vp, _vp]),
     "gcdf_collision_cost": (_i, [_vp, _vp, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _f, _vp, _vp, _vp, _vp]),
+    "gcdf_device_status": (_i, [_vp, ctypes.POINTER(_i)]),
     "gcdf_set_profile_events": (_i, [_vp, _vp, _vp]),
     "gcdf_last_error": (ctypes.c_char_p, []),
 }

@@ -324,15 +324,15 @@ fp32_fused_kernel(const WorkDesc w, const Fp32Weights fw) {
 template <int H, int KC>
 cudaError_t launch_h(const WorkDesc& w, const Fp32Weights& fw, int num_sms, cudaStream_t s) {
   const SmemLayout lay = smem_layout<H, KC>(fw.L);
-  // Opt in once per device to the largest dynamic shared memory any L needs.
-  static int attr_done[64] = {0};
+  // Opt in (per device) to the dynamic shared memory this L needs.
+  static int attr_bytes[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+  if (dev < 0 || dev >= 64 || attr_bytes[dev] < (int)lay.total) {
     cudaError_t e = cudaFuncSetAttribute(fp32_fused_kernel<H, KC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) attr_done[dev] = 1;
+    if (dev >= 0 && dev < 64) attr_bytes[dev] = (int)lay.total;
   }
   const int grid = w.n_tiles < num_sms ? w.n_tiles : num_sms;
   if (grid <= 0) return cudaSuccess;

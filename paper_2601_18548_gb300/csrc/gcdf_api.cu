@@ -16,6 +16,10 @@ int tc_tile_pairs();
 bool tc_supported(int H, int L, int n_dof);
 }  // namespace gcdf
 
+namespace {
+constexpr int kSmemLimit = 227 * 1024 - 1024;  // per-block opt-in limit less static shared memory
+}
+
 struct gcdf_net {
   int n_dof, H, L, precision, d_q, d_in;
   int device, num_sms;
@@ -26,9 +30,11 @@ struct gcdf_net {
   float* bias_p;
   float* wout_p;
   // BF16 tensor-core path images
-  __nv_bfloat16* slabs;
+  uint16_t* slabs;   // 16-bit operand image (BF16 or FP16 bits)
   float* tc_bias;
   float* tc_w1p;
+  TcWeights tcw;     // tensor maps and pointers for the tensor-core kernel
+  int* err_word;     // device status word written by bounded waits
   float bout;
   size_t off_W1, off_b1, off_wout;
   cudaEvent_t prof_start, prof_stop;  // optional events around the fused kernel
@@ -57,7 +63,7 @@ int shape_check(const gcdf_net_desc* d) {
   if (!d) return fail(GCDF_EINVAL, "desc is NULL");
   if (d->n_dof < 3 || d->n_dof > kMaxDof) return fail(GCDF_EINVAL, "n_dof %d outside [3, %d]", d->n_dof, kMaxDof);
   if (d->n_hidden_layers < 2) return fail(GCDF_EINVAL, "n_hidden_layers %d < 2", d->n_hidden_layers);
-  if (d->precision != GCDF_FP32 && d->precision != GCDF_BF16)
+  if (d->precision != GCDF_FP32 && d->precision != GCDF_BF16 && d->precision != GCDF_FP16)
     return fail(GCDF_EINVAL, "unknown precision %d", d->precision);
   if (d->hidden <= 0 || d->hidden > 512 || d->hidden % 32)
     return fail(GCDF_EINVAL, "hidden %d must be a positive multiple of 32, at most 512", d->hidden);
@@ -113,8 +119,9 @@ int build_fp32_images(gcdf_net* net, const float* w) {
 
 int build_tc_images(gcdf_net* net, const float* w) {
   const int H = net->H, L = net->L;
-  std::vector<__nv_bfloat16> slabs(tc_slab_elems(H, L, net->d_q));
-  tc_build_slabs(w, H, L, net->d_q, net->d_in, slabs.data());
+  const bool f16 = net->precision == GCDF_FP16;
+  std::vector<uint16_t> image(tc_image_elems(H, L, net->d_q));
+  tc_build_image(w, H, L, net->d_q, net->d_in, f16, image.data());
   std::vector<float> bias((size_t)(L - 1) * H), w1p((size_t)H * 3);
   size_t off = (size_t)H * net->d_in + H;
   for (int l = 0; l < L - 1; ++l) {
@@ -124,9 +131,21 @@ int build_tc_images(gcdf_net* net, const float* w) {
   for (int c = 0; c < H; ++c)
     for (int d = 0; d < 3; ++d) w1p[(size_t)c * 3 + d] = w[(size_t)c * net->d_in + d];
   int rc;
-  if ((rc = dev_alloc_copy(&net->slabs, slabs.data(), slabs.size()))) return rc;
+  if ((rc = dev_alloc_copy(&net->slabs, image.data(), image.size()))) return rc;
   if ((rc = dev_alloc_copy(&net->tc_bias, bias.data(), bias.size()))) return rc;
   if ((rc = dev_alloc_copy(&net->tc_w1p, w1p.data(), w1p.size()))) return rc;
+  TcWeights& tw = net->tcw;
+  if (tc_encode_maps(net->slabs, H, L, net->d_q, f16, tw)) return fail(GCDF_ECUDA, "cuTensorMapEncodeTiled failed");
+  tw.f16 = f16 ? 1 : 0;
+  tw.bias = net->tc_bias;
+  tw.W1p = net->tc_w1p;
+  tw.wout = net->w_dev + net->off_wout;
+  tw.bout = net->bout;
+  tw.H = H;
+  tw.L = L;
+  tw.d_q = net->d_q;
+  tw.nj = tc_nj(net->d_q);
+  tw.err = net->err_word;
   return GCDF_OK;
 }
 
@@ -140,6 +159,7 @@ void free_net(gcdf_net* n) {
   cudaFree(n->slabs);
   cudaFree(n->tc_bias);
   cudaFree(n->tc_w1p);
+  cudaFree(n->err_word);
   delete n;
 }
 
@@ -227,16 +247,7 @@ int run(gcdf_net* net, WorkDesc& w, const float* shift, Temps& tmp, cudaStream_t
     fw.d_q = net->d_q;
     if ((e = launch_fp32(w, fw, net->num_sms, s))) return cuda_fail(e, "fp32 kernel launch");
   } else {
-    TcWeights tw;
-    tw.slabs = net->slabs;
-    tw.bias = net->tc_bias;
-    tw.W1p = net->tc_w1p;
-    tw.wout = net->w_dev + net->off_wout;
-    tw.bout = net->bout;
-    tw.H = net->H;
-    tw.L = net->L;
-    tw.d_q = net->d_q;
-    if ((e = launch_tc(w, tw, net->num_sms, s))) return cuda_fail(e, "tensor-core kernel launch");
+    if ((e = launch_tc(w, net->tcw, net->num_sms, s))) return cuda_fail(e, "tensor-core kernel launch");
   }
   if (net->prof_stop && (e = cudaEventRecord(net->prof_stop, s))) return cuda_fail(e, "cudaEventRecord");
   return GCDF_OK;
@@ -261,10 +272,10 @@ int gcdf_create_net(const gcdf_net_desc* desc, const float* weights_host, size_t
     const int H = desc->hidden;
     if (H != 64 && H != 128 && H != 256 && H != 512)
       return fail(GCDF_EUNSUPPORTED, "FP32 path: hidden must be 64, 128, 256 or 512 (got %d)", H);
-    if (fp32_smem_bytes(H, desc->n_hidden_layers) > 227 * 1024)
+    if ((int)fp32_smem_bytes(H, desc->n_hidden_layers) > kSmemLimit)
       return fail(GCDF_EUNSUPPORTED, "FP32 path: %d layers of width %d exceed shared memory", desc->n_hidden_layers, H);
   } else if (!tc_supported(desc->hidden, desc->n_hidden_layers, desc->n_dof)) {
-    return fail(GCDF_EUNSUPPORTED, "BF16 path: shape (hidden %d, layers %d, n_dof %d) not built",
+    return fail(GCDF_EUNSUPPORTED, "tensor-core path: shape (hidden %d, layers %d, n_dof %d) not built",
                 desc->hidden, desc->n_hidden_layers, desc->n_dof);
   }
   gcdf_net* n = new (std::nothrow) gcdf_net();
@@ -285,6 +296,10 @@ int gcdf_create_net(const gcdf_net_desc* desc, const float* weights_host, size_t
   n->off_wout = need - 1 - n->H;
   n->bout = weights_host[need - 1];
   if ((rc = dev_alloc_copy(&n->w_dev, weights_host, need))) { free_net(n); return rc; }
+  {
+    const int zero = 0;
+    if ((rc = dev_alloc_copy(&n->err_word, &zero, 1))) { free_net(n); return rc; }
+  }
   rc = (n->precision == GCDF_FP32) ? build_fp32_images(n, weights_host) : build_tc_images(n, weights_host);
   if (rc) { free_net(n); return rc; }
   *out = n;
@@ -355,6 +370,19 @@ int gcdf_collision_cost(gcdf_net* net, const float* q, int N, const float* p, in
     w.tiles_per_wp = 0;
   }
   if ((e = launch_merge(w, N, cost, grad, argmin, s))) return cuda_fail(e, "merge launch");
+  g_err[0] = 0;
+  return GCDF_OK;
+}
+
+int gcdf_device_status(gcdf_net* net, int* status) {
+  if (!net || !status) return fail(GCDF_EINVAL, "net or status is NULL");
+  int v = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  if ((e = cudaMemcpy(&v, net->err_word, sizeof(int), cudaMemcpyDeviceToHost))) return cuda_fail(e, "cudaMemcpy");
+  const int zero = 0;
+  if ((e = cudaMemcpy(net->err_word, &zero, sizeof(int), cudaMemcpyHostToDevice))) return cuda_fail(e, "cudaMemcpy");
+  *status = v;
   g_err[0] = 0;
   return GCDF_OK;
 }

@@ -1,8 +1,10 @@
 // Internal declarations shared by the libgcdf translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "../../include/gcdf.h"
@@ -201,16 +203,20 @@ cudaError_t launch_fp32(const WorkDesc& w, const Fp32Weights& fw, int num_sms, c
 size_t fp32_smem_bytes(int H, int L);
 
 struct TcWeights {
-  const __nv_bfloat16* slabs;  // tensor-core weight image (see tc_path.cu)
+  CUtensorMap map_w;           // stacked 16-bit operands of layers 2..L (forward, then transposed)
+  CUtensorMap map_j;           // 16-bit W_1q^T, padded to nj rows
   const float* bias;           // (L-1) x [H] biases of layers 2..L
   const float* W1p;            // [H][3] point columns of layer 1
   const float* wout;           // [H]
   float bout;
-  int H, L, d_q;
-  int slab_count;
+  int H, L, d_q, nj;
+  int f16;                     // operand format: 1 = FP16, 0 = BF16
+  int* err;                    // device status word (set when a bounded wait gives up)
 };
 cudaError_t launch_tc(const WorkDesc& w, const TcWeights& tw, int num_sms, cudaStream_t s);
-size_t tc_slab_elems(int H, int L, int d_q);
-void tc_build_slabs(const float* W, int H, int L, int d_q, int d_in, __nv_bfloat16* out);
+size_t tc_image_elems(int H, int L, int d_q);
+void tc_build_image(const float* W, int H, int L, int d_q, int d_in, bool f16, uint16_t* out);
+int tc_encode_maps(const uint16_t* image, int H, int L, int d_q, bool f16, TcWeights& tw);
+int tc_nj(int d_q);
 
 }  // namespace gcdf
