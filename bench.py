@@ -108,8 +108,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+WAYPOINTS, POINTS = 128, 16384
+
+
 def make_workload():
-    return synth.box_scene(n_waypoints=128, n_points=16384)
+    return synth.box_scene(n_waypoints=WAYPOINTS, n_points=POINTS)
 
 
 # ---------------------------------------------------------------------------
@@ -168,8 +171,9 @@ def run_reference(args):
         "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * secs / len(rs), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name + "_softmin_T0.02", "n_waypoints": 128, "n_points": 16384,
-                   "net": "9-DOF 4x256 SiLU", "sample": "whole waypoints, bounded time per step"},
+        "config": {"workload": wl.name + "_softmin_T0.02", "n_waypoints": wl.q.shape[0],
+                   "n_points": wl.p.shape[0], "net": "9-DOF 4x256 SiLU",
+                   "sample": "whole waypoints, bounded time per step"},
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": rs[-1]["cores"], "kind": "oracle",
                          "sample": rs[-1]["sample"]},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -221,6 +225,9 @@ def run_gpu(args):
     k_stop = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     s_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     s_stop = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for ev in k_start + k_stop:
+        ev.record(stream)  # creates the CUDA event (PyTorch creates it on first record)
+    torch.cuda.synchronize()
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
@@ -285,10 +292,10 @@ def run_gpu(args):
     fpp = flops_per_pair(s)
     kern_avg_s = statistics.mean(kern_ms) / 1e3
     achieved_tflops = fpp * P / kern_avg_s / 1e12
-    if args.precision == "bf16":
+    if args.precision in ("bf16", "fp16"):
         peak = float(peaks["bf16_tflops"])
         bound, punit = "tensor", "TFLOP/s"
-        peak_note = f"bf16 dense burst, {peak_src}"
+        peak_note = f"bf16 dense burst, {peak_src} (fp16 dense rate is the same)"
     else:
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         bound, punit = "alu", "TFLOP/s"
@@ -309,7 +316,7 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "bf16" if args.precision == "bf16" else "f32",
+        "dtype": {"bf16": "bf16", "fp16": "f16", "fp32": "f32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": wl.name + "_softmin_T0.02", "n_waypoints": int(q.shape[0]),
                    "n_points": int(p.shape[0]), "pairs_per_step": P, "net": "9-DOF 4x256 SiLU",
@@ -337,11 +344,15 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
     ap.add_argument("--ref-budget", type=float, default=12.0, help="seconds of oracle work per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch from ncu")
+    ap.add_argument("--waypoints", type=int, default=128, help="smaller scenes for profiling only")
+    ap.add_argument("--points", type=int, default=16384, help="smaller scenes for profiling only")
     args = ap.parse_args()
+    global WAYPOINTS, POINTS
+    WAYPOINTS, POINTS = args.waypoints, args.points
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
