@@ -12,7 +12,8 @@
 //   df/denc = W_1q^T g_1,  then the sin/cos chain rule.
 //
 // Layout.  A tile is TP = 8192 / H pairs of one waypoint.  256 threads; thread
-// (pg, fg) owns pairs 4pg..4pg+3 and features fg + G f (f = 0..7, G = H / 8).
+// (pg, fg) owns pairs 4pg..4pg+3 and features fg + G f (f = 0..7, G = H / 8);
+// a warp spans 4 pair groups and 8 feature groups.
 // Activations live in shared memory feature-major, act[c][pair] (row stride
 // TP + 4 floats); weight rows stream through a double-buffered shared chunk of
 // KC rows with cp.async.  The weight images are pre-permuted on the host so a
@@ -101,8 +102,12 @@ fp32_fused_kernel(const WorkDesc w, const Fp32Weights fw) {
   float* pts = smem + lay.pts;
 
   const int tid = threadIdx.x;
-  const int pg = tid / C::G;
-  const int fg = tid - pg * C::G;
+  // A warp covers 4 pair groups x 8 feature groups, so its weight reads touch
+  // 8 distinct 32-byte rows (broadcast to the 4 pair groups) and its
+  // activation reads 4 distinct 16-byte rows.
+  const int warp = tid >> 5, lane = tid & 31;
+  const int pg = (warp / (C::G / 8)) * 4 + (lane >> 3);
+  const int fg = (warp % (C::G / 8)) * 8 + (lane & 7);
   const int L = fw.L;
   const int nseq = 2 * (L - 1) * C::NCH;  // chunks per tile
   const int n = w.n_dof;
@@ -306,7 +311,6 @@ fp32_fused_kernel(const WorkDesc w, const Fp32Weights fw) {
         pr = partial_warp_reduce(w.mode, w.param, pr);
         // TP <= 32 for H >= 256: one warp holds the tile.  Larger tiles merge warps in order.
         __shared__ Partial wpart[4];
-        const int warp = tid >> 5;
         if ((tid & 31) == 0) wpart[warp] = pr;
         if (C::TP > 32) asm volatile("bar.sync 1, %0;\n" ::"r"(((C::TP + 31) / 32) * 32));
         if (tid == 0) {

@@ -10,28 +10,42 @@
 // per-tile partial of the min / soft-min / hinge reduction.
 //
 // Mapping onto the SM.  A tile is 128 pairs of one waypoint (the MMA's M).
-// Every H x H product — forward and reverse — is one 128 x 256 x 256 MMA
-// chain issued by one thread: D (TMEM, FP32) = A (shared, 16-bit, 128 pairs x K)
-// x B (shared, 16-bit weight slab); the 16-bit format is BF16 or FP16.  A holds the current activations h_l (or
-// reverse gradients g_l) and is rewritten in place by the epilogue warps after
-// each MMA chain completes.  Weights stream through a ring of 32 KB slabs
-// (256 rows x 64 K, 128-byte swizzle) loaded by TMA; the forward operand of
-// layer l is W_l and the reverse operand is a stored copy of W_l^T, so both
-// are K-major.  s'(z_l) of layers 2..L-1 is kept in TMEM next to the
-// accumulator as packed FP16 pairs (an internal value, so it takes the 16-bit
-// format with more mantissa bits whatever the operand format); s'(z_1) is
-// recomputed from A_i + W_1p p_j.
+// Each H x H product of the forward pass and of the reverse sweep ("a step")
+// is two MMA chains of N = 128 output columns ("halves" a and b), each
+// D (TMEM, FP32) = A (shared, 16-bit, 128 pairs x 256) x B (shared, 16-bit
+// weight slabs of 128 rows x 64).  The A operand is double buffered: step s
+// reads buffer (tile + s) mod 2 and its epilogue writes the other, so the
+// epilogue of half a runs while the tensor core computes half b, and the
+// epilogue of half b runs while the next step's half a consumes its first 128
+// input columns (written by half a's epilogue).  Weights stream through a ring
+// of 16 KB slabs loaded by TMA; the reverse operands are stored copies of
+// W_l^T scaled by 1/2 (exact), so both directions are K-major.
 //
-// TMEM columns (512 allocated): [0, 256) accumulator; [256 + 128 s, 384 + 128 s)
-// stash of s'(z_{s+2}), s = 0..L-3.
+// Epilogue arithmetic (packed FP16 pairs for layers 2..L-1):
+//   u = z / 2 = acc / 2 + b / 2,  t = tanh(u),  s(z) = z sigma(z) = u (1 + t),
+//   2 s'(z) = (1 + t) + s(z) (1 - t)
+// 2 s'(z_l) of layers 2..L-1 stays in TMEM as FP16 pairs; the halved reverse
+// operands cancel the factor 2.  s'(z_1) is recomputed from A_i + W_1p p_j.
+// The last forward layer (f and g_L) uses FP32 arithmetic.
 //
-// Warp roles (320 threads): warp 0 issues TMA loads, warp 1 allocates TMEM and
-// issues MMAs, warps 2..9 are the epilogue (thread = one pair row; warps
-// 2..5 take columns 0..127, warps 6..9 columns 128..255).
+// TMEM columns (512 allocated): [0, 128) accumulator half a, [128, 256) half b,
+// [256 + 128 s, 384 + 128 s) FP16-pair stash of layer s + 2, s = 0..L-3;
+// the input-Jacobian chain writes [256, 256 + nj) after the stash is consumed.
 //
-// Every wait on an mbarrier is bounded (about a second); on expiry the kernel
-// records an error in a device status word, stops issuing work, drains its
-// outstanding copies and MMAs and frees TMEM before returning.
+// Tile boundary: as soon as the last reverse chain has finished reading its
+// A buffer, each group writes the next tile's first layer into it, so the
+// next tile's chains start while this tile's outputs (chain rule, reduction)
+// are still being produced.
+//
+// Warp roles (576 threads): warp 0 issues TMA loads, warp 1 allocates TMEM
+// and issues MMAs, warps 2..17 are the epilogue: two groups of 8 warps, one
+// per half; thread = one pair row (TMEM lane) and 64 columns.  The
+// input-Jacobian operand W_1q^T streams through the same ring as the weights.
+//
+// Every cross-warp handoff is an mbarrier and every wait on one is bounded
+// (about a second).  On expiry the kernel records an error in a device status
+// word, stops issuing work, drains its outstanding copies and MMAs and frees
+// TMEM before returning; no named barrier can strand a warp.
 #include <cstring>
 #include <vector>
 
@@ -42,55 +56,54 @@ namespace gcdf {
 
 namespace {
 
-constexpr int kTile = 128;          // pairs per tile (MMA M)
-constexpr int kH = 256;             // hidden width handled by this kernel
-constexpr int kStages = 4;          // weight ring depth
-constexpr int kSlabBytes = kH * 128;  // 256 rows x 64 bf16
+constexpr int kTile = 128;             // pairs per tile (MMA M)
+constexpr int kH = 256;                // hidden width handled by this kernel
+constexpr int kHalf = 128;             // output columns per MMA chain
+constexpr int kStages = 5;             // weight ring depth
+constexpr int kSlabBytes = kHalf * 128;  // 128 rows x 64 16-bit values
 constexpr int kABytes = kTile * kH * 2;
-constexpr int kThreads = 320;
-constexpr int kEpiThreads = 256;
+constexpr int kThreads = 576;
+constexpr int kGroupThreads = 256;     // epilogue threads per half
+constexpr int kEpiWarps = 16;
 constexpr uint32_t kTmemCols = 512;
 
 // shared memory map (offsets from the 1024-aligned base)
-constexpr int kOffA = 0;
-constexpr int kOffRing = kOffA + kABytes;                     // 65536
-constexpr int kOffJ = kOffRing + kStages * kSlabBytes;        // 196608
-constexpr int kJBytesMax = 4 * 32 * 128;                      // nj <= 32
-constexpr int kOffBias = kOffJ + kJBytesMax;                  // (L-1) x 256 floats, L <= 4
-constexpr int kOffW1p = kOffBias + 3 * kH * 4;
-constexpr int kOffWout = kOffW1p + 3 * kH * 4;
-constexpr int kOffAi = kOffWout + kH * 4;
-constexpr int kOffPts = kOffAi + kH * 4;                      // 128 x float4
-constexpr int kOffF = kOffPts + kTile * 16;                   // 2 x 128 floats
-constexpr int kOffPart = kOffF + 2 * kTile * 4;               // 4 partial records
+constexpr int kOffA0 = 0;
+constexpr int kOffA1 = kABytes;
+constexpr int kOffRing = 2 * kABytes;                           // 131072
+constexpr int kOffBiasF = kOffRing + kStages * kSlabBytes;      // [H] fp32 b_L / 2
+constexpr int kOffBiasH = kOffBiasF + kH * 4;                   // [(L-2) x H/2] f16x2 b_l / 2, L <= 4
+constexpr int kOffW1p = kOffBiasH + 2 * (kH / 2) * 4;           // [H] float4 W_1p / 2
+constexpr int kOffWoh = kOffW1p + kH * 16;                      // [H] fp32 w_o / 2
+constexpr int kOffAiw = kOffWoh + kH * 4;                       // [16 warps][64] fp32 A_i / 2
+constexpr int kOffTrig = kOffAiw + kEpiWarps * 64 * 4;          // [4 warps][2 tiles][24] sin, cos
+constexpr int kOffF = kOffTrig + 4 * 2 * 24 * 4;                // [4][128] f partials
+constexpr int kOffPart = kOffF + 4 * kTile * 4;                 // 4 partial records
 constexpr int kOffBar = kOffPart + 4 * (int)sizeof(Partial);
-constexpr int kNumBars = 2 * kStages + 4;
+constexpr int kNumBars = 2 * kStages + 6;
 constexpr int kOffSlot = kOffBar + kNumBars * 8;
-constexpr int kSmemBytes = kOffSlot + 16 + 1024;              // + alignment slack
+constexpr int kSmemBytes = kOffSlot + 16 + 1024;                // + alignment slack
+static_assert(kSmemBytes <= 227 * 1024 - 64, "shared memory budget");
+
+// barrier indices
+constexpr int B_FULL0 = 0;              // + stage
+constexpr int B_EMPTY0 = kStages;       // + stage
+constexpr int B_ACC0 = 2 * kStages;     // + half: accumulator half complete (tcgen05.commit)
+constexpr int B_ED0 = 2 * kStages + 2;  // + half: epilogue of that half done (256 arrivals)
+constexpr int B_FD = 2 * kStages + 4;   // f partials written (512 arrivals)
+constexpr int B_PD = 2 * kStages + 5;   // per-warp partial records written (4 arrivals)
 
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
 
-struct Shared {
-  uint32_t base;      // shared-window address of the aligned base
-  uint8_t* gbase;     // generic pointer to the aligned base
-};
+__device__ __forceinline__ uint32_t bar(uint32_t base, int i) { return base + kOffBar + 8 * i; }
 
-__device__ __forceinline__ uint32_t bar_addr(const Shared& sh, int i) { return sh.base + kOffBar + 8 * i; }
-// barrier indices
-__device__ __forceinline__ int B_FULL(int s) { return s; }
-__device__ __forceinline__ int B_EMPTY(int s) { return kStages + s; }
-constexpr int B_J = 2 * kStages;
-constexpr int B_ACC = 2 * kStages + 1;
-constexpr int B_AFULL = 2 * kStages + 2;
-constexpr int B_DONE = 2 * kStages + 3;
-
-// Bounded wait; returns false (and raises the abort flag) on expiry or when
-// another role has already aborted.
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
-  if (ptx::mbar_try_wait(bar, parity)) return true;
+// Wait used by the single-thread producer and MMA roles: gives up early when
+// another role has aborted.
+__device__ __forceinline__ bool wait_role(uint32_t b, uint32_t parity, volatile int* abort_flag, int* err) {
+  if (ptx::mbar_try_wait(b, parity)) return true;
   const long long t0 = clock64();
   while (true) {
-    if (ptx::mbar_try_wait(bar, parity)) return true;
+    if (ptx::mbar_try_wait(b, parity)) return true;
     if (*abort_flag) return false;
     if (clock64() - t0 > kWaitCycles) {
       *abort_flag = 1;
@@ -100,9 +113,22 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
   }
 }
 
-__device__ __forceinline__ float silu_sig(float z) { return fmaf(0.5f, ptx::tanh_approx(0.5f * z), 0.5f); }
+// Wait used by epilogue threads: only its own time limit ends it, so every
+// thread waiting on the same phase takes the same decision.
+__device__ __forceinline__ bool wait_epi(uint32_t b, uint32_t parity, volatile int* abort_flag, int* err) {
+  if (ptx::mbar_try_wait(b, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (ptx::mbar_try_wait(b, parity)) return true;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      atomicOr(err, 1);
+      return false;
+    }
+  }
+}
 
-// Byte offset of element (row, k) of a 128-row, 256-wide K-major BF16 operand
+// Byte offset of element (row, k) of a 128-row, 256-wide K-major 16-bit operand
 // stored as four 64-wide chunks in the 128-byte swizzle layout; k multiple of 8.
 __device__ __forceinline__ uint32_t a_offset(int row, int k) {
   const int chunk = k >> 6;
@@ -114,14 +140,100 @@ __device__ __forceinline__ int total_tiles(const WorkDesc& w) {
   return w.tile_start ? w.tile_start[w.N] : w.n_tiles;
 }
 
+constexpr uint32_t kOne2 = 0x3C003C00u;   // (1.0, 1.0) in FP16
+constexpr uint32_t kHalf2 = 0x38003800u;  // (0.5, 0.5) in FP16
+
+// Packed SiLU of u = z / 2: returns s(z) and 2 s'(z) for two values.
+__device__ __forceinline__ void silu2(uint32_t u, uint32_t& h, uint32_t& s2) {
+  const uint32_t t = ptx::htanh2(u);
+  h = ptx::hfma2(u, t, u);
+  s2 = ptx::hfma2(h, ptx::hsub2(kOne2, t), ptx::hadd2(kOne2, t));
+}
+
+template <bool kF16>
+__device__ __forceinline__ uint32_t to_operand(uint32_t f16pair) {
+  return kF16 ? f16pair : ptx::f16x2_to_bf16x2(f16pair);
+}
+
+// u_1 = z_1 / 2 for columns c, c+1 of this thread's pair (FP32); ah = A_i / 2
+// for those columns (warp-private staging), w = W_1p / 2.
+__device__ __forceinline__ void first_layer_u(const float4* s_w1p, float2 ah, int c, float px, float py, float pz,
+                                              float& u0, float& u1) {
+  const float4 w0 = s_w1p[c], w1 = s_w1p[c + 1];
+  u0 = fmaf(w0.z, pz, fmaf(w0.y, py, fmaf(w0.x, px, ah.x)));
+  u1 = fmaf(w1.z, pz, fmaf(w1.y, py, fmaf(w1.x, px, ah.y)));
+}
+
+__device__ __forceinline__ void store8(uint32_t abuf, int row, int c0, const uint32_t* o) {
+  ptx::st_shared_v4(abuf + a_offset(row, c0), o[0], o[1], o[2], o[3]);
+  ptx::st_shared_v4(abuf + a_offset(row, c0 + 8), o[4], o[5], o[6], o[7]);
+}
+
+// Per-tile reduction of 32 rows of a warp (lane = row) into one partial
+// record held by lane 0: argmin by (f, list position) with NaN first, then
+// the mode's sums.  SOFTMIN takes one exponential per row relative to the
+// warp minimum.
+__device__ __forceinline__ Partial warp_tile_partial(int mode, float param, bool valid, float f, const float* dq,
+                                                     int n, int idx, int pos) {
+  float fm = valid ? f : __int_as_float(0x7f800000);
+  int pm = valid ? pos : 0x7fffffff;
+  int im = valid ? idx : -1;
+  int src = threadIdx.x & 31;
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    const float fo = __shfl_xor_sync(0xffffffffu, fm, m);
+    const int po = __shfl_xor_sync(0xffffffffu, pm, m);
+    const int io = __shfl_xor_sync(0xffffffffu, im, m);
+    const int so = __shfl_xor_sync(0xffffffffu, src, m);
+    if (first_is_better(fo, po, fm, pm)) { fm = fo; pm = po; im = io; src = so; }
+  }
+  Partial r = partial_identity(mode);
+  if (pm == 0x7fffffff) return r;  // no valid row
+  r.idx = im;
+  r.pos = pm;
+  float wgt, v0;
+  if (mode == kMin) {
+    r.v0 = fm;
+#pragma unroll
+    for (int d = 0; d < kMaxDof; ++d) r.g[d] = __shfl_sync(0xffffffffu, dq[d], src);
+    return r;
+  }
+  if (mode == kSoftmin) {
+    wgt = valid ? __expf(-(f - fm) / param) : 0.f;
+    if (valid && f != f) wgt = f;
+    v0 = fm;
+  } else {
+    wgt = (valid && f < param) ? -1.f : 0.f;
+    v0 = valid ? fmaxf(0.f, param - f) : 0.f;
+    if (valid && f != f) v0 = f;
+  }
+  float acc[kMaxDof + 1];
+  acc[kMaxDof] = (mode == kSoftmin) ? wgt : v0;
+#pragma unroll
+  for (int d = 0; d < kMaxDof; ++d) acc[d] = (d < n) ? wgt * dq[d] : 0.f;
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1)
+#pragma unroll
+    for (int d = 0; d <= kMaxDof; ++d) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], m);
+  if (mode == kSoftmin) {
+    r.v0 = fm;
+    r.v1 = acc[kMaxDof];
+  } else {
+    r.v0 = acc[kMaxDof];
+    r.v1 = fm;
+  }
+#pragma unroll
+  for (int d = 0; d < kMaxDof; ++d) r.g[d] = acc[d];
+  return r;
+}
+
 template <bool kF16>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
                 const __grid_constant__ CUtensorMap map_j, const TcWeights tw) {
   extern __shared__ uint8_t smem_raw[];
-  Shared sh;
-  sh.base = (ptx::smem_u32(smem_raw) + 1023u) & ~1023u;
-  sh.gbase = smem_raw + (sh.base - ptx::smem_u32(smem_raw));
+  const uint32_t base = (ptx::smem_u32(smem_raw) + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - ptx::smem_u32(smem_raw));
   __shared__ int abort_flag_s;
   volatile int* abort_flag = &abort_flag_s;
 
@@ -129,44 +241,51 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
   const int warp = tid >> 5;
   const int lane = tid & 31;
   const int L = tw.L;
-  const int n_wphases = 2 * (L - 1);       // MMA chains that read weight slabs, per tile
-  const int n_phases = n_wphases + 1;      // plus the input-Jacobian chain
+  const int n_steps = 2 * (L - 1);  // weight steps per tile (forward then reverse)
   const int nj = tw.nj;
   const int ntiles = total_tiles(w);
   int my_tiles = 0;
   if ((int)blockIdx.x < ntiles) my_tiles = (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;
 
-  float* s_bias = reinterpret_cast<float*>(sh.gbase + kOffBias);
-  float* s_w1p = reinterpret_cast<float*>(sh.gbase + kOffW1p);
-  float* s_wout = reinterpret_cast<float*>(sh.gbase + kOffWout);
-  float* s_ai = reinterpret_cast<float*>(sh.gbase + kOffAi);
-  float4* s_pts = reinterpret_cast<float4*>(sh.gbase + kOffPts);
-  float* s_f = reinterpret_cast<float*>(sh.gbase + kOffF);
-  Partial* s_part = reinterpret_cast<Partial*>(sh.gbase + kOffPart);
-  uint32_t* s_slot = reinterpret_cast<uint32_t*>(sh.gbase + kOffSlot);
+  float* s_biasF = reinterpret_cast<float*>(gbase + kOffBiasF);
+  uint32_t* s_biasH = reinterpret_cast<uint32_t*>(gbase + kOffBiasH);
+  float4* s_w1p = reinterpret_cast<float4*>(gbase + kOffW1p);
+  float* s_woh = reinterpret_cast<float*>(gbase + kOffWoh);
+  float* s_aiw = reinterpret_cast<float*>(gbase + kOffAiw);
+  float* s_f = reinterpret_cast<float*>(gbase + kOffF);
+  Partial* s_part = reinterpret_cast<Partial*>(gbase + kOffPart);
+  uint32_t* s_slot = reinterpret_cast<uint32_t*>(gbase + kOffSlot);
 
   // ---- setup -------------------------------------------------------------------
   if (tid == 0) {
     abort_flag_s = 0;
     for (int s = 0; s < kStages; ++s) {
-      ptx::mbar_init(bar_addr(sh, B_FULL(s)), 1);
-      ptx::mbar_init(bar_addr(sh, B_EMPTY(s)), 1);
+      ptx::mbar_init(bar(base, B_FULL0 + s), 1);
+      ptx::mbar_init(bar(base, B_EMPTY0 + s), 1);
     }
-    ptx::mbar_init(bar_addr(sh, B_J), 1);
-    ptx::mbar_init(bar_addr(sh, B_ACC), 1);
-    ptx::mbar_init(bar_addr(sh, B_AFULL), kEpiThreads);
-    ptx::mbar_init(bar_addr(sh, B_DONE), 1);
+    ptx::mbar_init(bar(base, B_ACC0 + 0), 1);
+    ptx::mbar_init(bar(base, B_ACC0 + 1), 1);
+    ptx::mbar_init(bar(base, B_ED0 + 0), kGroupThreads);
+    ptx::mbar_init(bar(base, B_ED0 + 1), kGroupThreads);
+    ptx::mbar_init(bar(base, B_FD), 2 * kGroupThreads);
+    ptx::mbar_init(bar(base, B_PD), 4);
     ptx::fence_barrier_init();
     ptx::prefetch_tensormap(&map_w);
     ptx::prefetch_tensormap(&map_j);
   }
   if (warp == 1) {
-    ptx::tmem_alloc(sh.base + kOffSlot, kTmemCols);
+    ptx::tmem_alloc(base + kOffSlot, kTmemCols);
     ptx::tmem_relinquish();
   }
-  for (int i = tid; i < (L - 1) * kH; i += kThreads) s_bias[i] = tw.bias[i];
-  for (int i = tid; i < 3 * kH; i += kThreads) s_w1p[i] = tw.W1p[i];
-  for (int i = tid; i < kH; i += kThreads) s_wout[i] = tw.wout[i];
+  for (int c = tid; c < kH; c += kThreads) {
+    s_biasF[c] = 0.5f * tw.bias[(size_t)(L - 2) * kH + c];
+    s_w1p[c] = make_float4(0.5f * tw.W1p[3 * c], 0.5f * tw.W1p[3 * c + 1], 0.5f * tw.W1p[3 * c + 2], 0.f);
+    s_woh[c] = 0.5f * tw.wout[c];
+  }
+  for (int i = tid; i < (L - 2) * (kH / 2); i += kThreads) {
+    const int l = i / (kH / 2), c = 2 * (i % (kH / 2));
+    s_biasH[i] = ptx::pack_f16x2(0.5f * tw.bias[(size_t)l * kH + c], 0.5f * tw.bias[(size_t)l * kH + c + 1]);
+  }
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
@@ -175,261 +294,318 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
   if (warp == 0) {
     // ================= TMA producer =================
     if (lane == 0 && my_tiles > 0) {
-      const uint32_t jbytes = 4u * nj * 128u;
-      ptx::mbar_arrive_expect_tx(bar_addr(sh, B_J), jbytes);
-      for (int kc = 0; kc < 4; ++kc)
-        ptx::tma_load_2d(sh.base + kOffJ + kc * nj * 128, &map_j, kc * 64, 0, bar_addr(sh, B_J));
       long long g = 0;
       bool ok = true;
+      auto next_stage = [&](uint32_t bytes) -> int {
+        const int st = (int)(g % kStages);
+        const uint32_t u = (uint32_t)(g / kStages);
+        if (u > 0 && !wait_role(bar(base, B_EMPTY0 + st), (u - 1) & 1u, abort_flag, tw.err)) return -1;
+        ptx::mbar_arrive_expect_tx(bar(base, B_FULL0 + st), bytes);
+        return st;
+      };
       for (int it = 0; it < my_tiles && ok; ++it) {
-        for (int ph = 0; ph < n_wphases && ok; ++ph) {
-          const int row = (ph < L - 1) ? ph * kH : (L - 1 + (2 * L - 3 - ph)) * kH;
-          for (int kc = 0; kc < 4; ++kc, ++g) {
-            const int s = (int)(g % kStages);
-            const uint32_t u = (uint32_t)(g / kStages);
-            if (u > 0 && !wait_bar(bar_addr(sh, B_EMPTY(s)), (u - 1) & 1u, abort_flag, tw.err)) { ok = false; break; }
-            ptx::mbar_arrive_expect_tx(bar_addr(sh, B_FULL(s)), kSlabBytes);
-            ptx::tma_load_2d(sh.base + kOffRing + s * kSlabBytes, &map_w, kc * 64, row, bar_addr(sh, B_FULL(s)));
-          }
+        for (int s = 0; s < n_steps && ok; ++s) {
+          const int row0 = (s < L - 1) ? s * kH : (L - 1 + (2 * L - 3 - s)) * kH;
+          for (int hh = 0; hh < 2 && ok; ++hh)
+            for (int kc = 0; kc < 4; ++kc, ++g) {
+              const int st = next_stage(kSlabBytes);
+              if (st < 0) { ok = false; break; }
+              ptx::tma_load_2d(base + kOffRing + st * kSlabBytes, &map_w, kc * 64, row0 + hh * kHalf,
+                               bar(base, B_FULL0 + st));
+            }
+        }
+        for (int kc = 0; kc < 4 && ok; ++kc, ++g) {  // W_1q^T, nj rows
+          const int st = next_stage((uint32_t)nj * 128u);
+          if (st < 0) { ok = false; break; }
+          ptx::tma_load_2d(base + kOffRing + st * kSlabBytes, &map_j, kc * 64, 0, bar(base, B_FULL0 + st));
         }
       }
-      // drain: every issued load must land before the CTA exits
+      // drain: every issued load lands before the CTA exits
       for (long long k = (g > kStages ? g - kStages : 0); k < g; ++k) {
-        const int s = (int)(k % kStages);
         const long long t0 = clock64();
-        while (!ptx::mbar_try_wait(bar_addr(sh, B_FULL(s)), (uint32_t)(k / kStages) & 1u))
-          if (clock64() - t0 > kWaitCycles) { atomicOr(tw.err, 2); break; }
-      }
-      {
-        const long long t0 = clock64();
-        while (!ptx::mbar_try_wait(bar_addr(sh, B_J), 0))
+        while (!ptx::mbar_try_wait(bar(base, B_FULL0 + (int)(k % kStages)), (uint32_t)(k / kStages) & 1u))
           if (clock64() - t0 > kWaitCycles) { atomicOr(tw.err, 2); break; }
       }
     }
   } else if (warp == 1) {
     // ================= MMA issuer =================
     if (lane == 0 && my_tiles > 0) {
-      const uint32_t id256 = ptx::idesc_f16kind(kTile, kH, kF16);
+      const uint32_t id128 = ptx::idesc_f16kind(kTile, kHalf, kF16);
       const uint32_t idj = ptx::idesc_f16kind(kTile, nj, kF16);
       long long g = 0;
-      uint32_t ak = 0;
-      bool ok = wait_bar(bar_addr(sh, B_J), 0, abort_flag, tw.err);
+      uint32_t ea = 0, eb = 0;
+      bool ok = true;
       for (int it = 0; it < my_tiles && ok; ++it) {
-        for (int ph = 0; ph < n_phases && ok; ++ph) {
-          if (!wait_bar(bar_addr(sh, B_AFULL), ak & 1u, abort_flag, tw.err)) { ok = false; break; }
-          ++ak;
-          ptx::tc_fence_after();
-          if (ph < n_wphases) {
+        for (int s = 0; s <= n_steps && ok; ++s) {
+          const uint32_t abuf = base + (((it + s) & 1) ? kOffA1 : kOffA0);
+          // the input Jacobian df/denc = W_1q^T g_1 goes to TMEM columns [256, 256 + nj):
+          // the stash is free by then, so the next tile's first chain need not wait for it
+          const bool jstep = (s == n_steps);
+          for (int hh = 0; hh < (jstep ? 1 : 2) && ok; ++hh) {
             for (int kc = 0; kc < 4; ++kc, ++g) {
-              const int s = (int)(g % kStages);
-              if (!wait_bar(bar_addr(sh, B_FULL(s)), (uint32_t)(g / kStages) & 1u, abort_flag, tw.err)) {
+              if (hh == 0 && kc == 0) {
+                if (!wait_role(bar(base, B_ED0 + 0), ea & 1u, abort_flag, tw.err)) { ok = false; break; }
+                ++ea;
+                ptx::tc_fence_after();
+              }
+              if (hh == 0 && kc == 2) {
+                if (!wait_role(bar(base, B_ED0 + 1), eb & 1u, abort_flag, tw.err)) { ok = false; break; }
+                ++eb;
+                ptx::tc_fence_after();
+              }
+              const int st = (int)(g % kStages);
+              if (!wait_role(bar(base, B_FULL0 + st), (uint32_t)(g / kStages) & 1u, abort_flag, tw.err)) {
                 ok = false;
                 break;
               }
               ptx::tc_fence_after();
-              const uint32_t aslab = sh.base + kOffA + kc * (kTile * 128);
-              const uint32_t bslab = sh.base + kOffRing + s * kSlabBytes;
+              const uint32_t aslab = abuf + kc * (kTile * 128);
+              const uint32_t bslab = base + kOffRing + st * kSlabBytes;
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks)
-                ptx::mma_bf16(tmem, ptx::smem_desc_sw128(aslab + ks * 32, 1024),
-                              ptx::smem_desc_sw128(bslab + ks * 32, 1024), id256, (kc | ks) != 0);
-              ptx::mma_commit(bar_addr(sh, B_EMPTY(s)));
+                ptx::mma_bf16(tmem + (jstep ? 256 : hh * kHalf), ptx::smem_desc_sw128(aslab + ks * 32, 1024),
+                              ptx::smem_desc_sw128(bslab + ks * 32, 1024), jstep ? idj : id128, (kc | ks) != 0);
+              ptx::mma_commit(bar(base, B_EMPTY0 + st));
             }
-            if (!ok) break;
-          } else {
-            for (int kc = 0; kc < 4; ++kc) {
-              const uint32_t aslab = sh.base + kOffA + kc * (kTile * 128);
-              const uint32_t bslab = sh.base + kOffJ + kc * nj * 128;
-#pragma unroll
-              for (int ks = 0; ks < 4; ++ks)
-                ptx::mma_bf16(tmem, ptx::smem_desc_sw128(aslab + ks * 32, 1024),
-                              ptx::smem_desc_sw128(bslab + ks * 32, 1024), idj, (kc | ks) != 0);
-            }
+            if (ok) ptx::mma_commit(bar(base, B_ACC0 + hh));
           }
-          ptx::mma_commit(bar_addr(sh, B_ACC));
         }
       }
-      // all issued MMAs complete before TMEM is released
-      ptx::mma_commit(bar_addr(sh, B_DONE));
-      const long long t0 = clock64();
-      while (!ptx::mbar_try_wait(bar_addr(sh, B_DONE), 0))
-        if (clock64() - t0 > kWaitCycles) { atomicOr(tw.err, 2); break; }
+      // all issued MMAs complete before TMEM is released: wait for the last
+      // EMPTY arrivals (they follow every earlier MMA of this thread)
+      for (long long k = (g > kStages ? g - kStages : 0); k < g; ++k) {
+        const long long t0 = clock64();
+        while (!ptx::mbar_try_wait(bar(base, B_EMPTY0 + (int)(k % kStages)), (uint32_t)(k / kStages) & 1u))
+          if (clock64() - t0 > kWaitCycles) { atomicOr(tw.err, 2); break; }
+      }
     }
   } else {
-    // ================= epilogue: 8 warps, one pair row per thread =================
+    // ================= epilogue: 16 warps, one pair row and 64 columns per thread =========
     const int e = warp - 2;
     const int quad = warp & 3;
-    const int hf = e >> 2;
+    const int hf = (e >> 2) >> 1;   // half / group
+    const int ks64 = (e >> 2) & 1;  // which 64 of the group's 128 columns
     const int row = quad * 32 + lane;
-    const int col0 = hf * 128;
-    const int etid = e * 32 + lane;  // 0..255
+    const int cbase = hf * kHalf + ks64 * 64;
     const uint32_t t_lane = tmem + ((uint32_t)(quad * 32) << 16);
-    const uint32_t a_base = sh.base + kOffA;
     const int n = w.n_dof;
-    uint32_t acc_k = 0;
+    const bool ej = (hf == 0 && ks64 == 0);  // writes this tile's outputs
+    float* aiw = s_aiw + e * 64;             // this warp's A_i / 2 for columns cbase..cbase+63
+    float* trigw = reinterpret_cast<float*>(gbase + kOffTrig) + quad * 2 * 24;  // EJ warps only
+    uint32_t acc_n = 0;    // completions of ACC[hf] consumed
     bool ok = true;
-    for (int it = 0; it < my_tiles && ok; ++it) {
-      const int t = (int)blockIdx.x + it * (int)gridDim.x;
-      int wp = 0, start = 0, len = 0;
-      tile_lookup(w, t, wp, start, len);
-      ptx::named_bar_sync(1, kEpiThreads);  // previous tile fully consumed
-      s_ai[etid] = w.A[(size_t)wp * kH + etid];
-      if (etid < kTile) {
-        float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (etid < len) {
-          int j;
-          long long k;
-          pair_at(w, wp, start + etid, j, k);
-          pv = make_float4(w.p[3 * (size_t)j], w.p[3 * (size_t)j + 1], w.p[3 * (size_t)j + 2], 0.f);
-        }
-        s_pts[etid] = pv;
-      }
-      ptx::named_bar_sync(1, kEpiThreads);
-      const float4 pt = s_pts[row];
 
-      // ---- P1: h_1 = s(A_i + W_1p p) -> A --------------------------------------
-      for (int c = col0; c < col0 + 128; c += 8) {
-        uint32_t pk[4];
+    int t = 0, wp = 0, start = 0, len = 0;
+    float px = 0.f, py = 0.f, pz = 0.f;
+
+    auto load_tile = [&](int it) {
+      t = (int)blockIdx.x + it * (int)gridDim.x;
+      tile_lookup(w, t, wp, start, len);
+      px = py = pz = 0.f;
+      if (row < len) {
+        int j;
+        long long k;
+        pair_at(w, wp, start + row, j, k);
+        px = w.p[3 * (size_t)j];
+        py = w.p[3 * (size_t)j + 1];
+        pz = w.p[3 * (size_t)j + 2];
+      }
+      const float* Ai = w.A + (size_t)wp * kH + cbase;
+      __syncwarp();
+      aiw[lane] = 0.5f * Ai[lane];
+      aiw[32 + lane] = 0.5f * Ai[32 + lane];
+      if (ej && lane < 2 * w.n_ang) trigw[(it & 1) * 24 + lane] = w.trig[(size_t)wp * 2 * w.n_ang + lane];
+      __syncwarp();
+    };
+    // h_1 = s(A_i + W_1p p) for this thread's row and 64 columns -> A buffer (tile parity)
+    auto first_layer = [&](int it) {
+      const uint32_t abuf = base + ((it & 1) ? kOffA1 : kOffA0);
+#pragma unroll 1
+      for (int cc = 0; cc < 64; cc += 16) {
+        uint32_t o[8];
 #pragma unroll
-        for (int i = 0; i < 8; i += 2) {
-          float hv[2];
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int cc = c + i + u;
-            const float z = fmaf(s_w1p[3 * cc + 2], pt.z, fmaf(s_w1p[3 * cc + 1], pt.y, fmaf(s_w1p[3 * cc], pt.x, s_ai[cc])));
-            hv[u] = z * silu_sig(z);
-          }
-          pk[i >> 1] = ptx::pack2<kF16>(hv[0], hv[1]);
+        for (int i = 0; i < 8; ++i) {
+          float u0, u1;
+          first_layer_u(s_w1p, *reinterpret_cast<const float2*>(aiw + cc + 2 * i), cbase + cc + 2 * i, px, py, pz,
+                        u0, u1);
+          const uint32_t u = ptx::pack_f16x2(u0, u1);
+          const uint32_t tt = ptx::htanh2(u);
+          o[i] = to_operand<kF16>(ptx::hfma2(u, tt, u));
         }
-        ptx::st_shared_v4(a_base + a_offset(row, c), pk[0], pk[1], pk[2], pk[3]);
+        store8(abuf, row, cbase + cc, o);
       }
       ptx::tc_fence_before();
       ptx::fence_proxy_async_smem();
-      ptx::mbar_arrive(bar_addr(sh, B_AFULL));
+      ptx::mbar_arrive(bar(base, B_ED0 + hf));
+    };
 
-      float fpart = 0.f;
-      for (int ph = 0; ph < n_phases; ++ph) {
-        if (!wait_bar(bar_addr(sh, B_ACC), acc_k & 1u, abort_flag, tw.err)) { ok = false; break; }
-        ++acc_k;
+    if (my_tiles > 0) {
+      load_tile(0);
+      first_layer(0);
+    }
+    for (int it = 0; it < my_tiles && ok; ++it) {
+      for (int s = 0; s < n_steps; ++s) {
+        if (!wait_epi(bar(base, B_ACC0 + hf), acc_n & 1u, abort_flag, tw.err)) { ok = false; break; }
+        ++acc_n;
         ptx::tc_fence_after();
-        if (ph < L - 1) {
-          // forward epilogue of layer l = ph + 2
-          const int l = ph + 2;
-          const float* bias = s_bias + (l - 2) * kH;
-          for (int cc = 0; cc < 128; cc += 32) {
-            const int c0 = col0 + cc;
-            uint32_t v[32];
-            ptx::tmem_ld32(t_lane + c0, v);
+        const uint32_t obuf = base + (((it + s + 1) & 1) ? kOffA1 : kOffA0);
+        const uint32_t t_acc = t_lane + hf * kHalf + ks64 * 64;  // accumulator columns of this thread
+        if (s < L - 2) {
+          // middle forward layer l = s + 2: h_l -> A, 2 s'(z_l) -> stash
+          const uint32_t t_st = t_lane + 256 + 128 * s + (cbase >> 1);
+          const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + s * (kH / 2) + (cbase >> 1));
+#pragma unroll 1
+          for (int cc = 0; cc < 64; cc += 16) {
+            uint32_t v[16];
+            ptx::tmem_ld16(t_acc + cc, v);
+            const uint4 b0 = bh4[cc / 8], b1 = bh4[cc / 8 + 1];
+            const uint32_t bh[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
             ptx::tmem_wait_ld();
-            uint32_t hp[16], dp[16];
+            uint32_t o[8], st2[8];
 #pragma unroll
-            for (int i = 0; i < 32; i += 2) {
-              float hv[2], dv[2];
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                const float z = __uint_as_float(v[i + u]) + bias[c0 + i + u];
-                const float sg = silu_sig(z);
-                const float h = z * sg;
-                const float d = sg * fmaf(z, 1.f - sg, 1.f);
-                if (l == L) {
-                  fpart = fmaf(s_wout[c0 + i + u], h, fpart);
-                  hv[u] = s_wout[c0 + i + u] * d;  // g_L
-                } else {
-                  hv[u] = h;
-                }
-                dv[u] = d;
-              }
-              hp[i >> 1] = ptx::pack2<kF16>(hv[0], hv[1]);
-              dp[i >> 1] = ptx::pack_f16x2(dv[0], dv[1]);  // stash is always FP16
+            for (int i = 0; i < 8; ++i) {
+              const uint32_t zp = ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+              uint32_t h;
+              silu2(ptx::hfma2(zp, kHalf2, bh[i]), h, st2[i]);
+              o[i] = to_operand<kF16>(h);
             }
-#pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4)
-              ptx::st_shared_v4(a_base + a_offset(row, c0 + 8 * q4), hp[4 * q4], hp[4 * q4 + 1], hp[4 * q4 + 2],
-                                hp[4 * q4 + 3]);
-            if (l < L) ptx::tmem_st16(t_lane + 256 + 128 * (l - 2) + (c0 >> 1), dp);
+            store8(obuf, row, cbase + cc, o);
+            ptx::tmem_st8(t_st + cc / 2, st2);
           }
-          if (l < L) ptx::tmem_wait_st();
-          if (l == L) s_f[hf * kTile + row] = fpart;
-        } else if (ph < n_wphases) {
-          // reverse epilogue: g_{l-1} = u * s'(z_{l-1}), l = 2L - 1 - ph
-          const int lm1 = 2 * L - 2 - ph;
-          for (int cc = 0; cc < 128; cc += 32) {
-            const int c0 = col0 + cc;
-            uint32_t v[32];
-            uint32_t sd[16];
-            ptx::tmem_ld32(t_lane + c0, v);
-            if (lm1 >= 2) ptx::tmem_ld16(t_lane + 256 + 128 * (lm1 - 2) + (c0 >> 1), sd);
+          ptx::tmem_wait_st();
+        } else if (s == L - 2) {
+          // last forward layer (FP32): f partial, g_L = w_o s'(z_L) -> A
+          float fpart = 0.f;  // sum of (w_o / 2) s(z_L)
+#pragma unroll 1
+          for (int cc = 0; cc < 64; cc += 16) {
+            uint32_t v[16];
+            ptx::tmem_ld16(t_acc + cc, v);
             ptx::tmem_wait_ld();
-            uint32_t gp[16];
+            uint32_t o[8];
 #pragma unroll
-            for (int i = 0; i < 32; i += 2) {
-              float gv[2];
+            for (int i4 = 0; i4 < 16; i4 += 4) {
+              const float4 bf = *reinterpret_cast<const float4*>(s_biasF + cbase + cc + i4);
+              const float4 wh = *reinterpret_cast<const float4*>(s_woh + cbase + cc + i4);
+              const float bv[4] = {bf.x, bf.y, bf.z, bf.w};
+              const float wv[4] = {wh.x, wh.y, wh.z, wh.w};
+              float gv[4];
 #pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                float d;
-                if (lm1 >= 2) {
-                  d = u ? ptx::f16hi(sd[i >> 1]) : ptx::f16lo(sd[i >> 1]);
-                } else {
-                  const int c = c0 + i + u;
-                  const float z = fmaf(s_w1p[3 * c + 2], pt.z, fmaf(s_w1p[3 * c + 1], pt.y, fmaf(s_w1p[3 * c], pt.x, s_ai[c])));
-                  const float sg = silu_sig(z);
-                  d = sg * fmaf(z, 1.f - sg, 1.f);
-                }
-                gv[u] = __uint_as_float(v[i + u]) * d;
+              for (int q = 0; q < 4; ++q) {
+                const float u = fmaf(__uint_as_float(v[i4 + q]), 0.5f, bv[q]);
+                const float tt = ptx::tanh_approx(u);
+                const float h = fmaf(u, tt, u);
+                fpart = fmaf(wv[q], h, fpart);
+                gv[q] = wv[q] * fmaf(h, 1.f - tt, 1.f + tt);
               }
-              gp[i >> 1] = ptx::pack2<kF16>(gv[0], gv[1]);
+              o[i4 / 2] = ptx::pack2<kF16>(gv[0], gv[1]);
+              o[i4 / 2 + 1] = ptx::pack2<kF16>(gv[2], gv[3]);
             }
-#pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4)
-              ptx::st_shared_v4(a_base + a_offset(row, c0 + 8 * q4), gp[4 * q4], gp[4 * q4 + 1], gp[4 * q4 + 2],
-                                gp[4 * q4 + 3]);
+            store8(obuf, row, cbase + cc, o);
           }
+          s_f[(hf * 2 + ks64) * kTile + row] = 2.f * fpart;
+          ptx::mbar_arrive(bar(base, B_FD));
         } else {
-          // input-Jacobian result: df/denc in accumulator columns [0, d_q)
-          ptx::named_bar_sync(2, kEpiThreads);  // s_f written by both halves
-          if (hf == 0) {
-            uint32_t v[32];
-            ptx::tmem_ld32(t_lane, v);
+          // reverse step: g_{l-1} = acc * 2 s'(z_{l-1}), acc = (W_l^T / 2) g_l
+          const int lm1 = 2 * L - 2 - s;
+#pragma unroll 1
+          for (int cc = 0; cc < 64; cc += 16) {
+            uint32_t v[16], d2[8];
+            ptx::tmem_ld16(t_acc + cc, v);
+            if (lm1 >= 2) ptx::tmem_ld8(t_lane + 256 + 128 * (lm1 - 2) + ((cbase + cc) >> 1), d2);
             ptx::tmem_wait_ld();
-            const float fval = s_f[row] + s_f[kTile + row] + tw.bout;
-            const float* tr = w.trig + (size_t)wp * 2 * w.n_ang;
-            float dq[kMaxDof];
+            if (lm1 < 2) {
 #pragma unroll
-            for (int d = 0; d < kMaxDof; ++d) dq[d] = 0.f;
-            dq[0] = __uint_as_float(v[0]);
-            dq[1] = __uint_as_float(v[1]);
-#pragma unroll
-            for (int a = 0; a < kMaxAngles; ++a)
-              if (a < w.n_ang)
-                dq[2 + a] = tr[2 * a + 1] * __uint_as_float(v[2 + 2 * a]) - tr[2 * a] * __uint_as_float(v[3 + 2 * a]);
-            const bool valid = row < len;
-            int j = -1;
-            long long k = 0;
-            if (valid) pair_at(w, wp, start + row, j, k);
-            if (w.mode == kQuery) {
-              if (valid) {
-                w.f_out[k] = fval;
-                if (w.g_out)
-                  for (int d = 0; d < n; ++d) w.g_out[(size_t)k * n + d] = dq[d];
-              }
-            } else {
-              Partial pr = valid ? partial_of_pair(w.mode, w.param, fval, dq, n, j, start + row)
-                                 : partial_identity(w.mode);
-              pr = partial_warp_reduce(w.mode, w.param, pr);
-              if (lane == 0) s_part[quad] = pr;
-              ptx::named_bar_sync(3, 128);
-              if (quad == 0 && lane == 0) {
-                Partial a = s_part[0];
-                for (int qq = 1; qq < 4; ++qq) a = partial_combine(w.mode, w.param, a, s_part[qq]);
-                w.partials[t] = a;
+              for (int i = 0; i < 8; ++i) {
+                float u0, u1;
+                first_layer_u(s_w1p, *reinterpret_cast<const float2*>(aiw + cc + 2 * i), cbase + cc + 2 * i, px,
+                              py, pz, u0, u1);
+                uint32_t h;
+                silu2(ptx::pack_f16x2(u0, u1), h, d2[i]);
               }
             }
+            uint32_t o[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const uint32_t ap = ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+              o[i] = to_operand<kF16>(ptx::hmul2(ap, d2[i]));
+            }
+            store8(obuf, row, cbase + cc, o);
           }
-          break;  // no A write after the last chain of the tile
         }
         ptx::tc_fence_before();
         ptx::fence_proxy_async_smem();
-        ptx::mbar_arrive(bar_addr(sh, B_AFULL));
+        ptx::mbar_arrive(bar(base, B_ED0 + hf));
+      }
+      if (!ok) break;
+
+      // ---- tile tail -----------------------------------------------------------
+      const int cur_t = t, cur_wp = wp, cur_start = start, cur_len = len;
+      if (it + 1 < my_tiles) {
+        if (hf == 0) {
+          // the next first layer overwrites the buffer the last reverse chain of
+          // half b reads: wait for its completion (number (2L-2)(it+1) of ACC[b])
+          const uint32_t par = (uint32_t)((2 * L - 2) * (it + 1) - 1) & 1u;
+          if (!wait_epi(bar(base, B_ACC0 + 1), par, abort_flag, tw.err)) { ok = false; break; }
+          ptx::tc_fence_after();
+        }
+        load_tile(it + 1);
+        first_layer(it + 1);
+      }
+      if (hf == 0) {
+        // the input-Jacobian chain of this tile (completion 2L-1 of ACC[a] per tile)
+        if (!wait_epi(bar(base, B_ACC0 + 0), acc_n & 1u, abort_flag, tw.err)) { ok = false; break; }
+        ++acc_n;
+        ptx::tc_fence_after();
+      }
+      if (ej) {
+        if (!wait_epi(bar(base, B_FD), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }
+        uint32_t v[32];
+        if (w.n_ang <= 7) {
+          ptx::tmem_ld16(t_lane + 256, v);
+        } else {
+          ptx::tmem_ld32(t_lane + 256, v);
+        }
+        const float fval = s_f[row] + s_f[kTile + row] + s_f[2 * kTile + row] + s_f[3 * kTile + row] + tw.bout;
+        ptx::tmem_wait_ld();
+        const float* tr = trigw + (it & 1) * 24;
+        float dq[kMaxDof];
+        dq[0] = __uint_as_float(v[0]);
+        dq[1] = __uint_as_float(v[1]);
+#pragma unroll
+        for (int a = 0; a < kMaxAngles; ++a)
+          dq[2 + a] = (a < w.n_ang) ? tr[2 * a + 1] * __uint_as_float(v[2 + 2 * a]) -
+                                          tr[2 * a] * __uint_as_float(v[3 + 2 * a])
+                                    : 0.f;
+        const bool valid = row < cur_len;
+        int j = -1;
+        long long k = 0;
+        if (valid) pair_at(w, cur_wp, cur_start + row, j, k);
+        if (w.mode == kQuery) {
+          if (valid) {
+            w.f_out[k] = fval;
+            if (w.g_out) {
+              float* go = w.g_out + (size_t)k * n;
+#pragma unroll
+              for (int d = 0; d < kMaxDof; ++d)
+                if (d < n) go[d] = dq[d];
+            }
+          }
+        } else {
+          const Partial pr = warp_tile_partial(w.mode, w.param, valid, fval, dq, n, j, cur_start + row);
+          if (lane == 0) {
+            s_part[quad] = pr;
+            ptx::mbar_arrive(bar(base, B_PD));
+          }
+          if (quad == 0 && lane == 0) {
+            if (!wait_epi(bar(base, B_PD), (uint32_t)it & 1u, abort_flag, tw.err)) {
+              ok = false;
+            } else {
+              Partial a = s_part[0];
+              for (int qq = 1; qq < 4; ++qq) a = partial_combine(w.mode, w.param, a, s_part[qq]);
+              w.partials[cur_t] = a;
+            }
+          }
+        }
       }
     }
   }
@@ -459,17 +635,26 @@ EncodeTiledFn get_encode() {
   return fn;
 }
 
-int encode_2d(CUtensorMap* m, const void* base, int rows, int cols, int box_rows, bool f16) {
+int encode_2d(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows, bool f16) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return 1;
   cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t gstride[1] = {(cuuint64_t)cols * 2};
   cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void*>(ptr), gdim, gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : 2;
+}
+
+uint16_t to_bits(float x, bool f16) {
+  if (f16) {
+    const __half h = __float2half_rn(x);
+    return *reinterpret_cast<const uint16_t*>(&h);
+  }
+  const __nv_bfloat16 b = __float2bfloat16_rn(x);
+  return *reinterpret_cast<const uint16_t*>(&b);
 }
 
 }  // namespace
@@ -480,21 +665,13 @@ bool tc_supported(int H, int L, int n_dof) { return H == kH && L >= 2 && L <= 4 
 
 int tc_nj(int d_q) { return d_q <= 16 ? 16 : 32; }
 
-// Image layout (BF16, row-major, 256 columns): rows [256 m, 256 m + 256) hold
+// Image layout (16-bit, row-major, 256 columns): rows [256 m, 256 m + 256) hold
 // W_{m+2} for m = 0..L-2 (forward operands, row = output feature), then rows
-// [256 (L-1+m), ...) hold W_{m+2}^T (reverse operands, row = input feature),
-// then nj rows of W_1q^T (row d = input column 3 + d of layer 1; zero rows pad).
+// [256 (L-1+m), ...) hold W_{m+2}^T / 2 (reverse operands, row = input
+// feature; the factor 1/2 is exact), then nj rows of W_1q^T (row d = input
+// column 3 + d of layer 1; zero rows pad).
 size_t tc_image_elems(int H, int L, int d_q) {
   return (size_t)2 * (L - 1) * H * H + (size_t)tc_nj(d_q) * H;
-}
-
-static uint16_t to_bits(float x, bool f16) {
-  if (f16) {
-    const __half h = __float2half_rn(x);
-    return *reinterpret_cast<const uint16_t*>(&h);
-  }
-  const __nv_bfloat16 b = __float2bfloat16_rn(x);
-  return *reinterpret_cast<const uint16_t*>(&b);
 }
 
 void tc_build_image(const float* W, int H, int L, int d_q, int d_in, bool f16, uint16_t* out) {
@@ -505,21 +682,19 @@ void tc_build_image(const float* W, int H, int L, int d_q, int d_in, bool f16, u
     uint16_t* rev = out + (size_t)(L - 1 + m) * H * H;
     for (int o = 0; o < H; ++o)
       for (int i = 0; i < H; ++i) {
-        const uint16_t b = to_bits(Wl[(size_t)o * H + i], f16);
-        fwd[(size_t)o * H + i] = b;
-        rev[(size_t)i * H + o] = b;
+        fwd[(size_t)o * H + i] = to_bits(Wl[(size_t)o * H + i], f16);
+        rev[(size_t)i * H + o] = to_bits(0.5f * Wl[(size_t)o * H + i], f16);
       }
     off += (size_t)H * H + H;
   }
   uint16_t* J = out + (size_t)2 * (L - 1) * H * H;
   const int nj = tc_nj(d_q);
   for (int d = 0; d < nj; ++d)
-    for (int c = 0; c < H; ++c)
-      J[(size_t)d * H + c] = to_bits(d < d_q ? W[(size_t)c * d_in + 3 + d] : 0.f, f16);
+    for (int c = 0; c < H; ++c) J[(size_t)d * H + c] = to_bits(d < d_q ? W[(size_t)c * d_in + 3 + d] : 0.f, f16);
 }
 
 int tc_encode_maps(const uint16_t* image, int H, int L, int d_q, bool f16, TcWeights& tw) {
-  int rc = encode_2d(&tw.map_w, image, 2 * (L - 1) * H, H, 256, f16);
+  int rc = encode_2d(&tw.map_w, image, 2 * (L - 1) * H, H, kHalf, f16);
   if (rc) return rc;
   return encode_2d(&tw.map_j, image + (size_t)2 * (L - 1) * H * H, tc_nj(d_q), H, tc_nj(d_q), f16);
 }
