@@ -30,7 +30,8 @@
 //
 // TMEM columns (512 allocated): [0, 128) accumulator half a, [128, 256) half b,
 // [256 + 128 s, 384 + 128 s) FP16-pair stash of layer s + 2, s = 0..L-3;
-// the input-Jacobian chain writes [256, 256 + nj) after the stash is consumed.
+// the input-Jacobian chain writes [384, 384 + nj) after the stash is consumed
+// (the next tile refills those columns only after its outputs are read).
 //
 // Tile boundary: as soon as the last reverse chain has finished reading its
 // A buffer, each group writes the next tile's first layer into it, so the
@@ -38,8 +39,8 @@
 // are still being produced.
 //
 // Warp roles (576 threads): warp 0 issues TMA loads, warp 1 allocates TMEM
-// and issues MMAs, warps 2..17 are the epilogue: two groups of 8 warps, one
-// per half; thread = one pair row (TMEM lane) and 64 columns.  The
+// and issues MMAs, warps 2..17 are the epilogue: all 16 process each half in
+// turn; thread = one pair row (TMEM lane) and 32 columns of each half.  The
 // input-Jacobian operand W_1q^T streams through the same ring as the weights.
 //
 // Every cross-warp handoff is an mbarrier and every wait on one is bounded
@@ -63,7 +64,7 @@ constexpr int kStages = 5;             // weight ring depth
 constexpr int kSlabBytes = kHalf * 128;  // 128 rows x 64 16-bit values
 constexpr int kABytes = kTile * kH * 2;
 constexpr int kThreads = 576;
-constexpr int kGroupThreads = 256;     // epilogue threads per half
+constexpr int kEpiThreads = 512;       // epilogue threads (16 warps)
 constexpr int kEpiWarps = 16;
 constexpr uint32_t kTmemCols = 512;
 
@@ -89,7 +90,7 @@ static_assert(kSmemBytes <= 227 * 1024 - 64, "shared memory budget");
 constexpr int B_FULL0 = 0;              // + stage
 constexpr int B_EMPTY0 = kStages;       // + stage
 constexpr int B_ACC0 = 2 * kStages;     // + half: accumulator half complete (tcgen05.commit)
-constexpr int B_ED0 = 2 * kStages + 2;  // + half: epilogue of that half done (256 arrivals)
+constexpr int B_ED0 = 2 * kStages + 2;  // + half: epilogue of that half done (512 arrivals)
 constexpr int B_FD = 2 * kStages + 4;   // f partials written (512 arrivals)
 constexpr int B_PD = 2 * kStages + 5;   // per-warp partial records written (4 arrivals)
 
@@ -114,26 +115,19 @@ __device__ __forceinline__ bool wait_role(uint32_t b, uint32_t parity, volatile 
 }
 
 // Wait used by epilogue threads: only its own time limit ends it, so every
-// thread waiting on the same phase takes the same decision.
+// thread waiting on the same phase takes the same decision.  Waiting threads
+// sleep in hardware rather than poll, leaving issue slots to working warps.
 __device__ __forceinline__ bool wait_epi(uint32_t b, uint32_t parity, volatile int* abort_flag, int* err) {
   if (ptx::mbar_try_wait(b, parity)) return true;
   const long long t0 = clock64();
   while (true) {
-    if (ptx::mbar_try_wait(b, parity)) return true;
+    if (ptx::mbar_try_wait_sleep(b, parity, 100000u)) return true;
     if (clock64() - t0 > kWaitCycles) {
       *abort_flag = 1;
       atomicOr(err, 1);
       return false;
     }
   }
-}
-
-// Byte offset of element (row, k) of a 128-row, 256-wide K-major 16-bit operand
-// stored as four 64-wide chunks in the 128-byte swizzle layout; k multiple of 8.
-__device__ __forceinline__ uint32_t a_offset(int row, int k) {
-  const int chunk = k >> 6;
-  const int j = (k & 63) >> 3;
-  return chunk * (kTile * 128) + (row >> 3) * 1024 + (row & 7) * 128 + ((j ^ (row & 7)) << 4);
 }
 
 __device__ __forceinline__ int total_tiles(const WorkDesc& w) {
@@ -164,10 +158,6 @@ __device__ __forceinline__ void first_layer_u(const float4* s_w1p, float2 ah, in
   u1 = fmaf(w1.z, pz, fmaf(w1.y, py, fmaf(w1.x, px, ah.y)));
 }
 
-__device__ __forceinline__ void store8(uint32_t abuf, int row, int c0, const uint32_t* o) {
-  ptx::st_shared_v4(abuf + a_offset(row, c0), o[0], o[1], o[2], o[3]);
-  ptx::st_shared_v4(abuf + a_offset(row, c0 + 8), o[4], o[5], o[6], o[7]);
-}
 
 // Per-tile reduction of 32 rows of a warp (lane = row) into one partial
 // record held by lane 0: argmin by (f, list position) with NaN first, then
@@ -265,9 +255,9 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     }
     ptx::mbar_init(bar(base, B_ACC0 + 0), 1);
     ptx::mbar_init(bar(base, B_ACC0 + 1), 1);
-    ptx::mbar_init(bar(base, B_ED0 + 0), kGroupThreads);
-    ptx::mbar_init(bar(base, B_ED0 + 1), kGroupThreads);
-    ptx::mbar_init(bar(base, B_FD), 2 * kGroupThreads);
+    ptx::mbar_init(bar(base, B_ED0 + 0), kEpiThreads);
+    ptx::mbar_init(bar(base, B_ED0 + 1), kEpiThreads);
+    ptx::mbar_init(bar(base, B_FD), kEpiThreads);
     ptx::mbar_init(bar(base, B_PD), 4);
     ptx::fence_barrier_init();
     ptx::prefetch_tensormap(&map_w);
@@ -338,7 +328,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       for (int it = 0; it < my_tiles && ok; ++it) {
         for (int s = 0; s <= n_steps && ok; ++s) {
           const uint32_t abuf = base + (((it + s) & 1) ? kOffA1 : kOffA0);
-          // the input Jacobian df/denc = W_1q^T g_1 goes to TMEM columns [256, 256 + nj):
+          // the input Jacobian df/denc = W_1q^T g_1 goes to TMEM columns [384, 384 + nj):
           // the stash is free by then, so the next tile's first chain need not wait for it
           const bool jstep = (s == n_steps);
           for (int hh = 0; hh < (jstep ? 1 : 2) && ok; ++hh) {
@@ -363,7 +353,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               const uint32_t bslab = base + kOffRing + st * kSlabBytes;
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks)
-                ptx::mma_bf16(tmem + (jstep ? 256 : hh * kHalf), ptx::smem_desc_sw128(aslab + ks * 32, 1024),
+                ptx::mma_bf16(tmem + (jstep ? 384 : hh * kHalf), ptx::smem_desc_sw128(aslab + ks * 32, 1024),
                               ptx::smem_desc_sw128(bslab + ks * 32, 1024), jstep ? idj : id128, (kc | ks) != 0);
               ptx::mma_commit(bar(base, B_EMPTY0 + st));
             }
@@ -380,24 +370,32 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       }
     }
   } else {
-    // ================= epilogue: 16 warps, one pair row and 64 columns per thread =========
+    // ================= epilogue: 16 warps, one pair row, 32 columns of each half ========
     const int e = warp - 2;
     const int quad = warp & 3;
-    const int hf = (e >> 2) >> 1;   // half / group
-    const int ks64 = (e >> 2) & 1;  // which 64 of the group's 128 columns
+    const int kq = e >> 2;                 // which 32 columns of each half
     const int row = quad * 32 + lane;
-    const int cbase = hf * kHalf + ks64 * 64;
     const uint32_t t_lane = tmem + ((uint32_t)(quad * 32) << 16);
     const int n = w.n_dof;
-    const bool ej = (hf == 0 && ks64 == 0);  // writes this tile's outputs
-    float* aiw = s_aiw + e * 64;             // this warp's A_i / 2 for columns cbase..cbase+63
+    const bool ej = (kq == 0);             // writes this tile's outputs
+    const uint32_t rbase = (row >> 3) * 1024 + (row & 7) * 128;
+    const int r7 = row & 7;
+    float* aiw = s_aiw + e * 64;           // A_i / 2 for this thread's 32 + 32 columns
     float* trigw = reinterpret_cast<float*>(gbase + kOffTrig) + quad * 2 * 24;  // EJ warps only
-    uint32_t acc_n = 0;    // completions of ACC[hf] consumed
+    uint32_t acc_n[2] = {0, 0};            // completions of ACC[a], ACC[b] consumed
     bool ok = true;
 
     int t = 0, wp = 0, start = 0, len = 0;
     float px = 0.f, py = 0.f, pz = 0.f;
 
+    // byte offset (within an A buffer) of columns c0 + 8 q .. c0 + 8 q + 7 of this row
+    auto aoff = [&](int c0, int q) -> uint32_t {
+      return (c0 >> 6) * (kTile * 128) + rbase + (((((c0 & 63) >> 3) + q) ^ r7) << 4);
+    };
+    auto store8c = [&](uint32_t abuf, int c0, const uint32_t* o) {
+      ptx::st_shared_v4(abuf + aoff(c0, 0), o[0], o[1], o[2], o[3]);
+      ptx::st_shared_v4(abuf + aoff(c0, 1), o[4], o[5], o[6], o[7]);
+    };
     auto load_tile = [&](int it) {
       t = (int)blockIdx.x + it * (int)gridDim.x;
       tile_lookup(w, t, wp, start, len);
@@ -410,160 +408,160 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         py = w.p[3 * (size_t)j + 1];
         pz = w.p[3 * (size_t)j + 2];
       }
-      const float* Ai = w.A + (size_t)wp * kH + cbase;
+      const float* Ai = w.A + (size_t)wp * kH + 32 * kq;
       __syncwarp();
       aiw[lane] = 0.5f * Ai[lane];
-      aiw[32 + lane] = 0.5f * Ai[32 + lane];
+      aiw[32 + lane] = 0.5f * Ai[kHalf + lane];
       if (ej && lane < 2 * w.n_ang) trigw[(it & 1) * 24 + lane] = w.trig[(size_t)wp * 2 * w.n_ang + lane];
       __syncwarp();
     };
-    // h_1 = s(A_i + W_1p p) for this thread's row and 64 columns -> A buffer (tile parity)
-    auto first_layer = [&](int it) {
+    // h_1 = s(A_i + W_1p p) for this row and 32 columns of half h -> A buffer (tile parity)
+    auto first_layer = [&](int it, int h) {
       const uint32_t abuf = base + ((it & 1) ? kOffA1 : kOffA0);
+      const int c0 = h * kHalf + 32 * kq;
 #pragma unroll 1
-      for (int cc = 0; cc < 64; cc += 16) {
+      for (int cc = 0; cc < 32; cc += 16) {
         uint32_t o[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           float u0, u1;
-          first_layer_u(s_w1p, *reinterpret_cast<const float2*>(aiw + cc + 2 * i), cbase + cc + 2 * i, px, py, pz,
-                        u0, u1);
+          first_layer_u(s_w1p, *reinterpret_cast<const float2*>(aiw + 32 * h + cc + 2 * i), c0 + cc + 2 * i, px, py,
+                        pz, u0, u1);
           const uint32_t u = ptx::pack_f16x2(u0, u1);
           const uint32_t tt = ptx::htanh2(u);
           o[i] = to_operand<kF16>(ptx::hfma2(u, tt, u));
         }
-        store8(abuf, row, cbase + cc, o);
+        store8c(abuf, c0 + cc, o);
       }
       ptx::tc_fence_before();
       ptx::fence_proxy_async_smem();
-      ptx::mbar_arrive(bar(base, B_ED0 + hf));
+      ptx::mbar_arrive(bar(base, B_ED0 + h));
     };
 
     if (my_tiles > 0) {
       load_tile(0);
-      first_layer(0);
+      first_layer(0, 0);
+      first_layer(0, 1);
     }
+    float fpart = 0.f;  // sum of (w_o / 2) s(z_L) over this thread's 64 columns
     for (int it = 0; it < my_tiles && ok; ++it) {
-      for (int s = 0; s < n_steps; ++s) {
-        if (!wait_epi(bar(base, B_ACC0 + hf), acc_n & 1u, abort_flag, tw.err)) { ok = false; break; }
-        ++acc_n;
-        ptx::tc_fence_after();
+      for (int s = 0; s < n_steps && ok; ++s) {
         const uint32_t obuf = base + (((it + s + 1) & 1) ? kOffA1 : kOffA0);
-        const uint32_t t_acc = t_lane + hf * kHalf + ks64 * 64;  // accumulator columns of this thread
-        if (s < L - 2) {
-          // middle forward layer l = s + 2: h_l -> A, 2 s'(z_l) -> stash
-          const uint32_t t_st = t_lane + 256 + 128 * s + (cbase >> 1);
-          const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + s * (kH / 2) + (cbase >> 1));
+        for (int h = 0; h < 2; ++h) {
+          if (!wait_epi(bar(base, B_ACC0 + h), acc_n[h] & 1u, abort_flag, tw.err)) { ok = false; break; }
+          ++acc_n[h];
+          ptx::tc_fence_after();
+          const int c0 = h * kHalf + 32 * kq;     // first column of this thread in this half
+          const uint32_t t_acc = t_lane + c0;     // accumulator half h starts at column h * 128
+          if (s < L - 2) {
+            // middle forward layer l = s + 2: h_l -> A, 2 s'(z_l) -> stash
+            const uint32_t t_st = t_lane + 256 + 128 * s + (c0 >> 1);
+            const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + s * (kH / 2) + (c0 >> 1));
 #pragma unroll 1
-          for (int cc = 0; cc < 64; cc += 16) {
-            uint32_t v[16];
-            ptx::tmem_ld16(t_acc + cc, v);
-            const uint4 b0 = bh4[cc / 8], b1 = bh4[cc / 8 + 1];
-            const uint32_t bh[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-            ptx::tmem_wait_ld();
-            uint32_t o[8], st2[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const uint32_t zp = ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-              uint32_t h;
-              silu2(ptx::hfma2(zp, kHalf2, bh[i]), h, st2[i]);
-              o[i] = to_operand<kF16>(h);
-            }
-            store8(obuf, row, cbase + cc, o);
-            ptx::tmem_st8(t_st + cc / 2, st2);
-          }
-          ptx::tmem_wait_st();
-        } else if (s == L - 2) {
-          // last forward layer (FP32): f partial, g_L = w_o s'(z_L) -> A
-          float fpart = 0.f;  // sum of (w_o / 2) s(z_L)
-#pragma unroll 1
-          for (int cc = 0; cc < 64; cc += 16) {
-            uint32_t v[16];
-            ptx::tmem_ld16(t_acc + cc, v);
-            ptx::tmem_wait_ld();
-            uint32_t o[8];
-#pragma unroll
-            for (int i4 = 0; i4 < 16; i4 += 4) {
-              const float4 bf = *reinterpret_cast<const float4*>(s_biasF + cbase + cc + i4);
-              const float4 wh = *reinterpret_cast<const float4*>(s_woh + cbase + cc + i4);
-              const float bv[4] = {bf.x, bf.y, bf.z, bf.w};
-              const float wv[4] = {wh.x, wh.y, wh.z, wh.w};
-              float gv[4];
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const float u = fmaf(__uint_as_float(v[i4 + q]), 0.5f, bv[q]);
-                const float tt = ptx::tanh_approx(u);
-                const float h = fmaf(u, tt, u);
-                fpart = fmaf(wv[q], h, fpart);
-                gv[q] = wv[q] * fmaf(h, 1.f - tt, 1.f + tt);
-              }
-              o[i4 / 2] = ptx::pack2<kF16>(gv[0], gv[1]);
-              o[i4 / 2 + 1] = ptx::pack2<kF16>(gv[2], gv[3]);
-            }
-            store8(obuf, row, cbase + cc, o);
-          }
-          s_f[(hf * 2 + ks64) * kTile + row] = 2.f * fpart;
-          ptx::mbar_arrive(bar(base, B_FD));
-        } else {
-          // reverse step: g_{l-1} = acc * 2 s'(z_{l-1}), acc = (W_l^T / 2) g_l
-          const int lm1 = 2 * L - 2 - s;
-#pragma unroll 1
-          for (int cc = 0; cc < 64; cc += 16) {
-            uint32_t v[16], d2[8];
-            ptx::tmem_ld16(t_acc + cc, v);
-            if (lm1 >= 2) ptx::tmem_ld8(t_lane + 256 + 128 * (lm1 - 2) + ((cbase + cc) >> 1), d2);
-            ptx::tmem_wait_ld();
-            if (lm1 < 2) {
+            for (int cc = 0; cc < 32; cc += 16) {
+              uint32_t v[16];
+              ptx::tmem_ld16(t_acc + cc, v);
+              const uint4 b0 = bh4[cc / 8], b1 = bh4[cc / 8 + 1];
+              const uint32_t bh[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+              ptx::tmem_wait_ld();
+              uint32_t o[8], st2[8];
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                float u0, u1;
-                first_layer_u(s_w1p, *reinterpret_cast<const float2*>(aiw + cc + 2 * i), cbase + cc + 2 * i, px,
-                              py, pz, u0, u1);
-                uint32_t h;
-                silu2(ptx::pack_f16x2(u0, u1), h, d2[i]);
+                const uint32_t zp = ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+                uint32_t hh;
+                silu2(ptx::hfma2(zp, kHalf2, bh[i]), hh, st2[i]);
+                o[i] = to_operand<kF16>(hh);
               }
+              store8c(obuf, c0 + cc, o);
+              ptx::tmem_st8(t_st + cc / 2, st2);
             }
-            uint32_t o[8];
+            ptx::tmem_wait_st();
+          } else if (s == L - 2) {
+            // last forward layer (FP32): f partial, g_L = w_o s'(z_L) -> A
+            if (h == 0) fpart = 0.f;
+#pragma unroll 1
+            for (int cc = 0; cc < 32; cc += 16) {
+              uint32_t v[16];
+              ptx::tmem_ld16(t_acc + cc, v);
+              ptx::tmem_wait_ld();
+              uint32_t o[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const uint32_t ap = ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-              o[i] = to_operand<kF16>(ptx::hmul2(ap, d2[i]));
+              for (int i4 = 0; i4 < 16; i4 += 4) {
+                const float4 bf = *reinterpret_cast<const float4*>(s_biasF + c0 + cc + i4);
+                const float4 wh = *reinterpret_cast<const float4*>(s_woh + c0 + cc + i4);
+                const float bv[4] = {bf.x, bf.y, bf.z, bf.w};
+                const float wv[4] = {wh.x, wh.y, wh.z, wh.w};
+                float gv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const float u = fmaf(__uint_as_float(v[i4 + q]), 0.5f, bv[q]);
+                  const float tt = ptx::tanh_approx(u);
+                  const float hv = fmaf(u, tt, u);
+                  fpart = fmaf(wv[q], hv, fpart);
+                  gv[q] = wv[q] * fmaf(hv, 1.f - tt, 1.f + tt);
+                }
+                o[i4 / 2] = ptx::pack2<kF16>(gv[0], gv[1]);
+                o[i4 / 2 + 1] = ptx::pack2<kF16>(gv[2], gv[3]);
+              }
+              store8c(obuf, c0 + cc, o);
             }
-            store8(obuf, row, cbase + cc, o);
+            if (h == 1) {
+              s_f[kq * kTile + row] = 2.f * fpart;
+              ptx::mbar_arrive(bar(base, B_FD));
+            }
+          } else {
+            // reverse step: g_{l-1} = acc * 2 s'(z_{l-1}), acc = (W_l^T / 2) g_l
+            const int lm1 = 2 * L - 2 - s;
+#pragma unroll 1
+            for (int cc = 0; cc < 32; cc += 16) {
+              uint32_t v[16], d2[8];
+              ptx::tmem_ld16(t_acc + cc, v);
+              if (lm1 >= 2) ptx::tmem_ld8(t_lane + 256 + 128 * (lm1 - 2) + ((c0 + cc) >> 1), d2);
+              ptx::tmem_wait_ld();
+              if (lm1 < 2) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  float u0, u1;
+                  first_layer_u(s_w1p, *reinterpret_cast<const float2*>(aiw + 32 * h + cc + 2 * i), c0 + cc + 2 * i,
+                                px, py, pz, u0, u1);
+                  uint32_t hh;
+                  silu2(ptx::pack_f16x2(u0, u1), hh, d2[i]);
+                }
+              }
+              uint32_t o[8];
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const uint32_t ap = ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+                o[i] = to_operand<kF16>(ptx::hmul2(ap, d2[i]));
+              }
+              store8c(obuf, c0 + cc, o);
+            }
           }
+          ptx::tc_fence_before();
+          ptx::fence_proxy_async_smem();
+          ptx::mbar_arrive(bar(base, B_ED0 + h));
         }
-        ptx::tc_fence_before();
-        ptx::fence_proxy_async_smem();
-        ptx::mbar_arrive(bar(base, B_ED0 + hf));
       }
       if (!ok) break;
 
-      // ---- tile tail -----------------------------------------------------------
+      // ---- tile tail: the last reverse chain (both halves) has completed ------
       const int cur_t = t, cur_wp = wp, cur_start = start, cur_len = len;
       if (it + 1 < my_tiles) {
-        if (hf == 0) {
-          // the next first layer overwrites the buffer the last reverse chain of
-          // half b reads: wait for its completion (number (2L-2)(it+1) of ACC[b])
-          const uint32_t par = (uint32_t)((2 * L - 2) * (it + 1) - 1) & 1u;
-          if (!wait_epi(bar(base, B_ACC0 + 1), par, abort_flag, tw.err)) { ok = false; break; }
-          ptx::tc_fence_after();
-        }
         load_tile(it + 1);
-        first_layer(it + 1);
+        first_layer(it + 1, 0);
+        first_layer(it + 1, 1);
       }
-      if (hf == 0) {
-        // the input-Jacobian chain of this tile (completion 2L-1 of ACC[a] per tile)
-        if (!wait_epi(bar(base, B_ACC0 + 0), acc_n & 1u, abort_flag, tw.err)) { ok = false; break; }
-        ++acc_n;
-        ptx::tc_fence_after();
-      }
+      // the input-Jacobian chain of this tile (completion 2L-1 of ACC[a] per tile)
+      if (!wait_epi(bar(base, B_ACC0 + 0), acc_n[0] & 1u, abort_flag, tw.err)) { ok = false; break; }
+      ++acc_n[0];
+      ptx::tc_fence_after();
       if (ej) {
         if (!wait_epi(bar(base, B_FD), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }
         uint32_t v[32];
         if (w.n_ang <= 7) {
-          ptx::tmem_ld16(t_lane + 256, v);
+          ptx::tmem_ld16(t_lane + 384, v);
         } else {
-          ptx::tmem_ld32(t_lane + 256, v);
+          ptx::tmem_ld32(t_lane + 384, v);
         }
         const float fval = s_f[row] + s_f[kTile + row] + s_f[2 * kTile + row] + s_f[3 * kTile + row] + tw.bout;
         ptx::tmem_wait_ld();
