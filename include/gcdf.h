@@ -163,6 +163,37 @@ GCDF_API int gcdf_collision_cost(gcdf_net *net, const float *q, int n_waypoints,
                         int *argmin, gcdf_stream_t stream);
 
 /*
+ * gcdf_collision_cost without any device allocation.  The paper has no
+ * counterpart: this is a deployment variant of the same computation for
+ * callers that must not allocate once running (for example a trajectory
+ * optimizer inside a real-time control loop, where an allocation can block,
+ * synchronise or fail at an unpredictable moment, or an application whose GPU
+ * memory is budgeted up front).  Arguments, outputs and results are those of
+ * gcdf_collision_cost.
+ *
+ * Every temporary comes from one 16 MiB array that is part of the library's
+ * image on each device (every GPU that loads the library holds it until the
+ * process exits).  A request needing more — per-waypoint terms
+ * (n_waypoints x (hidden + 2 (n_dof - 2)) floats), the tile prefix of point
+ * lists and one 64-byte record per tile (tiles: 128 pairs on BF16/FP16,
+ * 8192 / hidden pairs on FP32) — is rejected with GCDF_EINVAL before any work
+ * is enqueued.  Nothing in the array needs to start at zero: each call writes
+ * every word it later reads.
+ *
+ * All calls on a device share the array, so calls whose GPU work overlaps in
+ * time (on different streams, or from different threads) race and corrupt
+ * each other's results; serialise them (one stream, or events).  The first
+ * call on each device looks up the array's device address (under a lock);
+ * make that first call before any stream capture.  Calls no cudaMalloc,
+ * cudaMallocAsync or cudaFree.
+ */
+GCDF_API int gcdf_collision_cost_noalloc(gcdf_net *net, const float *q, int n_waypoints,
+                                         const float *p, int n_points, const int *part_offsets,
+                                         const int *part_idx, int n_pairs, const float *shift,
+                                         int reduction, float param, float *cost, float *grad,
+                                         int *argmin, gcdf_stream_t stream);
+
+/*
  * Device-side status of a net's kernels since the last call: 0 when every
  * bounded wait inside the tensor-core kernel completed; bit 0 set when a wait
  * gave up (the kernel then stopped issuing work, drained its copies, released

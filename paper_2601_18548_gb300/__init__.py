@@ -118,6 +118,30 @@ def collision_cost(net: Net, q: torch.Tensor, p: torch.Tensor, reduction: str = 
     return cost, grad, amin
 
 
+def collision_cost_noalloc(net: Net, q: torch.Tensor, p: torch.Tensor, reduction: str = "softmin",
+                           param: float = 0.02, part_offsets=None, part_idx=None, shift=None,
+                           out=None, stream=None):
+    """gcdf_collision_cost_noalloc: as collision_cost, but the library allocates
+    nothing (its temporaries live in a fixed per-device array).  For callers that
+    must not allocate once running; pass preallocated `out` tensors as well."""
+    lib = _lib.load()
+    N, M = q.shape[0], p.shape[0]
+    P = N * M if part_offsets is None else int(part_idx.numel())
+    if out is None:
+        cost = torch.empty(N, device=q.device, dtype=torch.float32)
+        grad = torch.empty(N, net.n_dof, device=q.device, dtype=torch.float32)
+        amin = torch.empty(N, device=q.device, dtype=torch.int32)
+    else:
+        cost, grad, amin = out
+    _lib.check(lib.gcdf_collision_cost_noalloc(net.handle, _ptr(q, name="q"), N, _ptr(p, name="p"), M,
+                                               _ptr(part_offsets, torch.int32, "part_offsets"),
+                                               _ptr(part_idx, torch.int32, "part_idx"), P,
+                                               _ptr(shift, name="shift"), _RED[reduction], float(param),
+                                               _ptr(cost, name="cost"), _ptr(grad, name="grad"),
+                                               _ptr(amin, torch.int32, "argmin"), _stream(stream)))
+    return cost, grad, amin
+
+
 def device_status(net: Net) -> int:
     """gcdf_device_status: 0, or the bits of a bounded device wait that gave up."""
     v = ctypes.c_int(0)

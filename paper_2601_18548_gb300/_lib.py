@@ -31,6 +31,7 @@ SIGNATURES = {
     "gcdf_destroy_net": (_i, [_vp]),
     "gcdf_query": (_i, [_vp, _vp, _i, _vp, _i, _vp, _vp, _i, _vp, _vp, _vp, _vp]),
     "gcdf_collision_cost": (_i, [_vp, _vp, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _f, _vp, _vp, _vp, _vp]),
+    "gcdf_collision_cost_noalloc": (_i, [_vp, _vp, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _f, _vp, _vp, _vp, _vp]),
     "gcdf_device_status": (_i, [_vp, ctypes.POINTER(_i)]),
     "gcdf_set_profile_events": (_i, [_vp, _vp, _vp]),
     "gcdf_last_error": (ctypes.c_char_p, []),

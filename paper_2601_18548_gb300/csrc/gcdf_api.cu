@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -398,5 +399,125 @@ int gcdf_set_profile_events(gcdf_net* net, void* start_event, void* stop_event) 
 }
 
 const char* gcdf_last_error(void) { return g_err; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Collision cost without any allocation (gcdf_collision_cost_noalloc).
+//
+// Some callers must not allocate device memory once they are running: a
+// trajectory optimizer inside a real-time control loop, where cudaMalloc /
+// cudaMallocAsync can block, synchronise or fail at an unpredictable moment;
+// a host application whose GPU memory is budgeted up front by another
+// framework; or code that is certified to allocate only at start-up.  For
+// them this entry point takes every temporary of a collision-cost call from
+// one array that is part of the loaded library image on each device.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 16u << 20;  // 16 MiB per device, held until the process exits
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[64] = {nullptr};
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Device address of the scratch array for the current device, looked up once
+// per device (the host-side name of the array is not a device address).
+int noalloc_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= 64) return fail(GCDF_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return GCDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gcdf_collision_cost_noalloc(gcdf_net* net, const float* q, int N, const float* p, int M,
+                                const int* part_offsets, const int* part_idx, int n_pairs, const float* shift,
+                                int reduction, float param, float* cost, float* grad, int* argmin,
+                                gcdf_stream_t stream) {
+  WorkDesc w;
+  int rc = check_call(net, q, N, p, M, part_offsets, part_idx, n_pairs, shift, w);
+  if (rc) return rc;
+  if (reduction != GCDF_RED_MIN && reduction != GCDF_RED_SOFTMIN && reduction != GCDF_RED_HINGE)
+    return fail(GCDF_EINVAL, "unknown reduction %d", reduction);
+  if (reduction == GCDF_RED_SOFTMIN && !(param > 0.f)) return fail(GCDF_EINVAL, "soft-min temperature must be > 0");
+  if (reduction == GCDF_RED_HINGE && !(param == param)) return fail(GCDF_EINVAL, "hinge margin is NaN");
+  if (N == 0) return GCDF_OK;
+  if (!cost || !aligned16(cost) || !grad || !aligned16(grad))
+    return fail(GCDF_EINVAL, "cost / grad NULL or not 16-byte aligned");
+  if (argmin && !aligned16(argmin)) return fail(GCDF_EINVAL, "argmin not 16-byte aligned");
+  w.mode = reduction;
+  w.param = param;
+
+  // scratch layout: first-layer waypoint term, sin/cos, tile prefix (point
+  // lists only), per-tile partial records; each part 256-byte aligned
+  const size_t b_A = round256((size_t)N * net->H * sizeof(float));
+  const size_t b_trig = round256((size_t)N * 2 * w.n_ang * sizeof(float));
+  const size_t b_ts = part_offsets ? round256((size_t)(N + 1) * sizeof(int)) : 0;
+  const size_t b_part = round256((size_t)(w.n_tiles > 0 ? w.n_tiles : 1) * sizeof(Partial));
+  const size_t need = b_A + b_trig + b_ts + b_part;
+  if (need > kNoAllocScratchBytes)
+    return fail(GCDF_EINVAL,
+                "request needs %zu bytes of scratch; the allocation-free entry point has %zu "
+                "(use gcdf_collision_cost, or split the waypoints into smaller calls)",
+                need, kNoAllocScratchBytes);
+  void* scratch = nullptr;
+  if ((rc = noalloc_scratch(net->device, &scratch))) return rc;
+  unsigned char* sp = static_cast<unsigned char*>(scratch);
+  float* A = reinterpret_cast<float*>(sp);
+  float* trig = reinterpret_cast<float*>(sp + b_A);
+  int* ts = part_offsets ? reinterpret_cast<int*>(sp + b_A + b_trig) : nullptr;
+  Partial* parts = reinterpret_cast<Partial*>(sp + b_A + b_trig + b_ts);
+  w.A = A;
+  w.trig = trig;
+  w.partials = parts;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (part_offsets) {
+    if ((e = launch_tile_map(part_offsets, N, w.tile, ts, s))) return cuda_fail(e, "tile map launch");
+    w.tile_start = ts;
+  }
+  if (w.n_pairs > 0) {
+    if ((e = launch_prep(w, net->w_dev + net->off_W1, net->w_dev + net->off_b1, net->H, net->d_in, shift, A, trig,
+                         s)))
+      return cuda_fail(e, "prep launch");
+    if (net->prof_start && (e = cudaEventRecord(net->prof_start, s))) return cuda_fail(e, "cudaEventRecord");
+    if (net->precision == GCDF_FP32) {
+      Fp32Weights fw;
+      fw.BF = net->BF;
+      fw.BB = net->BB;
+      fw.bias = net->bias_p;
+      fw.W1 = net->w_dev + net->off_W1;
+      fw.wout = net->wout_p;
+      fw.bout = net->bout;
+      fw.H = net->H;
+      fw.L = net->L;
+      fw.d_in = net->d_in;
+      fw.d_q = net->d_q;
+      if ((e = launch_fp32(w, fw, net->num_sms, s))) return cuda_fail(e, "fp32 kernel launch");
+    } else {
+      if ((e = launch_tc(w, net->tcw, net->num_sms, s))) return cuda_fail(e, "tensor-core kernel launch");
+    }
+    if (net->prof_stop && (e = cudaEventRecord(net->prof_stop, s))) return cuda_fail(e, "cudaEventRecord");
+  } else if (!part_offsets) {
+    w.tiles_per_wp = 0;
+  }
+  if ((e = launch_merge(w, N, cost, grad, argmin, s))) return cuda_fail(e, "merge launch");
+  g_err[0] = 0;
+  return GCDF_OK;
+}
 
 }  // extern "C"
