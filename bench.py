@@ -47,6 +47,24 @@ def flops_per_pair(shape: synth.NetShape) -> int:
     return fwd + rev
 
 
+def measured_traffic(precision: str, workload: str):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    or None when that summary is for another workload or the kernel source has
+    changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh).get(precision)
+    if not rec or not workload.startswith(rec["workload"]):
+        return None
+    with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
+        if hashlib.sha1(fh.read()).hexdigest() != rec["sha1"]:
+            return None
+    return rec["dram_bytes_per_launch"]
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -323,7 +341,9 @@ def run_gpu(args):
                    "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": bound, "achieved": achieved_tflops, "peak": peak, "unit": punit,
-                     "frac": achieved_tflops / peak, "traffic": args.traffic, "peak_source": peak_note,
+                     "frac": achieved_tflops / peak,
+                     "traffic": args.traffic if args.traffic is not None else measured_traffic(args.precision, wl.name),
+                     "peak_source": peak_note,
                      "kernel_ms": 1e3 * kern_avg_s, "flops_per_pair": fpp},
         "cpu_baseline": cb,
         "e2e": {"value": world * P * args.steps / e2e_s, "unit": "pairs/s",
