@@ -47,6 +47,21 @@ def flops_per_pair(shape: synth.NetShape) -> int:
     return fwd + rev
 
 
+def job_throughput(local_seconds: float, units_per_rank: float, dist=None, device=None):
+    """Whole-job rate for replicas that each process `units_per_rank` units:
+    the slowest rank's time (maximum over ranks) bounds the job.  Returns
+    (max_seconds, units_per_second over all ranks)."""
+    world = 1
+    t = local_seconds
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        buf = torch.tensor([local_seconds], dtype=torch.float64, device=device)
+        dist.all_reduce(buf, op=dist.ReduceOp.MAX)
+        t = float(buf.item())
+    return t, world * units_per_rank / t
+
+
 def measured_traffic(precision: str, workload: str):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
     or None when that summary is for another workload or the kernel source has
@@ -269,11 +284,8 @@ def run_gpu(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(s_start, s_stop)]
     kern_ms = [a.elapsed_time(b) for a, b in zip(k_start, k_stop)]
-    total_s = sum(step_ms) / 1e3
+    total_s, value = job_throughput(sum(step_ms) / 1e3, P * args.steps, dist, dev)
     if dist:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
         dist.barrier()
 
     # end to end through the public API with host buffers (pinned), copies timed
@@ -296,11 +308,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if k >= args.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_s = sum(e2e_ms) / 1e3
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s, e2e_value = job_throughput(sum(e2e_ms) / 1e3, P * args.steps, dist, dev)
 
     if rank != 0:
         dist.destroy_process_group()
@@ -318,7 +326,6 @@ def run_gpu(args):
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         bound, punit = "alu", "TFLOP/s"
         peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock (derived)"
-    value = world * P * args.steps / total_s
     cb = None
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_oracle_leg(wl, budget_s=args.ref_budget,
@@ -346,7 +353,7 @@ def run_gpu(args):
                      "peak_source": peak_note,
                      "kernel_ms": 1e3 * kern_avg_s, "flops_per_pair": fpp},
         "cpu_baseline": cb,
-        "e2e": {"value": world * P * args.steps / e2e_s, "unit": "pairs/s",
+        "e2e": {"value": e2e_value, "unit": "pairs/s",
                 "h2d_bytes_per_step": int(q_h.numel() * 4 + p_h.numel() * 4),
                 "d2h_bytes_per_step": int(c_h.numel() * 4 + g_h.numel() * 4 + a_h.numel() * 4)},
         "gpu_launches": 3 * args.steps,
