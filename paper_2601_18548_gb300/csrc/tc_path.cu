@@ -284,13 +284,15 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
   if (warp == 0) {
     // ================= TMA producer =================
     if (lane == 0 && my_tiles > 0) {
-      long long g = 0;
+      long long g = 0;         // slabs issued
+      int pst = 0;             // ring stage of slab g
+      uint32_t pph = 0;        // its use parity (g / kStages) & 1
       bool ok = true;
       auto next_stage = [&](uint32_t bytes) -> int {
-        const int st = (int)(g % kStages);
-        const uint32_t u = (uint32_t)(g / kStages);
-        if (u > 0 && !wait_role(bar(base, B_EMPTY0 + st), (u - 1) & 1u, abort_flag, tw.err)) return -1;
+        const int st = pst;
+        if (g >= kStages && !wait_role(bar(base, B_EMPTY0 + st), pph ^ 1u, abort_flag, tw.err)) return -1;
         ptx::mbar_arrive_expect_tx(bar(base, B_FULL0 + st), bytes);
+        if (++pst == kStages) { pst = 0; pph ^= 1u; }
         return st;
       };
       for (int it = 0; it < my_tiles && ok; ++it) {
@@ -322,12 +324,18 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     if (lane == 0 && my_tiles > 0) {
       const uint32_t id128 = ptx::idesc_f16kind(kTile, kHalf, kF16);
       const uint32_t idj = ptx::idesc_f16kind(kTile, nj, kF16);
-      long long g = 0;
+      long long g = 0;         // slabs consumed
+      int cst = 0;             // ring stage of slab g
+      uint32_t cph = 0;        // its use parity
       uint32_t ea = 0, eb = 0;
       bool ok = true;
+      // Shared-memory descriptors are linear in the start address (bits 0-13 hold
+      // address / 16), so every operand descriptor is a base plus a small offset.
+      const uint64_t dA[2] = {ptx::smem_desc_sw128(base + kOffA0, 1024), ptx::smem_desc_sw128(base + kOffA1, 1024)};
+      const uint64_t dRing = ptx::smem_desc_sw128(base + kOffRing, 1024);
       for (int it = 0; it < my_tiles && ok; ++it) {
         for (int s = 0; s <= n_steps && ok; ++s) {
-          const uint32_t abuf = base + (((it + s) & 1) ? kOffA1 : kOffA0);
+          const uint64_t dAbuf = dA[(it + s) & 1];
           // the input Jacobian df/denc = W_1q^T g_1 goes to TMEM columns [384, 384 + nj):
           // the stash is free by then, so the next tile's first chain need not wait for it
           const bool jstep = (s == n_steps);
@@ -343,19 +351,20 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
                 ++eb;
                 ptx::tc_fence_after();
               }
-              const int st = (int)(g % kStages);
-              if (!wait_role(bar(base, B_FULL0 + st), (uint32_t)(g / kStages) & 1u, abort_flag, tw.err)) {
+              const int st = cst;
+              if (!wait_role(bar(base, B_FULL0 + st), cph, abort_flag, tw.err)) {
                 ok = false;
                 break;
               }
               ptx::tc_fence_after();
-              const uint32_t aslab = abuf + kc * (kTile * 128);
-              const uint32_t bslab = base + kOffRing + st * kSlabBytes;
+              const uint64_t da = dAbuf + (uint64_t)(kc * (kTile * 128) >> 4);
+              const uint64_t db = dRing + (uint64_t)(st * kSlabBytes >> 4);
+              const uint32_t dtm = tmem + (jstep ? 384 : hh * kHalf);
+              const uint32_t idd = jstep ? idj : id128;
 #pragma unroll
-              for (int ks = 0; ks < 4; ++ks)
-                ptx::mma_bf16(tmem + (jstep ? 384 : hh * kHalf), ptx::smem_desc_sw128(aslab + ks * 32, 1024),
-                              ptx::smem_desc_sw128(bslab + ks * 32, 1024), jstep ? idj : id128, (kc | ks) != 0);
+              for (int ks = 0; ks < 4; ++ks) ptx::mma_bf16(dtm, da + 2 * ks, db + 2 * ks, idd, (kc | ks) != 0);
               ptx::mma_commit(bar(base, B_EMPTY0 + st));
+              if (++cst == kStages) { cst = 0; cph ^= 1u; }
             }
             if (ok) ptx::mma_commit(bar(base, B_ACC0 + hh));
           }
