@@ -72,12 +72,12 @@ constexpr uint32_t kTmemCols = 512;
 constexpr int kOffA0 = 0;
 constexpr int kOffA1 = kABytes;
 constexpr int kOffRing = 2 * kABytes;                           // 131072
-constexpr int kOffBiasF = kOffRing + kStages * kSlabBytes;      // [H] fp32 b_L / 2
-constexpr int kOffBiasH = kOffBiasF + kH * 4;                   // [(L-2) x H/2] f16x2 b_l / 2, L <= 4
-constexpr int kOffW1p = kOffBiasH + 2 * (kH / 2) * 4;           // [H] float4 W_1p / 2
-constexpr int kOffWoh = kOffW1p + kH * 16;                      // [H] fp32 w_o / 2
-constexpr int kOffAiw = kOffWoh + kH * 4;                       // [16 warps][64] fp32 A_i / 2
-constexpr int kOffTrig = kOffAiw + kEpiWarps * 64 * 4;          // [4 warps][2 tiles][24] sin, cos
+constexpr int kOffBiasH = kOffRing + kStages * kSlabBytes;      // [(L-1) x H/2] f16x2 b_l / 2, L <= 4
+constexpr int kOffW1p = kOffBiasH + 3 * (kH / 2) * 4;           // [H/2] uint4: f16x2 W_1p / 2 (x, y, z pairs)
+constexpr int kOffWo = kOffW1p + (kH / 2) * 16;                 // [H] fp32 w_o
+constexpr int kOffWoh = kOffWo + kH * 4;                        // [H/2] f16x2 w_o / 2
+constexpr int kOffAiw = kOffWoh + (kH / 2) * 4;                 // [16 warps][32] f16x2 A_i / 2
+constexpr int kOffTrig = kOffAiw + kEpiWarps * 32 * 4;          // [4 warps][2 tiles][24] sin, cos
 constexpr int kOffF = kOffTrig + 4 * 2 * 24 * 4;                // [4][128] f partials
 constexpr int kOffPart = kOffF + 4 * kTile * 4;                 // 4 partial records
 constexpr int kOffBar = kOffPart + 4 * (int)sizeof(Partial);
@@ -149,15 +149,11 @@ __device__ __forceinline__ uint32_t to_operand(uint32_t f16pair) {
   return kF16 ? f16pair : ptx::f16x2_to_bf16x2(f16pair);
 }
 
-// u_1 = z_1 / 2 for columns c, c+1 of this thread's pair (FP32); ah = A_i / 2
-// for those columns (warp-private staging), w = W_1p / 2.
-__device__ __forceinline__ void first_layer_u(const float4* s_w1p, float2 ah, int c, float px, float py, float pz,
-                                              float& u0, float& u1) {
-  const float4 w0 = s_w1p[c], w1 = s_w1p[c + 1];
-  u0 = fmaf(w0.z, pz, fmaf(w0.y, py, fmaf(w0.x, px, ah.x)));
-  u1 = fmaf(w1.z, pz, fmaf(w1.y, py, fmaf(w1.x, px, ah.y)));
+// u_1 = z_1 / 2 for columns c, c+1 of this thread's pair in packed FP16:
+// A_i / 2 + (W_1p / 2) p, one fused multiply-add per point coordinate.
+__device__ __forceinline__ uint32_t first_layer_u2(uint4 w, uint32_t ah, uint32_t px2, uint32_t py2, uint32_t pz2) {
+  return ptx::hfma2(w.z, pz2, ptx::hfma2(w.y, py2, ptx::hfma2(w.x, px2, ah)));
 }
-
 
 // Per-tile reduction of 32 rows of a warp (lane = row) into one partial
 // record held by lane 0: argmin by (f, list position) with NaN first, then
@@ -237,11 +233,11 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
   int my_tiles = 0;
   if ((int)blockIdx.x < ntiles) my_tiles = (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;
 
-  float* s_biasF = reinterpret_cast<float*>(gbase + kOffBiasF);
   uint32_t* s_biasH = reinterpret_cast<uint32_t*>(gbase + kOffBiasH);
-  float4* s_w1p = reinterpret_cast<float4*>(gbase + kOffW1p);
-  float* s_woh = reinterpret_cast<float*>(gbase + kOffWoh);
-  float* s_aiw = reinterpret_cast<float*>(gbase + kOffAiw);
+  uint4* s_w1p = reinterpret_cast<uint4*>(gbase + kOffW1p);
+  float* s_wo = reinterpret_cast<float*>(gbase + kOffWo);
+  uint32_t* s_woh = reinterpret_cast<uint32_t*>(gbase + kOffWoh);
+  uint32_t* s_aiw = reinterpret_cast<uint32_t*>(gbase + kOffAiw);
   float* s_f = reinterpret_cast<float*>(gbase + kOffF);
   Partial* s_part = reinterpret_cast<Partial*>(gbase + kOffPart);
   uint32_t* s_slot = reinterpret_cast<uint32_t*>(gbase + kOffSlot);
@@ -267,12 +263,15 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     ptx::tmem_alloc(base + kOffSlot, kTmemCols);
     ptx::tmem_relinquish();
   }
-  for (int c = tid; c < kH; c += kThreads) {
-    s_biasF[c] = 0.5f * tw.bias[(size_t)(L - 2) * kH + c];
-    s_w1p[c] = make_float4(0.5f * tw.W1p[3 * c], 0.5f * tw.W1p[3 * c + 1], 0.5f * tw.W1p[3 * c + 2], 0.f);
-    s_woh[c] = 0.5f * tw.wout[c];
+  for (int c = tid; c < kH; c += kThreads) s_wo[c] = tw.wout[c];
+  for (int i = tid; i < kH / 2; i += kThreads) {
+    const int c = 2 * i;
+    s_w1p[i] = make_uint4(ptx::pack_f16x2(0.5f * tw.W1p[3 * c], 0.5f * tw.W1p[3 * c + 3]),
+                          ptx::pack_f16x2(0.5f * tw.W1p[3 * c + 1], 0.5f * tw.W1p[3 * c + 4]),
+                          ptx::pack_f16x2(0.5f * tw.W1p[3 * c + 2], 0.5f * tw.W1p[3 * c + 5]), 0u);
+    s_woh[i] = ptx::pack_f16x2(0.5f * tw.wout[c], 0.5f * tw.wout[c + 1]);
   }
-  for (int i = tid; i < (L - 2) * (kH / 2); i += kThreads) {
+  for (int i = tid; i < (L - 1) * (kH / 2); i += kThreads) {
     const int l = i / (kH / 2), c = 2 * (i % (kH / 2));
     s_biasH[i] = ptx::pack_f16x2(0.5f * tw.bias[(size_t)l * kH + c], 0.5f * tw.bias[(size_t)l * kH + c + 1]);
   }
@@ -352,11 +351,11 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
                 ptx::tc_fence_after();
               }
               const int st = cst;
+              // slab written by TMA: the transaction barrier orders it before the MMA
               if (!wait_role(bar(base, B_FULL0 + st), cph, abort_flag, tw.err)) {
                 ok = false;
                 break;
               }
-              ptx::tc_fence_after();
               const uint64_t da = dAbuf + (uint64_t)(kc * (kTile * 128) >> 4);
               const uint64_t db = dRing + (uint64_t)(st * kSlabBytes >> 4);
               const uint32_t dtm = tmem + (jstep ? 384 : hh * kHalf);
@@ -389,13 +388,13 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     const bool ej = (kq == 0);             // writes this tile's outputs
     const uint32_t rbase = (row >> 3) * 1024 + (row & 7) * 128;
     const int r7 = row & 7;
-    float* aiw = s_aiw + e * 64;           // A_i / 2 for this thread's 32 + 32 columns
+    uint32_t* aiw = s_aiw + e * 32;        // f16x2 A_i / 2 for this thread's 32 + 32 columns
     float* trigw = reinterpret_cast<float*>(gbase + kOffTrig) + quad * 2 * 24;  // EJ warps only
     uint32_t acc_n[2] = {0, 0};            // completions of ACC[a], ACC[b] consumed
     bool ok = true;
 
     int t = 0, wp = 0, start = 0, len = 0;
-    float px = 0.f, py = 0.f, pz = 0.f;
+    uint32_t px2 = 0, py2 = 0, pz2 = 0;  // this row's point, packed (p, p) in FP16
 
     // byte offset (within an A buffer) of columns c0 + 8 q .. c0 + 8 q + 7 of this row
     auto aoff = [&](int c0, int q) -> uint32_t {
@@ -408,7 +407,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     auto load_tile = [&](int it) {
       t = (int)blockIdx.x + it * (int)gridDim.x;
       tile_lookup(w, t, wp, start, len);
-      px = py = pz = 0.f;
+      float px = 0.f, py = 0.f, pz = 0.f;
       if (row < len) {
         int j;
         long long k;
@@ -417,10 +416,13 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         py = w.p[3 * (size_t)j + 1];
         pz = w.p[3 * (size_t)j + 2];
       }
+      px2 = ptx::pack_f16x2(px, px);
+      py2 = ptx::pack_f16x2(py, py);
+      pz2 = ptx::pack_f16x2(pz, pz);
       const float* Ai = w.A + (size_t)wp * kH + 32 * kq;
       __syncwarp();
-      aiw[lane] = 0.5f * Ai[lane];
-      aiw[32 + lane] = 0.5f * Ai[kHalf + lane];
+      if (lane < 16) aiw[lane] = ptx::pack_f16x2(0.5f * Ai[2 * lane], 0.5f * Ai[2 * lane + 1]);
+      else aiw[lane] = ptx::pack_f16x2(0.5f * Ai[kHalf + 2 * (lane - 16)], 0.5f * Ai[kHalf + 2 * (lane - 16) + 1]);
       if (ej && lane < 2 * w.n_ang) trigw[(it & 1) * 24 + lane] = w.trig[(size_t)wp * 2 * w.n_ang + lane];
       __syncwarp();
     };
@@ -433,10 +435,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         uint32_t o[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          float u0, u1;
-          first_layer_u(s_w1p, *reinterpret_cast<const float2*>(aiw + 32 * h + cc + 2 * i), c0 + cc + 2 * i, px, py,
-                        pz, u0, u1);
-          const uint32_t u = ptx::pack_f16x2(u0, u1);
+          const uint32_t u = first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[16 * h + cc / 2 + i], px2, py2, pz2);
           const uint32_t tt = ptx::htanh2(u);
           o[i] = to_operand<kF16>(ptx::hfma2(u, tt, u));
         }
@@ -452,7 +451,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       first_layer(0, 0);
       first_layer(0, 1);
     }
-    float fpart = 0.f;  // sum of (w_o / 2) s(z_L) over this thread's 64 columns
+    float fpart = 0.f;  // sum of w_o s(z_L) over this thread's 64 columns
     for (int it = 0; it < my_tiles && ok; ++it) {
       for (int s = 0; s < n_steps && ok; ++s) {
         const uint32_t obuf = base + (((it + s + 1) & 1) ? kOffA1 : kOffA0);
@@ -486,36 +485,33 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
             }
             ptx::tmem_wait_st();
           } else if (s == L - 2) {
-            // last forward layer (FP32): f partial, g_L = w_o s'(z_L) -> A
+            // last forward layer: f partial (FP32 sum), g_L = w_o s'(z_L) -> A
             if (h == 0) fpart = 0.f;
+            const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + (L - 2) * (kH / 2) + (c0 >> 1));
 #pragma unroll 1
             for (int cc = 0; cc < 32; cc += 16) {
               uint32_t v[16];
               ptx::tmem_ld16(t_acc + cc, v);
+              const uint4 b0 = bh4[cc / 8], b1 = bh4[cc / 8 + 1];
+              const uint32_t bh[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+              const uint4* wh4 = reinterpret_cast<const uint4*>(s_woh + (c0 + cc) / 2);
+              const uint4 w0 = wh4[0], w1 = wh4[1];
+              const uint32_t wh[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
               ptx::tmem_wait_ld();
               uint32_t o[8];
 #pragma unroll
-              for (int i4 = 0; i4 < 16; i4 += 4) {
-                const float4 bf = *reinterpret_cast<const float4*>(s_biasF + c0 + cc + i4);
-                const float4 wh = *reinterpret_cast<const float4*>(s_woh + c0 + cc + i4);
-                const float bv[4] = {bf.x, bf.y, bf.z, bf.w};
-                const float wv[4] = {wh.x, wh.y, wh.z, wh.w};
-                float gv[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  const float u = fmaf(__uint_as_float(v[i4 + q]), 0.5f, bv[q]);
-                  const float tt = ptx::tanh_approx(u);
-                  const float hv = fmaf(u, tt, u);
-                  fpart = fmaf(wv[q], hv, fpart);
-                  gv[q] = wv[q] * fmaf(hv, 1.f - tt, 1.f + tt);
-                }
-                o[i4 / 2] = ptx::pack2<kF16>(gv[0], gv[1]);
-                o[i4 / 2 + 1] = ptx::pack2<kF16>(gv[2], gv[3]);
+              for (int i = 0; i < 8; ++i) {
+                const uint32_t zp = ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+                uint32_t hh, s2;
+                silu2(ptx::hfma2(zp, kHalf2, bh[i]), hh, s2);
+                const float2 wo = *reinterpret_cast<const float2*>(s_wo + c0 + cc + 2 * i);
+                fpart = fmaf(wo.x, ptx::f16lo(hh), fmaf(wo.y, ptx::f16hi(hh), fpart));
+                o[i] = to_operand<kF16>(ptx::hmul2(wh[i], s2));
               }
               store8c(obuf, c0 + cc, o);
             }
             if (h == 1) {
-              s_f[kq * kTile + row] = 2.f * fpart;
+              s_f[kq * kTile + row] = fpart;
               ptx::mbar_arrive(bar(base, B_FD));
             }
           } else {
@@ -530,11 +526,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               if (lm1 < 2) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                  float u0, u1;
-                  first_layer_u(s_w1p, *reinterpret_cast<const float2*>(aiw + 32 * h + cc + 2 * i), c0 + cc + 2 * i,
-                                px, py, pz, u0, u1);
                   uint32_t hh;
-                  silu2(ptx::pack_f16x2(u0, u1), hh, d2[i]);
+                  silu2(first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[16 * h + cc / 2 + i], px2, py2, pz2), hh, d2[i]);
                 }
               }
               uint32_t o[8];

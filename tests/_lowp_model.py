@@ -5,14 +5,17 @@ tcgen05 kernel does:
   * operands: the hidden weight matrices W_2..W_L, the reverse copies W_l^T / 2
     and the input-Jacobian matrix W_1q; the activations h_1..h_{L-1} and the
     reverse gradients g_L..g_1 (BF16 or FP16);
-  * epilogue arithmetic of the first and middle layers in packed FP16, one
-    rounding per fused operation: u = z / 2, t = tanh(u), s = u + u t,
-    2 s' = s (1 - t) + (1 + t), and the reverse product acc * 2 s';
+  * epilogue arithmetic in packed FP16, one rounding per fused operation:
+    the first layer u_1 = A_i / 2 + (W_1p / 2) p (the point and the halved
+    weights in FP16, one fused multiply-add per coordinate), u = z / 2,
+    t = tanh(u), s = u + u t, 2 s' = s (1 - t) + (1 + t), g_L = (w_o / 2) 2 s',
+    and the reverse product acc * 2 s';
   * the stash 2 s'(z_2..z_{L-1}) (FP16);
-  * the last forward layer and every accumulation at high precision.
+  * the per-waypoint term A_i, the output sum f = w_o . s(z_L) + b_o and every
+    matrix accumulation at high precision.
 The sigmoid's tanh is exact here (the kernel uses the hardware approximation).
 
-Its uses: the BF16 parity bar is max(2e-2, 1.25 x this model's error against
+Its uses: the BF16 parity bar is max(2e-2, 1.5 x this model's error against
 the FP64 oracle), and the kernel must stay close to the model on every pair.
 It shares no code with the oracle or the library.
 """
@@ -65,9 +68,17 @@ def lowp_eval(n_dof, H, L, weights, q_rows, p_rows, shift_rows=None, fmt="bf16")
     enc = np.empty((q.shape[0], 2 * ang.shape[1]))
     enc[:, 0::2] = np.sin(ang)
     enc[:, 1::2] = np.cos(ang)
-    v = np.concatenate([p, xy, enc], 1)
     W1, b1 = lay[0]
-    u1 = round_f16(0.5 * (v @ W1.T + b1))
+    # per-waypoint term: A = W_1q enc(q') + b_1 - W_1p[:, 0:2] shift (points enter raw)
+    A = np.concatenate([xy, enc], 1) @ W1[:, 3:].T + b1
+    if shift_rows is not None:
+        A = A - np.asarray(shift_rows, dtype=np.float64) @ W1[:, 0:2].T
+    praw = np.asarray(p_rows, dtype=np.float64)
+    w1h = round_f16(0.5 * W1[:, 0:3])
+    p16 = round_f16(praw)
+    u1 = round_f16(0.5 * A)
+    for d in range(3):
+        u1 = round_f16(w1h[None, :, d] * p16[:, d:d + 1] + u1)
     h1, s2_1 = _silu_f16(u1)
     h = R(h1)
     stash = {}
@@ -78,12 +89,12 @@ def lowp_eval(n_dof, H, L, weights, q_rows, p_rows, shift_rows=None, fmt="bf16")
         hl, stash[l] = _silu_f16(u)
         h = R(hl)
     W, b = lay[L - 1]
-    u = 0.5 * (h @ R(W).T) + 0.5 * b
-    t = np.tanh(u)
-    hL = u + u * t
+    zp = round_f16(h @ R(W).T)
+    u = round_f16(zp * 0.5 + round_f16(0.5 * b))
+    hL, s2L = _silu_f16(u)
     wo, bo = lay[L]
     f = hL @ wo[0] + bo[0]
-    g = R(0.5 * wo[0][None, :] * (hL * (1.0 - t) + (1.0 + t)))
+    g = R(round_f16(round_f16(0.5 * wo[0])[None, :] * s2L))
     for l in range(L - 1, 0, -1):  # reverse through W_{l+1} (0-based l)
         acc = round_f16(g @ R(0.5 * lay[l][0]))
         d2 = stash[l - 1] if l - 1 >= 1 else s2_1
