@@ -9,44 +9,56 @@
 // followed by the sin/cos chain rule and either per-pair outputs or a
 // per-tile partial of the min / soft-min / hinge reduction.
 //
-// Mapping onto the SM.  A tile is 128 pairs of one waypoint (the MMA's M).
+// Mapping onto the GPU.  CTAs run in clusters of two, one CTA per SM; each
+// CTA owns a tile of 128 pairs of one waypoint and the pair's MMAs are 2-SM
+// tcgen05 MMAs (cta_group::2, M = 256) issued by the even CTA: each CTA holds
+// the A operand of its own 128 rows and half of every weight slab, so every
+// SM receives half the weight bytes (weight streaming from L2 is what bounds a
+// CTA that reloads the whole network for each tile).
+//
 // Each H x H product of the forward pass and of the reverse sweep ("a step")
 // is two MMA chains of N = 128 output columns ("halves" a and b), each
-// D (TMEM, FP32) = A (shared, 16-bit, 128 pairs x 256) x B (shared, 16-bit
-// weight slabs of 128 rows x 64).  The A operand is double buffered: step s
+// D (TMEM, FP32) = A (shared, 16-bit, 128 pairs x 256 per CTA) x B (shared,
+// 16-bit weight rows, 64 per CTA).  The A operand is double buffered: step s
 // reads buffer (tile + s) mod 2 and its epilogue writes the other, so the
 // epilogue of half a runs while the tensor core computes half b, and the
 // epilogue of half b runs while the next step's half a consumes its first 128
 // input columns (written by half a's epilogue).  Weights stream through a ring
-// of 16 KB slabs loaded by TMA; the reverse operands are stored copies of
+// of 16 KB stages (K = 128 of one chain) loaded by TMA; both CTAs' loads of a
+// stage complete on one barrier of the even CTA, and the even CTA's commit
+// releases the stage in both.  The reverse operands are stored copies of
 // W_l^T scaled by 1/2 (exact), so both directions are K-major.
 //
-// Epilogue arithmetic (packed FP16 pairs for layers 2..L-1):
+// Epilogue arithmetic (packed FP16 pairs):
 //   u = z / 2 = acc / 2 + b / 2,  t = tanh(u),  s(z) = z sigma(z) = u (1 + t),
 //   2 s'(z) = (1 + t) + s(z) (1 - t)
 // 2 s'(z_l) of layers 2..L-1 stays in TMEM as FP16 pairs; the halved reverse
 // operands cancel the factor 2.  s'(z_1) is recomputed from A_i + W_1p p_j.
-// The last forward layer (f and g_L) uses FP32 arithmetic.
+// The output sum f = w_o . s(z_L) accumulates in FP32.
 //
-// TMEM columns (512 allocated): [0, 128) accumulator half a, [128, 256) half b,
-// [256 + 128 s, 384 + 128 s) FP16-pair stash of layer s + 2, s = 0..L-3;
-// the input-Jacobian chain writes [384, 384 + nj) after the stash is consumed
-// (the next tile refills those columns only after its outputs are read).
+// TMEM columns (512, allocated for the CTA pair): [0, 128) accumulator half a,
+// [128, 256) half b, [256 + 128 s, 384 + 128 s) FP16-pair stash of layer
+// s + 2, s = 0..L-3; the input-Jacobian chain (N = 32) writes [384, 416) after
+// the stash is consumed (the next tile refills those columns only after its
+// outputs are read).
 //
 // Tile boundary: as soon as the last reverse chain has finished reading its
 // A buffer, each group writes the next tile's first layer into it, so the
 // next tile's chains start while this tile's outputs (chain rule, reduction)
 // are still being produced.
 //
-// Warp roles (576 threads): warp 0 issues TMA loads, warp 1 allocates TMEM
-// and issues MMAs, warps 2..17 are the epilogue: all 16 process each half in
-// turn; thread = one pair row (TMEM lane) and 32 columns of each half.  The
-// input-Jacobian operand W_1q^T streams through the same ring as the weights.
+// Warp roles (576 threads per CTA): warp 0 issues TMA loads, warp 1 allocates
+// TMEM and (even CTA) issues the pair's MMAs, warps 2..17 are the epilogue:
+// all 16 process each half in turn; thread = one pair row (TMEM lane) and 32
+// columns of each half; each warp signals the end of a half to the MMA issuer
+// with one arrival.  The input-Jacobian operand W_1q^T streams through the
+// same ring as the weights.
 //
-// Every cross-warp handoff is an mbarrier and every wait on one is bounded
-// (about a second).  On expiry the kernel records an error in a device status
-// word, stops issuing work, drains its outstanding copies and MMAs and frees
-// TMEM before returning; no named barrier can strand a warp.
+// Every cross-warp and cross-CTA handoff is an mbarrier and every wait on one
+// is bounded (about a second).  On expiry the kernel records an error in a
+// device status word, stops issuing work, drains its outstanding copies and
+// MMAs and frees TMEM before returning; both CTAs of a pair always reach the
+// closing cluster barrier.
 #include <cstring>
 #include <vector>
 
@@ -57,11 +69,13 @@ namespace gcdf {
 
 namespace {
 
-constexpr int kTile = 128;             // pairs per tile (MMA M)
+constexpr int kTile = 128;             // pairs per CTA tile; a CTA pair shares each MMA (M = 256)
 constexpr int kH = 256;                // hidden width handled by this kernel
 constexpr int kHalf = 128;             // output columns per MMA chain
+constexpr int kRowsCta = kHalf / 2;    // weight rows of a chain held by each CTA of the pair
 constexpr int kStages = 5;             // weight ring depth
-constexpr int kSlabBytes = kHalf * 128;  // 128 rows x 64 16-bit values
+constexpr int kSlabBytes = kRowsCta * 128;  // 64 rows x 64 16-bit values (one K = 64 slab)
+constexpr int kStageBytes = 2 * kSlabBytes; // K = 128 of one chain per stage
 constexpr int kABytes = kTile * kH * 2;
 constexpr int kThreads = 576;
 constexpr int kEpiThreads = 512;       // epilogue threads (16 warps)
@@ -72,7 +86,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr int kOffA0 = 0;
 constexpr int kOffA1 = kABytes;
 constexpr int kOffRing = 2 * kABytes;                           // 131072
-constexpr int kOffBiasH = kOffRing + kStages * kSlabBytes;      // [(L-1) x H/2] f16x2 b_l / 2, L <= 4
+constexpr int kOffBiasH = kOffRing + kStages * kStageBytes;      // [(L-1) x H/2] f16x2 b_l / 2, L <= 4
 constexpr int kOffW1p = kOffBiasH + 3 * (kH / 2) * 4;           // [H/2] uint4: f16x2 W_1p / 2 (x, y, z pairs)
 constexpr int kOffWo = kOffW1p + (kH / 2) * 16;                 // [H] fp32 w_o
 constexpr int kOffWoh = kOffWo + kH * 4;                        // [H/2] f16x2 w_o / 2
@@ -87,10 +101,10 @@ constexpr int kSmemBytes = kOffSlot + 16 + 1024;                // + alignment s
 static_assert(kSmemBytes <= 227 * 1024 - 64, "shared memory budget");
 
 // barrier indices
-constexpr int B_FULL0 = 0;              // + stage
-constexpr int B_EMPTY0 = kStages;       // + stage
-constexpr int B_ACC0 = 2 * kStages;     // + half: accumulator half complete (tcgen05.commit)
-constexpr int B_ED0 = 2 * kStages + 2;  // + half: epilogue of that half done (512 arrivals)
+constexpr int B_FULL0 = 0;              // + stage: both CTAs' slabs landed (used in the even CTA)
+constexpr int B_EMPTY0 = kStages;       // + stage: its MMAs completed (commit to both CTAs)
+constexpr int B_ACC0 = 2 * kStages;     // + half: accumulator half complete (commit to both CTAs)
+constexpr int B_ED0 = 2 * kStages + 2;  // + half: epilogues of both CTAs done (even CTA, 32 warp arrivals)
 constexpr int B_FD = 2 * kStages + 4;   // f partials written (512 arrivals)
 constexpr int B_PD = 2 * kStages + 5;   // per-warp partial records written (4 arrivals)
 
@@ -130,6 +144,13 @@ __device__ __forceinline__ bool wait_epi(uint32_t b, uint32_t parity, volatile i
   }
 }
 
+// wait_epi by every lane of a warp, with one decision for the whole warp (the
+// epilogue synchronises its warps, so no lane may leave a loop alone)
+__device__ __forceinline__ bool wait_epi_warp(uint32_t b, uint32_t parity, volatile int* abort_flag, int* err) {
+  const bool got = wait_epi(b, parity, abort_flag, err);
+  return __all_sync(0xffffffffu, got);
+}
+
 __device__ __forceinline__ int total_tiles(const WorkDesc& w) {
   return w.tile_start ? w.tile_start[w.N] : w.n_tiles;
 }
@@ -155,62 +176,90 @@ __device__ __forceinline__ uint32_t first_layer_u2(uint4 w, uint32_t ah, uint32_
   return ptx::hfma2(w.z, pz2, ptx::hfma2(w.y, py2, ptx::hfma2(w.x, px2, ah)));
 }
 
-// Per-tile reduction of 32 rows of a warp (lane = row) into one partial
-// record held by lane 0: argmin by (f, list position) with NaN first, then
-// the mode's sums.  SOFTMIN takes one exponential per row relative to the
-// warp minimum.
-__device__ __forceinline__ Partial warp_tile_partial(int mode, float param, bool valid, float f, const float* dq,
-                                                     int n, int idx, int pos) {
-  float fm = valid ? f : __int_as_float(0x7f800000);
-  int pm = valid ? pos : 0x7fffffff;
-  int im = valid ? idx : -1;
-  int src = threadIdx.x & 31;
-#pragma unroll
-  for (int m = 16; m >= 1; m >>= 1) {
-    const float fo = __shfl_xor_sync(0xffffffffu, fm, m);
-    const int po = __shfl_xor_sync(0xffffffffu, pm, m);
-    const int io = __shfl_xor_sync(0xffffffffu, im, m);
-    const int so = __shfl_xor_sync(0xffffffffu, src, m);
-    if (first_is_better(fo, po, fm, pm)) { fm = fo; pm = po; im = io; src = so; }
+// Minimum over the 32 lanes of a warp (no NaN among the inputs).
+__device__ __forceinline__ float warp_min(float x) {
+  float r;
+  asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Per-tile reduction of the 32 rows of a warp (lane = row; the list position
+// grows with the lane) into the partial record *out in shared memory, written
+// by the lanes of the warp (the caller synchronises the warp afterwards).
+// Argmin by (f, list position) with NaN first: a NaN ballot, else the warp
+// minimum and the lowest lane that holds it.  The sums of the mode (SOFTMIN:
+// one exponential per row relative to the warp minimum) are reduce-scattered:
+// after the exchanges lanes 2k and 2k + 1 hold the total of value k.
+__device__ __forceinline__ void warp_tile_partial(int mode, float param, bool valid, float f, const float* dq,
+                                                  int n, int idx, int pos, Partial* out) {
+  const int lane = threadIdx.x & 31;
+  float* rec = reinterpret_cast<float*>(out);  // v0, v1, idx, pos, g[kMaxDof]
+  const unsigned nanm = __ballot_sync(0xffffffffu, valid && f != f);
+  float fm;
+  unsigned win;
+  if (nanm) {
+    win = nanm;
+    fm = __int_as_float(0x7fc00000);
+  } else {
+    const float fv = valid ? f : __int_as_float(0x7f800000);
+    fm = warp_min(fv);
+    win = __ballot_sync(0xffffffffu, valid && fv == fm);
   }
-  Partial r = partial_identity(mode);
-  if (pm == 0x7fffffff) return r;  // no valid row
-  r.idx = im;
-  r.pos = pm;
-  float wgt, v0;
+  if (win == 0u) {  // no valid row
+    if (lane == 0) *out = partial_identity(mode);
+    return;
+  }
+  const int src = __ffs(win) - 1;
   if (mode == kMin) {
-    r.v0 = fm;
+    if (lane == src) {
+      rec[0] = f;
+      rec[1] = 0.f;
+      reinterpret_cast<int*>(rec)[2] = idx;
+      reinterpret_cast<int*>(rec)[3] = pos;
 #pragma unroll
-    for (int d = 0; d < kMaxDof; ++d) r.g[d] = __shfl_sync(0xffffffffu, dq[d], src);
-    return r;
+      for (int d = 0; d < kMaxDof; ++d) rec[4 + d] = dq[d];
+    }
+    return;
   }
+  float wgt, v0;
   if (mode == kSoftmin) {
     wgt = valid ? __expf(-(f - fm) / param) : 0.f;
     if (valid && f != f) wgt = f;
-    v0 = fm;
+    v0 = 0.f;
   } else {
     wgt = (valid && f < param) ? -1.f : 0.f;
     v0 = valid ? fmaxf(0.f, param - f) : 0.f;
     if (valid && f != f) v0 = f;
   }
-  float acc[kMaxDof + 1];
-  acc[kMaxDof] = (mode == kSoftmin) ? wgt : v0;
+  float v[16];
 #pragma unroll
-  for (int d = 0; d < kMaxDof; ++d) acc[d] = (d < n) ? wgt * dq[d] : 0.f;
+  for (int d = 0; d < kMaxDof; ++d) v[d] = (d < n) ? wgt * dq[d] : 0.f;
+  v[kMaxDof] = (mode == kSoftmin) ? wgt : v0;
 #pragma unroll
-  for (int m = 16; m >= 1; m >>= 1)
+  for (int d = kMaxDof + 1; d < 16; ++d) v[d] = 0.f;
+  // reduce-scatter: at the exchange with lane ^ m each lane keeps the half of its
+  // values selected by that lane bit and adds the partner's copy of it
 #pragma unroll
-    for (int d = 0; d <= kMaxDof; ++d) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], m);
-  if (mode == kSoftmin) {
-    r.v0 = fm;
-    r.v1 = acc[kMaxDof];
-  } else {
-    r.v0 = acc[kMaxDof];
-    r.v1 = fm;
+  for (int m = 16, nv = 8; m >= 2; m >>= 1, nv >>= 1) {
+    const bool up = (lane & m) != 0;
+#pragma unroll
+    for (int i = 0; i < nv; ++i) {
+      const float keep = up ? v[i + nv] : v[i];
+      const float send = up ? v[i] : v[i + nv];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
   }
-#pragma unroll
-  for (int d = 0; d < kMaxDof; ++d) r.g[d] = acc[d];
-  return r;
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  const int k = lane >> 1;  // value held by this lane
+  if ((lane & 1) == 0) {
+    if (k < kMaxDof) rec[4 + k] = v[0];
+    else if (k == kMaxDof) rec[mode == kSoftmin ? 1 : 0] = v[0];
+  }
+  if (lane == src) {
+    rec[mode == kSoftmin ? 0 : 1] = fm;
+    reinterpret_cast<int*>(rec)[2] = idx;
+    reinterpret_cast<int*>(rec)[3] = pos;
+  }
 }
 
 template <bool kF16>
@@ -230,8 +279,15 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
   const int n_steps = 2 * (L - 1);  // weight steps per tile (forward then reverse)
   const int nj = tw.nj;
   const int ntiles = total_tiles(w);
-  int my_tiles = 0;
-  if ((int)blockIdx.x < ntiles) my_tiles = (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;
+  // CTA pairs (clusters of 2) take pair tiles round robin; CTA `rank` of the pair
+  // owns tile 2 k + rank of pair tile k (past the last tile: an empty tile)
+  const uint32_t rank = ptx::cluster_ctarank();
+  const bool leader = (rank == 0);
+  const int cluster = (int)blockIdx.x >> 1;
+  const int nclusters = (int)gridDim.x >> 1;
+  const int npt = (ntiles + 1) >> 1;
+  int my_tiles = 0;  // pair tiles of this cluster (the same for both CTAs)
+  if (cluster < npt) my_tiles = (npt - 1 - cluster) / nclusters + 1;
 
   uint32_t* s_biasH = reinterpret_cast<uint32_t*>(gbase + kOffBiasH);
   uint4* s_w1p = reinterpret_cast<uint4*>(gbase + kOffW1p);
@@ -251,8 +307,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     }
     ptx::mbar_init(bar(base, B_ACC0 + 0), 1);
     ptx::mbar_init(bar(base, B_ACC0 + 1), 1);
-    ptx::mbar_init(bar(base, B_ED0 + 0), kEpiThreads);
-    ptx::mbar_init(bar(base, B_ED0 + 1), kEpiThreads);
+    ptx::mbar_init(bar(base, B_ED0 + 0), 2 * kEpiWarps);
+    ptx::mbar_init(bar(base, B_ED0 + 1), 2 * kEpiWarps);
     ptx::mbar_init(bar(base, B_FD), kEpiThreads);
     ptx::mbar_init(bar(base, B_PD), 4);
     ptx::fence_barrier_init();
@@ -260,8 +316,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     ptx::prefetch_tensormap(&map_j);
   }
   if (warp == 1) {
-    ptx::tmem_alloc(base + kOffSlot, kTmemCols);
-    ptx::tmem_relinquish();
+    ptx::tmem_alloc_pair(base + kOffSlot, kTmemCols);
+    ptx::tmem_relinquish_pair();
   }
   for (int c = tid; c < kH; c += kThreads) s_wo[c] = tw.wout[c];
   for (int i = tid; i < kH / 2; i += kThreads) {
@@ -275,97 +331,109 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     const int l = i / (kH / 2), c = 2 * (i % (kH / 2));
     s_biasH[i] = ptx::pack_f16x2(0.5f * tw.bias[(size_t)l * kH + c], 0.5f * tw.bias[(size_t)l * kH + c + 1]);
   }
+  // both CTAs' barriers are initialised before either signals the other's
   ptx::tc_fence_before();
-  __syncthreads();
+  ptx::cluster_sync();
   ptx::tc_fence_after();
   const uint32_t tmem = *s_slot;
 
   if (warp == 0) {
-    // ================= TMA producer =================
+    // ================= TMA producer (both CTAs) =================
+    // Stage g mod kStages holds K = 128 of one chain: this CTA's kRowsCta weight
+    // rows (two 64-wide slabs).  Both CTAs' loads complete on the even CTA's
+    // FULL barrier; each CTA refills a stage once the MMAs that read it have
+    // completed (the even CTA's commit arrives on both CTAs' EMPTY barriers).
     if (lane == 0 && my_tiles > 0) {
-      long long g = 0;         // slabs issued
-      int pst = 0;             // ring stage of slab g
-      uint32_t pph = 0;        // its use parity (g / kStages) & 1
+      const uint32_t full_lead = ptx::mapa_shared(bar(base, B_FULL0), 0);
+      long long g = 0;         // stages issued
+      int pst = 0;             // ring stage of g
+      uint32_t puse = 0;       // (g / kStages) & 1
       bool ok = true;
-      auto next_stage = [&](uint32_t bytes) -> int {
+      auto load_stage = [&](const CUtensorMap* map, int x0, int y, uint32_t slab_bytes) -> bool {
         const int st = pst;
-        if (g >= kStages && !wait_role(bar(base, B_EMPTY0 + st), pph ^ 1u, abort_flag, tw.err)) return -1;
-        ptx::mbar_arrive_expect_tx(bar(base, B_FULL0 + st), bytes);
-        if (++pst == kStages) { pst = 0; pph ^= 1u; }
-        return st;
+        if (g >= kStages && !wait_role(bar(base, B_EMPTY0 + st), puse ^ 1u, abort_flag, tw.err)) return false;
+        const uint32_t fb = full_lead + 8u * (uint32_t)st;
+        if (leader) ptx::mbar_arrive_expect_tx(bar(base, B_FULL0 + st), 4u * slab_bytes);  // 2 slabs x 2 CTAs
+        ptx::tma_load_2d_pair(base + kOffRing + st * kStageBytes, map, x0, y, fb);
+        ptx::tma_load_2d_pair(base + kOffRing + st * kStageBytes + kSlabBytes, map, x0 + 64, y, fb);
+        ++g;
+        if (++pst == kStages) { pst = 0; puse ^= 1u; }
+        return true;
       };
       for (int it = 0; it < my_tiles && ok; ++it) {
         for (int s = 0; s < n_steps && ok; ++s) {
           const int row0 = (s < L - 1) ? s * kH : (L - 1 + (2 * L - 3 - s)) * kH;
           for (int hh = 0; hh < 2 && ok; ++hh)
-            for (int kc = 0; kc < 4; ++kc, ++g) {
-              const int st = next_stage(kSlabBytes);
-              if (st < 0) { ok = false; break; }
-              ptx::tma_load_2d(base + kOffRing + st * kSlabBytes, &map_w, kc * 64, row0 + hh * kHalf,
-                               bar(base, B_FULL0 + st));
-            }
+            for (int pr = 0; pr < 2 && ok; ++pr)
+              ok = load_stage(&map_w, pr * 128, row0 + hh * kHalf + (int)rank * kRowsCta, kSlabBytes);
         }
-        for (int kc = 0; kc < 4 && ok; ++kc, ++g) {  // W_1q^T, nj rows
-          const int st = next_stage((uint32_t)nj * 128u);
-          if (st < 0) { ok = false; break; }
-          ptx::tma_load_2d(base + kOffRing + st * kSlabBytes, &map_j, kc * 64, 0, bar(base, B_FULL0 + st));
-        }
+        for (int pr = 0; pr < 2 && ok; ++pr)  // W_1q^T: nj rows, nj / 2 per CTA
+          ok = load_stage(&map_j, pr * 128, (int)rank * (nj / 2), (uint32_t)(nj / 2) * 128u);
       }
-      // drain: every issued load lands before the CTA exits
-      for (long long k = (g > kStages ? g - kStages : 0); k < g; ++k) {
-        const long long t0 = clock64();
-        while (!ptx::mbar_try_wait(bar(base, B_FULL0 + (int)(k % kStages)), (uint32_t)(k / kStages) & 1u))
-          if (clock64() - t0 > kWaitCycles) { atomicOr(tw.err, 2); break; }
+      // drain (even CTA): the last kStages stages are the only ones that can be
+      // in flight; their FULL phases cover both CTAs' loads
+      if (leader) {
+        for (long long k = (g > kStages ? g - kStages : 0); k < g; ++k) {
+          const long long t0 = clock64();
+          while (!ptx::mbar_try_wait(bar(base, B_FULL0 + (int)(k % kStages)), (uint32_t)(k / kStages) & 1u))
+            if (clock64() - t0 > kWaitCycles) { atomicOr(tw.err, 2); break; }
+        }
       }
     }
   } else if (warp == 1) {
-    // ================= MMA issuer =================
-    if (lane == 0 && my_tiles > 0) {
-      const uint32_t id128 = ptx::idesc_f16kind(kTile, kHalf, kF16);
-      const uint32_t idj = ptx::idesc_f16kind(kTile, nj, kF16);
-      long long g = 0;         // slabs consumed
-      int cst = 0;             // ring stage of slab g
-      uint32_t cph = 0;        // its use parity
+    // ================= MMA issuer (even CTA, for both) =================
+    if (lane == 0 && my_tiles > 0 && leader) {
+      const uint32_t id128 = ptx::idesc_f16kind(2 * kTile, kHalf, kF16);
+      const uint32_t idj = ptx::idesc_f16kind(2 * kTile, nj, kF16);
+      long long g = 0;         // stages consumed
+      int cst = 0;             // ring stage of g
+      uint32_t cph = 0;        // its FULL phase parity
       uint32_t ea = 0, eb = 0;
       bool ok = true;
       // Shared-memory descriptors are linear in the start address (bits 0-13 hold
-      // address / 16), so every operand descriptor is a base plus a small offset.
+      // address / 16), so every operand descriptor is a base plus a small offset;
+      // the same offsets address the peer CTA's operands.
       const uint64_t dA[2] = {ptx::smem_desc_sw128(base + kOffA0, 1024), ptx::smem_desc_sw128(base + kOffA1, 1024)};
       const uint64_t dRing = ptx::smem_desc_sw128(base + kOffRing, 1024);
+      // one stage: K = 128 of a chain (8 MMAs of K = 16), then release the stage in both CTAs
+      auto stage_mmas = [&](uint32_t dtm, uint64_t da, uint32_t idd, bool first) {
+        const uint64_t db = dRing + (uint64_t)(cst * (kStageBytes >> 4));
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            ptx::mma_pair(dtm, da + (uint64_t)(q * (kTile * 128 >> 4) + 2 * ks),
+                          db + (uint64_t)(q * (kSlabBytes >> 4) + 2 * ks), idd, (first && q == 0 && ks == 0) ? 0u : 1u);
+        ptx::mma_commit_pair(bar(base, B_EMPTY0 + cst));
+        ++g;
+        if (++cst == kStages) { cst = 0; cph ^= 1u; }
+      };
       for (int it = 0; it < my_tiles && ok; ++it) {
         for (int s = 0; s <= n_steps && ok; ++s) {
           const uint64_t dAbuf = dA[(it + s) & 1];
           // the input Jacobian df/denc = W_1q^T g_1 goes to TMEM columns [384, 384 + nj):
           // the stash is free by then, so the next tile's first chain need not wait for it
           const bool jstep = (s == n_steps);
+          const uint32_t idd = jstep ? idj : id128;
           for (int hh = 0; hh < (jstep ? 1 : 2) && ok; ++hh) {
-            for (int kc = 0; kc < 4; ++kc, ++g) {
-              if (hh == 0 && kc == 0) {
-                if (!wait_role(bar(base, B_ED0 + 0), ea & 1u, abort_flag, tw.err)) { ok = false; break; }
-                ++ea;
-                ptx::tc_fence_after();
-              }
-              if (hh == 0 && kc == 2) {
-                if (!wait_role(bar(base, B_ED0 + 1), eb & 1u, abort_flag, tw.err)) { ok = false; break; }
-                ++eb;
-                ptx::tc_fence_after();
-              }
-              const int st = cst;
-              // slab written by TMA: the transaction barrier orders it before the MMA
-              if (!wait_role(bar(base, B_FULL0 + st), cph, abort_flag, tw.err)) {
-                ok = false;
-                break;
-              }
-              const uint64_t da = dAbuf + (uint64_t)(kc * (kTile * 128) >> 4);
-              const uint64_t db = dRing + (uint64_t)(st * kSlabBytes >> 4);
-              const uint32_t dtm = tmem + (jstep ? 384 : hh * kHalf);
-              const uint32_t idd = jstep ? idj : id128;
+            const uint32_t dtm = tmem + (jstep ? 384 : hh * kHalf);
 #pragma unroll
-              for (int ks = 0; ks < 4; ++ks) ptx::mma_bf16(dtm, da + 2 * ks, db + 2 * ks, idd, (kc | ks) != 0);
-              ptx::mma_commit(bar(base, B_EMPTY0 + st));
-              if (++cst == kStages) { cst = 0; cph ^= 1u; }
+            for (int pr = 0; pr < 2; ++pr) {
+              if (hh == 0) {
+                // input columns [128 pr, 128 pr + 128) come from the previous step's half pr
+                // (both CTAs' epilogues arrive)
+                if (!wait_role(bar(base, B_ED0 + pr), (pr ? eb : ea) & 1u, abort_flag, tw.err)) {
+                  ok = false;
+                  break;
+                }
+                if (pr) ++eb; else ++ea;
+                ptx::tc_fence_after();
+              }
+              // both CTAs' slabs written by TMA: the transaction barrier orders them before the MMAs
+              if (!wait_role(bar(base, B_FULL0 + cst), cph, abort_flag, tw.err)) { ok = false; break; }
+              stage_mmas(dtm, dAbuf + (uint64_t)((2 * pr) * (kTile * 128) >> 4), idd, pr == 0);
             }
-            if (ok) ptx::mma_commit(bar(base, B_ACC0 + hh));
+            if (ok) ptx::mma_commit_pair(bar(base, B_ACC0 + hh));
           }
         }
       }
@@ -404,9 +472,30 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       ptx::st_shared_v4(abuf + aoff(c0, 0), o[0], o[1], o[2], o[3]);
       ptx::st_shared_v4(abuf + aoff(c0, 1), o[4], o[5], o[6], o[7]);
     };
+    // the half's epilogue is done in this warp: release the accumulator half and
+    // the A-buffer columns it wrote to the even CTA's MMA issuer, one arrival per
+    // warp.  Every lane's TMEM loads have completed (wait::ld) and are ordered by
+    // the tcgen05 fence; its shared-memory stores are made visible to the async
+    // proxy (which the tensor core reads through) before the warp synchronises.
+    const uint32_t ed_lead = ptx::mapa_shared(bar(base, B_ED0), 0);
+    auto epi_done = [&](int h) {
+      ptx::tc_fence_before();
+      ptx::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        if (leader) ptx::mbar_arrive(bar(base, B_ED0 + h));
+        else ptx::mbar_arrive_remote(ed_lead + 8u * (uint32_t)h);
+      }
+    };
     auto load_tile = [&](int it) {
-      t = (int)blockIdx.x + it * (int)gridDim.x;
-      tile_lookup(w, t, wp, start, len);
+      t = 2 * (cluster + it * nclusters) + (int)rank;
+      if (t < ntiles) {
+        tile_lookup(w, t, wp, start, len);
+      } else {  // the odd CTA's half of the last pair tile when the tile count is odd
+        wp = 0;
+        start = 0;
+        len = 0;
+      }
       float px = 0.f, py = 0.f, pz = 0.f;
       if (row < len) {
         int j;
@@ -441,9 +530,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         }
         store8c(abuf, c0 + cc, o);
       }
-      ptx::tc_fence_before();
-      ptx::fence_proxy_async_smem();
-      ptx::mbar_arrive(bar(base, B_ED0 + h));
+      epi_done(h);
     };
 
     if (my_tiles > 0) {
@@ -456,7 +543,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       for (int s = 0; s < n_steps && ok; ++s) {
         const uint32_t obuf = base + (((it + s + 1) & 1) ? kOffA1 : kOffA0);
         for (int h = 0; h < 2; ++h) {
-          if (!wait_epi(bar(base, B_ACC0 + h), acc_n[h] & 1u, abort_flag, tw.err)) { ok = false; break; }
+          if (!wait_epi_warp(bar(base, B_ACC0 + h), acc_n[h] & 1u, abort_flag, tw.err)) { ok = false; break; }
           ++acc_n[h];
           ptx::tc_fence_after();
           const int c0 = h * kHalf + 32 * kq;     // first column of this thread in this half
@@ -539,9 +626,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               store8c(obuf, c0 + cc, o);
             }
           }
-          ptx::tc_fence_before();
-          ptx::fence_proxy_async_smem();
-          ptx::mbar_arrive(bar(base, B_ED0 + h));
+          epi_done(h);
         }
       }
       if (!ok) break;
@@ -554,11 +639,11 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         first_layer(it + 1, 1);
       }
       // the input-Jacobian chain of this tile (completion 2L-1 of ACC[a] per tile)
-      if (!wait_epi(bar(base, B_ACC0 + 0), acc_n[0] & 1u, abort_flag, tw.err)) { ok = false; break; }
+      if (!wait_epi_warp(bar(base, B_ACC0 + 0), acc_n[0] & 1u, abort_flag, tw.err)) { ok = false; break; }
       ++acc_n[0];
       ptx::tc_fence_after();
       if (ej) {
-        if (!wait_epi(bar(base, B_FD), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }
+        if (!wait_epi_warp(bar(base, B_FD), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }
         uint32_t v[32];
         if (w.n_ang <= 7) {
           ptx::tmem_ld16(t_lane + 384, v);
@@ -591,31 +676,32 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
             }
           }
         } else {
-          const Partial pr = warp_tile_partial(w.mode, w.param, valid, fval, dq, n, j, cur_start + row);
-          if (lane == 0) {
-            s_part[quad] = pr;
-            ptx::mbar_arrive(bar(base, B_PD));
-          }
+          warp_tile_partial(w.mode, w.param, valid, fval, dq, n, j, cur_start + row, &s_part[quad]);
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(bar(base, B_PD));
           if (quad == 0 && lane == 0) {
             if (!wait_epi(bar(base, B_PD), (uint32_t)it & 1u, abort_flag, tw.err)) {
               ok = false;
-            } else {
+            } else if (cur_t < ntiles) {
               Partial a = s_part[0];
               for (int qq = 1; qq < 4; ++qq) a = partial_combine(w.mode, w.param, a, s_part[qq]);
               w.partials[cur_t] = a;
             }
           }
+          if (quad == 0) ok = __all_sync(0xffffffffu, ok);  // lane 0's wait decides for its warp
         }
       }
     }
   }
 
   // ---- teardown ---------------------------------------------------------------
+  // every thread of both CTAs gets here (all waits are bounded): no CTA leaves
+  // while its peer may still signal its barriers or read its operands
   ptx::tc_fence_before();
-  __syncthreads();
+  ptx::cluster_sync();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, kTmemCols);
+    ptx::tmem_dealloc_pair(tmem, kTmemCols);
   }
 }
 
@@ -663,7 +749,9 @@ int tc_tile_pairs() { return kTile; }
 
 bool tc_supported(int H, int L, int n_dof) { return H == kH && L >= 2 && L <= 4 && n_dof >= 3 && n_dof <= kMaxDof; }
 
-int tc_nj(int d_q) { return d_q <= 16 ? 16 : 32; }
+// the input-Jacobian chain is one MMA of N = 32 (16 rows per CTA of the pair):
+// d_q = 2 n_dof - 2 <= 22 for every supported n_dof, zero rows pad
+int tc_nj(int) { return 32; }
 
 // Image layout (16-bit, row-major, 256 columns): rows [256 m, 256 m + 256) hold
 // W_{m+2} for m = 0..L-2 (forward operands, row = output feature), then rows
@@ -694,25 +782,46 @@ void tc_build_image(const float* W, int H, int L, int d_q, int d_in, bool f16, u
 }
 
 int tc_encode_maps(const uint16_t* image, int H, int L, int d_q, bool f16, TcWeights& tw) {
-  int rc = encode_2d(&tw.map_w, image, 2 * (L - 1) * H, H, kHalf, f16);
+  // boxes: one CTA's share of a chain (kRowsCta weight rows, nj / 2 Jacobian rows) x 64 columns
+  int rc = encode_2d(&tw.map_w, image, 2 * (L - 1) * H, H, kRowsCta, f16);
   if (rc) return rc;
-  return encode_2d(&tw.map_j, image + (size_t)2 * (L - 1) * H * H, tc_nj(d_q), H, tc_nj(d_q), f16);
+  return encode_2d(&tw.map_j, image + (size_t)2 * (L - 1) * H * H, tc_nj(d_q), H, tc_nj(d_q) / 2, f16);
 }
 
 template <bool kF16>
 cudaError_t launch_tc_t(const WorkDesc& w, const TcWeights& tw, int num_sms, cudaStream_t s) {
-  static int attr_done[64] = {0};
+  // clusters of 2 CTAs (one per SM); as many as can be resident at once, each
+  // looping over pair tiles
+  static int max_clusters[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+  const bool cached = dev >= 0 && dev < 64;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int mc = cached ? max_clusters[dev] : 0;
+  if (mc <= 0) {
     cudaError_t e = cudaFuncSetAttribute(tc_fused_kernel<kF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) attr_done[dev] = 1;
+    cfg.gridDim = dim3(2);
+    e = cudaOccupancyMaxActiveClusters(&mc, (void*)tc_fused_kernel<kF16>, &cfg);
+    if (e != cudaSuccess) return e;
+    if (mc <= 0) return cudaErrorLaunchOutOfResources;
+    if (cached) max_clusters[dev] = mc;
   }
-  const int grid = w.n_tiles < num_sms ? w.n_tiles : num_sms;
-  if (grid <= 0) return cudaSuccess;
-  tc_fused_kernel<kF16><<<grid, kThreads, kSmemBytes, s>>>(w, tw.map_w, tw.map_j, tw);
-  return cudaGetLastError();
+  if (num_sms > 0 && 2 * mc > num_sms) mc = num_sms / 2 > 0 ? num_sms / 2 : 1;
+  const int npt = (w.n_tiles + 1) / 2;
+  if (npt <= 0) return cudaSuccess;
+  cfg.gridDim = dim3(2 * (npt < mc ? npt : mc));
+  return cudaLaunchKernelEx(&cfg, tc_fused_kernel<kF16>, w, tw.map_w, tw.map_j, tw);
 }
 
 cudaError_t launch_tc(const WorkDesc& w, const TcWeights& tw, int num_sms, cudaStream_t s) {
