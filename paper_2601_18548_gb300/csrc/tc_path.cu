@@ -393,7 +393,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       // Shared-memory descriptors are linear in the start address (bits 0-13 hold
       // address / 16), so every operand descriptor is a base plus a small offset;
       // the same offsets address the peer CTA's operands.
-      const uint64_t dA[2] = {ptx::smem_desc_sw128(base + kOffA0, 1024), ptx::smem_desc_sw128(base + kOffA1, 1024)};
+      // (selected, never indexed: a dynamically indexed array would live in local memory)
+      const uint64_t dA0 = ptx::smem_desc_sw128(base + kOffA0, 1024), dA1 = ptx::smem_desc_sw128(base + kOffA1, 1024);
       const uint64_t dRing = ptx::smem_desc_sw128(base + kOffRing, 1024);
       // one stage: K = 128 of a chain (8 MMAs of K = 16), then release the stage in both CTAs
       auto stage_mmas = [&](uint32_t dtm, uint64_t da, uint32_t idd, bool first) {
@@ -410,7 +411,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       };
       for (int it = 0; it < my_tiles && ok; ++it) {
         for (int s = 0; s <= n_steps && ok; ++s) {
-          const uint64_t dAbuf = dA[(it + s) & 1];
+          const uint64_t dAbuf = ((it + s) & 1) ? dA1 : dA0;
           // the input Jacobian df/denc = W_1q^T g_1 goes to TMEM columns [384, 384 + nj):
           // the stash is free by then, so the next tile's first chain need not wait for it
           const bool jstep = (s == n_steps);
@@ -458,7 +459,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     const int r7 = row & 7;
     uint32_t* aiw = s_aiw + e * 32;        // f16x2 A_i / 2 for this thread's 32 + 32 columns
     float* trigw = reinterpret_cast<float*>(gbase + kOffTrig) + quad * 2 * 24;  // EJ warps only
-    uint32_t acc_n[2] = {0, 0};            // completions of ACC[a], ACC[b] consumed
+    uint32_t acc_na = 0, acc_nb = 0;       // completions of ACC[a], ACC[b] consumed (scalars: no local memory)
     bool ok = true;
 
     int t = 0, wp = 0, start = 0, len = 0;
@@ -543,8 +544,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       for (int s = 0; s < n_steps && ok; ++s) {
         const uint32_t obuf = base + (((it + s + 1) & 1) ? kOffA1 : kOffA0);
         for (int h = 0; h < 2; ++h) {
-          if (!wait_epi_warp(bar(base, B_ACC0 + h), acc_n[h] & 1u, abort_flag, tw.err)) { ok = false; break; }
-          ++acc_n[h];
+          if (!wait_epi_warp(bar(base, B_ACC0 + h), (h ? acc_nb : acc_na) & 1u, abort_flag, tw.err)) { ok = false; break; }
+          if (h) ++acc_nb; else ++acc_na;
           ptx::tc_fence_after();
           const int c0 = h * kHalf + 32 * kq;     // first column of this thread in this half
           const uint32_t t_acc = t_lane + c0;     // accumulator half h starts at column h * 128
@@ -639,8 +640,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         first_layer(it + 1, 1);
       }
       // the input-Jacobian chain of this tile (completion 2L-1 of ACC[a] per tile)
-      if (!wait_epi_warp(bar(base, B_ACC0 + 0), acc_n[0] & 1u, abort_flag, tw.err)) { ok = false; break; }
-      ++acc_n[0];
+      if (!wait_epi_warp(bar(base, B_ACC0 + 0), acc_na & 1u, abort_flag, tw.err)) { ok = false; break; }
+      ++acc_na;
       ptx::tc_fence_after();
       if (ej) {
         if (!wait_epi_warp(bar(base, B_FD), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }
