@@ -64,8 +64,9 @@ def job_throughput(local_seconds: float, units_per_rank: float, dist=None, devic
 
 def measured_traffic(precision: str, workload: str):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    or None when that summary is for another workload or the kernel source has
-    changed since the counters were taken."""
+    or None when that summary is for another workload or a source file of the
+    kernel has changed since the counters were taken (sha1 over the files in
+    order)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
@@ -74,9 +75,14 @@ def measured_traffic(precision: str, workload: str):
         rec = json.load(fh).get(precision)
     if not rec or not workload.startswith(rec["workload"]):
         return None
-    with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
-        if hashlib.sha1(fh.read()).hexdigest() != rec["sha1"]:
-            return None
+    if "sources" not in rec:
+        return None
+    h = hashlib.sha1()
+    for src in rec["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != rec["sha1"]:
+        return None
     return rec["dram_bytes_per_launch"]
 
 
