@@ -91,8 +91,8 @@ constexpr int kOffW1p = kOffBiasH + 3 * (kH / 2) * 4;           // [H/2] uint4: 
 constexpr int kOffWo = kOffW1p + (kH / 2) * 16;                 // [H] fp32 w_o
 constexpr int kOffWoh = kOffWo + kH * 4;                        // [H/2] f16x2 w_o / 2
 constexpr int kOffAiw = kOffWoh + (kH / 2) * 4;                 // [16 warps][32] f16x2 A_i / 2
-constexpr int kOffTrig = kOffAiw + kEpiWarps * 32 * 4;          // [4 warps][2 tiles][24] sin, cos
-constexpr int kOffF = kOffTrig + 4 * 2 * 24 * 4;                // [4][128] f partials
+constexpr int kOffTrig = kOffAiw + kEpiWarps * 32 * 4;          // [16 warps][2 tiles][24] sin, cos
+constexpr int kOffF = kOffTrig + kEpiWarps * 2 * 24 * 4;        // [4][128] f partials
 constexpr int kOffPart = kOffF + 4 * kTile * 4;                 // 4 partial records
 constexpr int kOffBar = kOffPart + 4 * (int)sizeof(Partial);
 constexpr int kNumBars = 2 * kStages + 6;
@@ -106,7 +106,7 @@ constexpr int B_EMPTY0 = kStages;       // + stage: its MMAs completed (commit t
 constexpr int B_ACC0 = 2 * kStages;     // + half: accumulator half complete (commit to both CTAs)
 constexpr int B_ED0 = 2 * kStages + 2;  // + half: epilogues of both CTAs done (even CTA, 32 warp arrivals)
 constexpr int B_FD = 2 * kStages + 4;   // f partials written (512 arrivals)
-constexpr int B_PD = 2 * kStages + 5;   // per-warp partial records written (4 arrivals)
+constexpr int B_PD = 2 * kStages + 5;   // partial-record parts written (16 warp arrivals)
 
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
 
@@ -183,15 +183,16 @@ __device__ __forceinline__ float warp_min(float x) {
   return r;
 }
 
-// Per-tile reduction of the 32 rows of a warp (lane = row; the list position
-// grows with the lane) into the partial record *out in shared memory, written
-// by the lanes of the warp (the caller synchronises the warp afterwards).
-// Argmin by (f, list position) with NaN first: a NaN ballot, else the warp
-// minimum and the lowest lane that holds it.  The sums of the mode (SOFTMIN:
-// one exponential per row relative to the warp minimum) are reduce-scattered:
-// after the exchanges lanes 2k and 2k + 1 hold the total of value k.
-__device__ __forceinline__ void warp_tile_partial(int mode, float param, bool valid, float f, const float* dq,
-                                                  int n, int idx, int pos, Partial* out) {
+// Part of the per-tile partial record of a row quad: the 32 rows of a warp (lane =
+// row; the list position grows with the lane) reduced for the gradient components
+// d = d0, d0 + 4, d0 + 8 held in dqm[] (zero past n).  The four warps of the quad
+// (d0 = 0..3) compute the same argmin and weights and write disjoint fields of
+// *out; the warp with d0 = 0 also writes the value fields and the argmin.
+// Argmin by (f, list position) with NaN first: a NaN ballot, else the warp minimum
+// (redux) and the lowest lane holding it.  SOFTMIN takes one exponential per row
+// relative to the warp minimum.  Sums use a fixed butterfly (deterministic).
+__device__ __forceinline__ void warp_partial_part(int mode, float param, bool valid, float f, const float* dqm,
+                                                  int d0, int n, int idx, int pos, Partial* out) {
   const int lane = threadIdx.x & 31;
   float* rec = reinterpret_cast<float*>(out);  // v0, v1, idx, pos, g[kMaxDof]
   const unsigned nanm = __ballot_sync(0xffffffffu, valid && f != f);
@@ -206,18 +207,20 @@ __device__ __forceinline__ void warp_tile_partial(int mode, float param, bool va
     win = __ballot_sync(0xffffffffu, valid && fv == fm);
   }
   if (win == 0u) {  // no valid row
-    if (lane == 0) *out = partial_identity(mode);
+    if (d0 == 0 && lane == 0) *out = partial_identity(mode);
     return;
   }
   const int src = __ffs(win) - 1;
   if (mode == kMin) {
     if (lane == src) {
-      rec[0] = f;
-      rec[1] = 0.f;
-      reinterpret_cast<int*>(rec)[2] = idx;
-      reinterpret_cast<int*>(rec)[3] = pos;
+      if (d0 == 0) {
+        rec[0] = f;
+        rec[1] = 0.f;
+        reinterpret_cast<int*>(rec)[2] = idx;
+        reinterpret_cast<int*>(rec)[3] = pos;
+      }
 #pragma unroll
-      for (int d = 0; d < kMaxDof; ++d) rec[4 + d] = dq[d];
+      for (int m = 0; m < 3; ++m) rec[4 + d0 + 4 * m] = dqm[m];
     }
     return;
   }
@@ -231,31 +234,20 @@ __device__ __forceinline__ void warp_tile_partial(int mode, float param, bool va
     v0 = valid ? fmaxf(0.f, param - f) : 0.f;
     if (valid && f != f) v0 = f;
   }
-  float v[16];
+  float v[4];
 #pragma unroll
-  for (int d = 0; d < kMaxDof; ++d) v[d] = (d < n) ? wgt * dq[d] : 0.f;
-  v[kMaxDof] = (mode == kSoftmin) ? wgt : v0;
+  for (int m = 0; m < 3; ++m) v[m] = (d0 + 4 * m < n) ? wgt * dqm[m] : 0.f;
+  v[3] = (mode == kSoftmin) ? wgt : v0;
 #pragma unroll
-  for (int d = kMaxDof + 1; d < 16; ++d) v[d] = 0.f;
-  // reduce-scatter: at the exchange with lane ^ m each lane keeps the half of its
-  // values selected by that lane bit and adds the partner's copy of it
+  for (int o = 16; o >= 1; o >>= 1)
 #pragma unroll
-  for (int m = 16, nv = 8; m >= 2; m >>= 1, nv >>= 1) {
-    const bool up = (lane & m) != 0;
+    for (int m = 0; m < 4; ++m) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
+  if (lane == 0) {
 #pragma unroll
-    for (int i = 0; i < nv; ++i) {
-      const float keep = up ? v[i + nv] : v[i];
-      const float send = up ? v[i] : v[i + nv];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
-    }
+    for (int m = 0; m < 3; ++m) rec[4 + d0 + 4 * m] = v[m];
+    if (d0 == 0) rec[mode == kSoftmin ? 1 : 0] = v[3];
   }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-  const int k = lane >> 1;  // value held by this lane
-  if ((lane & 1) == 0) {
-    if (k < kMaxDof) rec[4 + k] = v[0];
-    else if (k == kMaxDof) rec[mode == kSoftmin ? 1 : 0] = v[0];
-  }
-  if (lane == src) {
+  if (d0 == 0 && lane == src) {
     rec[mode == kSoftmin ? 0 : 1] = fm;
     reinterpret_cast<int*>(rec)[2] = idx;
     reinterpret_cast<int*>(rec)[3] = pos;
@@ -310,7 +302,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     ptx::mbar_init(bar(base, B_ED0 + 0), 2 * kEpiWarps);
     ptx::mbar_init(bar(base, B_ED0 + 1), 2 * kEpiWarps);
     ptx::mbar_init(bar(base, B_FD), kEpiThreads);
-    ptx::mbar_init(bar(base, B_PD), 4);
+    ptx::mbar_init(bar(base, B_PD), kEpiWarps);
     ptx::fence_barrier_init();
     ptx::prefetch_tensormap(&map_w);
     ptx::prefetch_tensormap(&map_j);
@@ -454,11 +446,10 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     const int row = quad * 32 + lane;
     const uint32_t t_lane = tmem + ((uint32_t)(quad * 32) << 16);
     const int n = w.n_dof;
-    const bool ej = (kq == 0);             // writes this tile's outputs
     const uint32_t rbase = (row >> 3) * 1024 + (row & 7) * 128;
     const int r7 = row & 7;
     uint32_t* aiw = s_aiw + e * 32;        // f16x2 A_i / 2 for this thread's 32 + 32 columns
-    float* trigw = reinterpret_cast<float*>(gbase + kOffTrig) + quad * 2 * 24;  // EJ warps only
+    float* trigw = reinterpret_cast<float*>(gbase + kOffTrig) + e * 2 * 24;  // this warp's sin, cos (2 tiles)
     uint32_t acc_na = 0, acc_nb = 0;       // completions of ACC[a], ACC[b] consumed (scalars: no local memory)
     bool ok = true;
 
@@ -513,7 +504,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       __syncwarp();
       if (lane < 16) aiw[lane] = ptx::pack_f16x2(0.5f * Ai[2 * lane], 0.5f * Ai[2 * lane + 1]);
       else aiw[lane] = ptx::pack_f16x2(0.5f * Ai[kHalf + 2 * (lane - 16)], 0.5f * Ai[kHalf + 2 * (lane - 16) + 1]);
-      if (ej && lane < 2 * w.n_ang) trigw[(it & 1) * 24 + lane] = w.trig[(size_t)wp * 2 * w.n_ang + lane];
+      if (lane < 2 * w.n_ang) trigw[(it & 1) * 24 + lane] = w.trig[(size_t)wp * 2 * w.n_ang + lane];
       __syncwarp();
     };
     // h_1 = s(A_i + W_1p p) for this row and 32 columns of half h -> A buffer (tile parity)
@@ -643,54 +634,60 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       if (!wait_epi_warp(bar(base, B_ACC0 + 0), acc_na & 1u, abort_flag, tw.err)) { ok = false; break; }
       ++acc_na;
       ptx::tc_fence_after();
-      if (ej) {
-        if (!wait_epi_warp(bar(base, B_FD), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }
-        uint32_t v[32];
-        if (w.n_ang <= 7) {
-          ptx::tmem_ld16(t_lane + 384, v);
-        } else {
-          ptx::tmem_ld32(t_lane + 384, v);
-        }
-        const float fval = s_f[row] + s_f[kTile + row] + s_f[2 * kTile + row] + s_f[3 * kTile + row] + tw.bout;
-        ptx::tmem_wait_ld();
-        const float* tr = trigw + (it & 1) * 24;
-        float dq[kMaxDof];
-        dq[0] = __uint_as_float(v[0]);
-        dq[1] = __uint_as_float(v[1]);
+      // output stage, shared by all 16 warps: the 4 warps of a row quad split the
+      // gradient components (d = kq, kq + 4, kq + 8) and each reads only the
+      // Jacobian columns they need (warp-uniform columns, no indexed registers)
+      if (!wait_epi_warp(bar(base, B_FD), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }
+      uint32_t jv[3][2];
 #pragma unroll
-        for (int a = 0; a < kMaxAngles; ++a)
-          dq[2 + a] = (a < w.n_ang) ? tr[2 * a + 1] * __uint_as_float(v[2 + 2 * a]) -
-                                          tr[2 * a] * __uint_as_float(v[3 + 2 * a])
-                                    : 0.f;
-        const bool valid = row < cur_len;
-        int j = -1;
-        long long k = 0;
-        if (valid) pair_at(w, cur_wp, cur_start + row, j, k);
-        if (w.mode == kQuery) {
-          if (valid) {
-            w.f_out[k] = fval;
-            if (w.g_out) {
-              float* go = w.g_out + (size_t)k * n;
+      for (int m = 0; m < 3; ++m) {
+        const int d = kq + 4 * m;
+        ptx::tmem_ld2(t_lane + 384 + (d < 2 ? 0 : 2 * d - 2), jv[m]);
+      }
+      const float fval = s_f[row] + s_f[kTile + row] + s_f[2 * kTile + row] + s_f[3 * kTile + row] + tw.bout;
+      ptx::tmem_wait_ld();
+      const float* tr = trigw + (it & 1) * 24;
+      float dqm[3];
 #pragma unroll
-              for (int d = 0; d < kMaxDof; ++d)
-                if (d < n) go[d] = dq[d];
-            }
-          }
+      for (int m = 0; m < 3; ++m) {
+        const int d = kq + 4 * m;
+        if (d < 2) {
+          dqm[m] = __uint_as_float(d == 0 ? jv[m][0] : jv[m][1]);
+        } else if (d < n) {  // angle a = d - 2: (sin, cos) chain rule of Eq. (10)
+          const int a = d - 2;
+          dqm[m] = tr[2 * a + 1] * __uint_as_float(jv[m][0]) - tr[2 * a] * __uint_as_float(jv[m][1]);
         } else {
-          warp_tile_partial(w.mode, w.param, valid, fval, dq, n, j, cur_start + row, &s_part[quad]);
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(bar(base, B_PD));
-          if (quad == 0 && lane == 0) {
-            if (!wait_epi(bar(base, B_PD), (uint32_t)it & 1u, abort_flag, tw.err)) {
-              ok = false;
-            } else if (cur_t < ntiles) {
-              Partial a = s_part[0];
-              for (int qq = 1; qq < 4; ++qq) a = partial_combine(w.mode, w.param, a, s_part[qq]);
-              w.partials[cur_t] = a;
-            }
-          }
-          if (quad == 0) ok = __all_sync(0xffffffffu, ok);  // lane 0's wait decides for its warp
+          dqm[m] = 0.f;
         }
+      }
+      const bool valid = row < cur_len;
+      int j = -1;
+      long long k = 0;
+      if (valid) pair_at(w, cur_wp, cur_start + row, j, k);
+      if (w.mode == kQuery) {
+        if (valid) {
+          if (kq == 0) w.f_out[k] = fval;
+          if (w.g_out) {
+            float* go = w.g_out + (size_t)k * n;
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+              if (kq + 4 * m < n) go[kq + 4 * m] = dqm[m];
+          }
+        }
+      } else {
+        warp_partial_part(w.mode, w.param, valid, fval, dqm, kq, n, j, cur_start + row, &s_part[quad]);
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(bar(base, B_PD));
+        if (e == 0 && lane == 0) {
+          if (!wait_epi(bar(base, B_PD), (uint32_t)it & 1u, abort_flag, tw.err)) {
+            ok = false;
+          } else if (cur_t < ntiles) {
+            Partial a = s_part[0];
+            for (int qq = 1; qq < 4; ++qq) a = partial_combine(w.mode, w.param, a, s_part[qq]);
+            w.partials[cur_t] = a;
+          }
+        }
+        if (e == 0) ok = __all_sync(0xffffffffu, ok);  // lane 0's wait decides for its warp
       }
     }
   }

@@ -163,6 +163,9 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
                : GCDF_R(0), GCDF_R(1), GCDF_R(2), GCDF_R(3), GCDF_R(4), GCDF_R(5), GCDF_R(6), GCDF_R(7)
                : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];\n" : GCDF_R(0), GCDF_R(1) : "r"(taddr));
+}
 #undef GCDF_R
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
