@@ -47,8 +47,9 @@
 // next tile's chains start while this tile's outputs (chain rule, reduction)
 // are still being produced.
 //
-// Warp roles (576 threads per CTA): warp 0 issues TMA loads, warp 1 allocates
-// TMEM and (even CTA) issues the pair's MMAs, warps 2..17 are the epilogue:
+// Warp roles (608 threads per CTA): warp 0 issues TMA loads, warp 1 allocates
+// TMEM and (even CTA) issues the pair's MMAs, warp 18 merges each tile's four
+// row-quad partial records into the tile's record, warps 2..17 are the epilogue:
 // all 16 process each half in turn; thread = one pair row (TMEM lane) and 32
 // columns of each half; each warp signals the end of a half to the MMA issuer
 // with one arrival.  The input-Jacobian operand W_1q^T streams through the
@@ -77,7 +78,8 @@ constexpr int kStages = 5;             // weight ring depth
 constexpr int kSlabBytes = kRowsCta * 128;  // 64 rows x 64 16-bit values (one K = 64 slab)
 constexpr int kStageBytes = 2 * kSlabBytes; // K = 128 of one chain per stage
 constexpr int kABytes = kTile * kH * 2;
-constexpr int kThreads = 576;
+constexpr int kThreads = 608;          // 19 warps
+constexpr int kMergeWarp = 18;         // merges each tile's four row-quad records
 constexpr int kEpiThreads = 512;       // epilogue threads (16 warps)
 constexpr int kEpiWarps = 16;
 constexpr uint32_t kTmemCols = 512;
@@ -95,7 +97,7 @@ constexpr int kOffTrig = kOffAiw + kEpiWarps * 32 * 4;          // [16 warps][2 
 constexpr int kOffF = kOffTrig + kEpiWarps * 2 * 24 * 4;        // [4][128] f partials
 constexpr int kOffPart = kOffF + 4 * kTile * 4;                 // 4 partial records
 constexpr int kOffBar = kOffPart + 4 * (int)sizeof(Partial);
-constexpr int kNumBars = 2 * kStages + 6;
+constexpr int kNumBars = 2 * kStages + 7;
 constexpr int kOffSlot = kOffBar + kNumBars * 8;
 constexpr int kSmemBytes = kOffSlot + 16 + 1024;                // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024 - 64, "shared memory budget");
@@ -107,6 +109,7 @@ constexpr int B_ACC0 = 2 * kStages;     // + half: accumulator half complete (co
 constexpr int B_ED0 = 2 * kStages + 2;  // + half: epilogues of both CTAs done (even CTA, 32 warp arrivals)
 constexpr int B_FD = 2 * kStages + 4;   // f partials written (512 arrivals)
 constexpr int B_PD = 2 * kStages + 5;   // partial-record parts written (16 warp arrivals)
+constexpr int B_MD = 2 * kStages + 6;   // the merge warp has read them (1 arrival)
 
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
 
@@ -254,6 +257,68 @@ __device__ __forceinline__ void warp_partial_part(int mode, float param, bool va
   }
 }
 
+// Merge of the four row-quad records of a tile into rec_out (global), one field
+// per lane (lanes 0..15), the result of folding them left to right with
+// partial_combine up to rounding: winner by (min f, position) with NaN first;
+// SOFTMIN rescales every record to the winner's minimum (one exponential per
+// record), HINGE adds the hinge sums.
+__device__ __forceinline__ void warp_combine_quads(int mode, float T, const Partial* parts, Partial* rec_out) {
+  const int lane = threadIdx.x & 31;
+  const float* R = reinterpret_cast<const float*>(parts);
+  const int* Ri = reinterpret_cast<const int*>(parts);
+  constexpr int kF = (int)(sizeof(Partial) / 4);
+  int wq = -1;
+  float wf = 0.f;
+  int wp = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int pq = Ri[q * kF + 3];
+    if (pq == 0x7fffffff) continue;  // identity record
+    const float fq = (mode == kHinge) ? R[q * kF + 1] : R[q * kF + 0];
+    if (wq < 0 || first_is_better(fq, pq, wf, wp)) {
+      wq = q;
+      wf = fq;
+      wp = pq;
+    }
+  }
+  float eq = 1.f;  // SOFTMIN rescale factor of record `lane` (lanes 0..3)
+  if (mode == kSoftmin && wq >= 0 && lane < 4) {
+    const float m = R[wq * kF + 0], v0 = R[lane * kF + 0];
+    eq = (v0 == m) ? 1.f : __expf(-(v0 - m) / T);
+  }
+  float e4[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) e4[q] = __shfl_sync(0xffffffffu, eq, q);
+  if (lane >= kF) return;
+  float* out = reinterpret_cast<float*>(rec_out);
+  if (wq < 0) {  // the identity record, field by field (as partial_identity)
+    float v = 0.f;
+    if (lane == 0) v = (mode == kHinge) ? 0.f : __int_as_float(0x7f800000);
+    if (lane == 1) v = (mode == kHinge) ? __int_as_float(0x7f800000) : 0.f;
+    if (lane == 2) v = __int_as_float(-1);
+    if (lane == 3) v = __int_as_float(0x7fffffff);
+    out[lane] = v;
+    return;
+  }
+  if (mode == kMin || lane == 2 || lane == 3) {
+    out[lane] = R[wq * kF + lane];
+    return;
+  }
+  if (mode == kHinge && lane == 1) {
+    out[1] = R[wq * kF + 1];
+    return;
+  }
+  if (mode == kSoftmin && lane == 0) {
+    out[0] = R[wq * kF + 0];
+    return;
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (Ri[q * kF + 3] != 0x7fffffff) acc += R[q * kF + lane] * e4[q];
+  out[lane] = acc;
+}
+
 template <bool kF16>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
@@ -303,6 +368,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     ptx::mbar_init(bar(base, B_ED0 + 1), 2 * kEpiWarps);
     ptx::mbar_init(bar(base, B_FD), kEpiThreads);
     ptx::mbar_init(bar(base, B_PD), kEpiWarps);
+    ptx::mbar_init(bar(base, B_MD), 1);
     ptx::fence_barrier_init();
     ptx::prefetch_tensormap(&map_w);
     ptx::prefetch_tensormap(&map_j);
@@ -436,6 +502,17 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         const long long t0 = clock64();
         while (!ptx::mbar_try_wait(bar(base, B_EMPTY0 + (int)(k % kStages)), (uint32_t)(k / kStages) & 1u))
           if (clock64() - t0 > kWaitCycles) { atomicOr(tw.err, 2); break; }
+      }
+    }
+  } else if (warp == kMergeWarp) {
+    // ================= merge warp: one partial record per tile =================
+    if (w.mode != kQuery) {
+      for (int it = 0; it < my_tiles; ++it) {
+        if (!wait_epi_warp(bar(base, B_PD), (uint32_t)it & 1u, abort_flag, tw.err)) break;
+        const int t = 2 * (cluster + it * nclusters) + (int)rank;
+        if (t < ntiles) warp_combine_quads(w.mode, w.param, s_part, &w.partials[t]);
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(bar(base, B_MD));  // s_part may be rewritten
       }
     }
   } else {
@@ -675,19 +752,14 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
           }
         }
       } else {
+        // the merge warp has read the previous tile's records
+        if (it > 0 && !wait_epi_warp(bar(base, B_MD), (uint32_t)(it - 1) & 1u, abort_flag, tw.err)) {
+          ok = false;
+          break;
+        }
         warp_partial_part(w.mode, w.param, valid, fval, dqm, kq, n, j, cur_start + row, &s_part[quad]);
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(bar(base, B_PD));
-        if (e == 0 && lane == 0) {
-          if (!wait_epi(bar(base, B_PD), (uint32_t)it & 1u, abort_flag, tw.err)) {
-            ok = false;
-          } else if (cur_t < ntiles) {
-            Partial a = s_part[0];
-            for (int qq = 1; qq < 4; ++qq) a = partial_combine(w.mode, w.param, a, s_part[qq]);
-            w.partials[cur_t] = a;
-          }
-        }
-        if (e == 0) ok = __all_sync(0xffffffffu, ok);  // lane 0's wait decides for its warp
       }
     }
   }
