@@ -621,13 +621,17 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
             // middle forward layer l = s + 2: h_l -> A, 2 s'(z_l) -> stash
             const uint32_t t_st = t_lane + 256 + 128 * s + (c0 >> 1);
             const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + s * (kH / 2) + (c0 >> 1));
-#pragma unroll 1
+            // both 16-column chunks are loaded at once, so the second load's
+            // latency hides behind the first chunk's arithmetic
+            uint32_t va[16], vb[16];
+            ptx::tmem_ld16(t_acc, va);
+            ptx::tmem_ld16(t_acc + 16, vb);
+            ptx::tmem_wait_ld();
+#pragma unroll
             for (int cc = 0; cc < 32; cc += 16) {
-              uint32_t v[16];
-              ptx::tmem_ld16(t_acc + cc, v);
+              const uint32_t* v = cc ? vb : va;
               const uint4 b0 = bh4[cc / 8], b1 = bh4[cc / 8 + 1];
               const uint32_t bh[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-              ptx::tmem_wait_ld();
               uint32_t o[8], st2[8];
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
@@ -701,7 +705,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       if (!ok) break;
 
       // ---- tile tail: the last reverse chain (both halves) has completed ------
-      const int cur_t = t, cur_wp = wp, cur_start = start, cur_len = len;
+      const int cur_wp = wp, cur_start = start, cur_len = len;
       if (it + 1 < my_tiles) {
         load_tile(it + 1);
         first_layer(it + 1, 0);

@@ -188,6 +188,42 @@ def test_collision_cost_scene(prec, kind, param):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("n_wp,n_pts", [(1, 100), (3, 300), (5, 257)])
+@pytest.mark.parametrize("kind,param", [("min", 0.0), ("softmin", 0.1), ("hinge", 0.05)])
+def test_collision_cost_odd_tile_counts(prec, n_wp, n_pts, kind, param):
+    """Tile counts 1, 9 and 15: CTA pairs share each MMA, so the odd CTA of the
+    last pair works on an empty tile whose results must not be written.  The
+    reduction is checked against the FP64 definition applied to the kernel's own
+    per-pair values and gradients (query mode, same arithmetic), which isolates
+    the tile, pair and merge logic from the low-precision error of f."""
+    from oracle.reduce import reduce_waypoint
+    torch = need_gpu()
+    g = lib()
+    shape, w = small_net(9, 256, 4, seed=5)
+    q = random_traj(n_wp, 9, 12)
+    p = synth.uniform_points(synth.SplitMix64(13), n_pts, [-2, -2, 0], [2, 2, 2])
+    net = _net(g, shape, w, prec)
+    qd, pd = to_dev(torch, q), to_dev(torch, p)
+    c, gc, am = g.collision_cost(net, qd, pd, kind, param)
+    f_gpu, g_gpu = g.query(net, qd, pd)
+    torch.cuda.synchronize()
+    assert g.device_status(net) == 0
+    c, gc, am = c.cpu().numpy(), gc.cpu().numpy(), am.cpu().numpy()
+    f_gpu = f_gpu.cpu().numpy().astype(np.float64).reshape(n_wp, n_pts)
+    g_gpu = g_gpu.cpu().numpy().astype(np.float64).reshape(n_wp, n_pts, -1)
+    for i in range(n_wp):
+        c_i, g_i, a_i = reduce_waypoint(kind, param, f_gpu[i], g_gpu[i], np.arange(n_pts))
+        assert am[i] == a_i  # the argmin (lowest index on ties) is exact
+        if kind == "min":  # a selection: exact
+            assert c[i] == np.float32(c_i) and np.array_equal(gc[i], g_gpu[i, a_i].astype(np.float32))
+        else:
+            scale = max(1.0, np.abs(c_i))
+            assert abs(c[i] - c_i) <= 1e-5 * scale, (c[i], c_i)
+            gs = max(1e-3, np.abs(g_i).max())
+            assert np.abs(gc[i] - g_i).max() <= 1e-4 * gs, (gc[i], g_i)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 def test_full_size_scene_sampled_waypoints(prec):
     """The benchmark workload (128 waypoints x 16,384 points, soft-min T = 0.02),
     in the bench's launch configuration; the oracle checks 4 whole waypoints."""
