@@ -50,9 +50,11 @@
 // Warp roles (608 threads per CTA): warp 0 issues TMA loads, warp 1 allocates
 // TMEM and (even CTA) issues the pair's MMAs, warp 18 merges each tile's four
 // row-quad partial records into the tile's record, warps 2..17 are the epilogue:
-// all 16 process each half in turn; thread = one pair row (TMEM lane) and 32
-// columns of each half; each warp signals the end of a half to the MMA issuer
-// with one arrival.  The input-Jacobian operand W_1q^T streams through the
+// 8 warps process half a of every step and 8 warps half b, so the epilogue of
+// half b starts as soon as its accumulator is ready instead of after half a's;
+// thread = one pair row (TMEM lane) and 64 columns of its half; each warp
+// signals the end of a half to the MMA issuer with one arrival.  The output
+// stage uses all 16 warps.  The input-Jacobian operand W_1q^T streams through the
 // same ring as the weights.
 //
 // Every cross-warp and cross-CTA handoff is an mbarrier and every wait on one
@@ -97,7 +99,7 @@ constexpr int kOffTrig = kOffAiw + kEpiWarps * 32 * 4;          // [16 warps][2 
 constexpr int kOffF = kOffTrig + kEpiWarps * 2 * 24 * 4;        // [4][128] f partials
 constexpr int kOffPart = kOffF + 4 * kTile * 4;                 // 4 partial records
 constexpr int kOffBar = kOffPart + 4 * (int)sizeof(Partial);
-constexpr int kNumBars = 2 * kStages + 7;
+constexpr int kNumBars = 2 * kStages + 8;
 constexpr int kOffSlot = kOffBar + kNumBars * 8;
 constexpr int kSmemBytes = kOffSlot + 16 + 1024;                // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024 - 64, "shared memory budget");
@@ -106,10 +108,11 @@ static_assert(kSmemBytes <= 227 * 1024 - 64, "shared memory budget");
 constexpr int B_FULL0 = 0;              // + stage: both CTAs' slabs landed (used in the even CTA)
 constexpr int B_EMPTY0 = kStages;       // + stage: its MMAs completed (commit to both CTAs)
 constexpr int B_ACC0 = 2 * kStages;     // + half: accumulator half complete (commit to both CTAs)
-constexpr int B_ED0 = 2 * kStages + 2;  // + half: epilogues of both CTAs done (even CTA, 32 warp arrivals)
+constexpr int B_ED0 = 2 * kStages + 2;  // + half: epilogues of both CTAs done (even CTA, 16 warp arrivals)
 constexpr int B_FD = 2 * kStages + 4;   // f partials written (512 arrivals)
 constexpr int B_PD = 2 * kStages + 5;   // partial-record parts written (16 warp arrivals)
 constexpr int B_MD = 2 * kStages + 6;   // the merge warp has read them (1 arrival)
+constexpr int B_ACCJ = 2 * kStages + 7; // input-Jacobian chain complete (commit to both CTAs)
 
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
 
@@ -364,11 +367,12 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     }
     ptx::mbar_init(bar(base, B_ACC0 + 0), 1);
     ptx::mbar_init(bar(base, B_ACC0 + 1), 1);
-    ptx::mbar_init(bar(base, B_ED0 + 0), 2 * kEpiWarps);
-    ptx::mbar_init(bar(base, B_ED0 + 1), 2 * kEpiWarps);
+    ptx::mbar_init(bar(base, B_ED0 + 0), kEpiWarps);  // 8 warps of the half x 2 CTAs
+    ptx::mbar_init(bar(base, B_ED0 + 1), kEpiWarps);
     ptx::mbar_init(bar(base, B_FD), kEpiThreads);
     ptx::mbar_init(bar(base, B_PD), kEpiWarps);
     ptx::mbar_init(bar(base, B_MD), 1);
+    ptx::mbar_init(bar(base, B_ACCJ), 1);
     ptx::fence_barrier_init();
     ptx::prefetch_tensormap(&map_w);
     ptx::prefetch_tensormap(&map_j);
@@ -492,7 +496,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               if (!wait_role(bar(base, B_FULL0 + cst), cph, abort_flag, tw.err)) { ok = false; break; }
               stage_mmas(dtm, dAbuf + (uint64_t)((2 * pr) * (kTile * 128) >> 4), idd, pr == 0);
             }
-            if (ok) ptx::mma_commit_pair(bar(base, B_ACC0 + hh));
+            if (ok) ptx::mma_commit_pair(bar(base, jstep ? B_ACCJ : B_ACC0 + hh));
           }
         }
       }
@@ -519,7 +523,9 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     // ================= epilogue: 16 warps, one pair row, 32 columns of each half ========
     const int e = warp - 2;
     const int quad = warp & 3;
-    const int kq = e >> 2;                 // which 32 columns of each half
+    const int kq = e >> 2;                 // 0..3: split of the output stage's gradient components
+    const int hg = kq >> 1;                // the half this warp processes in every step
+    const int cw = hg * kHalf + 64 * (kq & 1);  // first of its 64 columns
     const int row = quad * 32 + lane;
     const uint32_t t_lane = tmem + ((uint32_t)(quad * 32) << 16);
     const int n = w.n_dof;
@@ -527,7 +533,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     const int r7 = row & 7;
     uint32_t* aiw = s_aiw + e * 32;        // f16x2 A_i / 2 for this thread's 32 + 32 columns
     float* trigw = reinterpret_cast<float*>(gbase + kOffTrig) + e * 2 * 24;  // this warp's sin, cos (2 tiles)
-    uint32_t acc_na = 0, acc_nb = 0;       // completions of ACC[a], ACC[b] consumed (scalars: no local memory)
+    uint32_t acc_n = 0;                    // completions of this warp's ACC half consumed
     bool ok = true;
 
     int t = 0, wp = 0, start = 0, len = 0;
@@ -577,59 +583,60 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       px2 = ptx::pack_f16x2(px, px);
       py2 = ptx::pack_f16x2(py, py);
       pz2 = ptx::pack_f16x2(pz, pz);
-      const float* Ai = w.A + (size_t)wp * kH + 32 * kq;
+      const float* Ai = w.A + (size_t)wp * kH + cw;
       __syncwarp();
-      if (lane < 16) aiw[lane] = ptx::pack_f16x2(0.5f * Ai[2 * lane], 0.5f * Ai[2 * lane + 1]);
-      else aiw[lane] = ptx::pack_f16x2(0.5f * Ai[kHalf + 2 * (lane - 16)], 0.5f * Ai[kHalf + 2 * (lane - 16) + 1]);
+      aiw[lane] = ptx::pack_f16x2(0.5f * Ai[2 * lane], 0.5f * Ai[2 * lane + 1]);
       if (lane < 2 * w.n_ang) trigw[(it & 1) * 24 + lane] = w.trig[(size_t)wp * 2 * w.n_ang + lane];
       __syncwarp();
     };
-    // h_1 = s(A_i + W_1p p) for this row and 32 columns of half h -> A buffer (tile parity)
-    auto first_layer = [&](int it, int h) {
+    // h_1 = s(A_i + W_1p p) for this row and the warp's 64 columns -> A buffer (tile parity)
+    auto first_layer = [&](int it) {
       const uint32_t abuf = base + ((it & 1) ? kOffA1 : kOffA0);
-      const int c0 = h * kHalf + 32 * kq;
+      const int c0 = cw;
 #pragma unroll 1
-      for (int cc = 0; cc < 32; cc += 16) {
+      for (int cc = 0; cc < 64; cc += 16) {
         uint32_t o[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const uint32_t u = first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[16 * h + cc / 2 + i], px2, py2, pz2);
+          const uint32_t u = first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2);
           const uint32_t tt = ptx::htanh2(u);
           o[i] = to_operand<kF16>(ptx::hfma2(u, tt, u));
         }
         store8c(abuf, c0 + cc, o);
       }
-      epi_done(h);
+      epi_done(hg);
     };
 
     if (my_tiles > 0) {
       load_tile(0);
-      first_layer(0, 0);
-      first_layer(0, 1);
+      first_layer(0);
     }
     float fpart = 0.f;  // sum of w_o s(z_L) over this thread's 64 columns
     for (int it = 0; it < my_tiles && ok; ++it) {
       for (int s = 0; s < n_steps && ok; ++s) {
         const uint32_t obuf = base + (((it + s + 1) & 1) ? kOffA1 : kOffA0);
-        for (int h = 0; h < 2; ++h) {
-          if (!wait_epi_warp(bar(base, B_ACC0 + h), (h ? acc_nb : acc_na) & 1u, abort_flag, tw.err)) { ok = false; break; }
-          if (h) ++acc_nb; else ++acc_na;
+        {
+          const int h = hg;
+          if (!wait_epi_warp(bar(base, B_ACC0 + h), acc_n & 1u, abort_flag, tw.err)) { ok = false; break; }
+          ++acc_n;
           ptx::tc_fence_after();
-          const int c0 = h * kHalf + 32 * kq;     // first column of this thread in this half
+          const int c0 = cw;                      // first of this warp's 64 columns
           const uint32_t t_acc = t_lane + c0;     // accumulator half h starts at column h * 128
           if (s < L - 2) {
             // middle forward layer l = s + 2: h_l -> A, 2 s'(z_l) -> stash
             const uint32_t t_st = t_lane + 256 + 128 * s + (c0 >> 1);
             const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + s * (kH / 2) + (c0 >> 1));
-            // both 16-column chunks are loaded at once, so the second load's
+            // two 16-column chunks are loaded at once, so the second load's
             // latency hides behind the first chunk's arithmetic
+#pragma unroll 1
+            for (int cp = 0; cp < 64; cp += 32) {
             uint32_t va[16], vb[16];
-            ptx::tmem_ld16(t_acc, va);
-            ptx::tmem_ld16(t_acc + 16, vb);
+            ptx::tmem_ld16(t_acc + cp, va);
+            ptx::tmem_ld16(t_acc + cp + 16, vb);
             ptx::tmem_wait_ld();
 #pragma unroll
-            for (int cc = 0; cc < 32; cc += 16) {
-              const uint32_t* v = cc ? vb : va;
+            for (int cc = cp; cc < cp + 32; cc += 16) {
+              const uint32_t* v = (cc - cp) ? vb : va;
               const uint4 b0 = bh4[cc / 8], b1 = bh4[cc / 8 + 1];
               const uint32_t bh[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
               uint32_t o[8], st2[8];
@@ -643,13 +650,14 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               store8c(obuf, c0 + cc, o);
               ptx::tmem_st8(t_st + cc / 2, st2);
             }
+            }
             ptx::tmem_wait_st();
           } else if (s == L - 2) {
             // last forward layer: f partial (FP32 sum), g_L = w_o s'(z_L) -> A
-            if (h == 0) fpart = 0.f;
+            fpart = 0.f;
             const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + (L - 2) * (kH / 2) + (c0 >> 1));
 #pragma unroll 1
-            for (int cc = 0; cc < 32; cc += 16) {
+            for (int cc = 0; cc < 64; cc += 16) {
               uint32_t v[16];
               ptx::tmem_ld16(t_acc + cc, v);
               const uint4 b0 = bh4[cc / 8], b1 = bh4[cc / 8 + 1];
@@ -670,15 +678,13 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               }
               store8c(obuf, c0 + cc, o);
             }
-            if (h == 1) {
-              s_f[kq * kTile + row] = fpart;
-              ptx::mbar_arrive(bar(base, B_FD));
-            }
+            s_f[kq * kTile + row] = fpart;
+            ptx::mbar_arrive(bar(base, B_FD));
           } else {
             // reverse step: g_{l-1} = acc * 2 s'(z_{l-1}), acc = (W_l^T / 2) g_l
             const int lm1 = 2 * L - 2 - s;
 #pragma unroll 1
-            for (int cc = 0; cc < 32; cc += 16) {
+            for (int cc = 0; cc < 64; cc += 16) {
               uint32_t v[16], d2[8];
               ptx::tmem_ld16(t_acc + cc, v);
               if (lm1 >= 2) ptx::tmem_ld8(t_lane + 256 + 128 * (lm1 - 2) + ((c0 + cc) >> 1), d2);
@@ -687,7 +693,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                   uint32_t hh;
-                  silu2(first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[16 * h + cc / 2 + i], px2, py2, pz2), hh, d2[i]);
+                  silu2(first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2), hh, d2[i]);
                 }
               }
               uint32_t o[8];
@@ -708,12 +714,10 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       const int cur_wp = wp, cur_start = start, cur_len = len;
       if (it + 1 < my_tiles) {
         load_tile(it + 1);
-        first_layer(it + 1, 0);
-        first_layer(it + 1, 1);
+        first_layer(it + 1);
       }
-      // the input-Jacobian chain of this tile (completion 2L-1 of ACC[a] per tile)
-      if (!wait_epi_warp(bar(base, B_ACC0 + 0), acc_na & 1u, abort_flag, tw.err)) { ok = false; break; }
-      ++acc_na;
+      // the input-Jacobian chain of this tile
+      if (!wait_epi_warp(bar(base, B_ACCJ), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }
       ptx::tc_fence_after();
       // output stage, shared by all 16 warps: the 4 warps of a row quad split the
       // gradient components (d = kq, kq + 4, kq + 8) and each reads only the
