@@ -683,13 +683,16 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
           } else {
             // reverse step: g_{l-1} = acc * 2 s'(z_{l-1}), acc = (W_l^T / 2) g_l
             const int lm1 = 2 * L - 2 - s;
+            // 2 s'(z_1) sits in the stash columns of z_{L-1} when there is a stash
+            const int lsrc = (lm1 >= 2) ? lm1 : (L - 1);
+            const bool stashed = lm1 >= 2 || L >= 3;
 #pragma unroll 1
             for (int cc = 0; cc < 64; cc += 16) {
               uint32_t v[16], d2[8];
               ptx::tmem_ld16(t_acc + cc, v);
-              if (lm1 >= 2) ptx::tmem_ld8(t_lane + 256 + 128 * (lm1 - 2) + ((c0 + cc) >> 1), d2);
+              if (stashed) ptx::tmem_ld8(t_lane + 256 + 128 * (lsrc - 2) + ((c0 + cc) >> 1), d2);
               ptx::tmem_wait_ld();
-              if (lm1 < 2) {
+              if (!stashed) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                   uint32_t hh;
@@ -706,14 +709,39 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
             }
           }
           epi_done(h);
+          if (s == L - 1 && L >= 3) {
+            // the first reverse step has read this warp's stash columns of z_{L-1}:
+            // recompute 2 s'(z_1) = 2 s'(A_i + W_1p p) into them while the tensor
+            // core runs the next reverse chains (the last reverse step loads it)
+            const uint32_t t_r1 = t_lane + 256 + 128 * (L - 3) + (c0 >> 1);
+#pragma unroll 1
+            for (int cc = 0; cc < 64; cc += 16) {
+              uint32_t d2[8];
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                uint32_t hh;
+                silu2(first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2), hh, d2[i]);
+              }
+              ptx::tmem_st8(t_r1 + cc / 2, d2);
+            }
+            ptx::tmem_wait_st();
+          }
         }
       }
       if (!ok) break;
 
-      // ---- tile tail: the last reverse chain (both halves) has completed ------
+      // ---- tile tail ------------------------------------------------------------
       const int cur_wp = wp, cur_start = start, cur_len = len;
       if (it + 1 < my_tiles) {
         load_tile(it + 1);
+        // the next tile's first layer overwrites the A buffer that the last reverse
+        // step's chains read: the warps of half 0 have seen only their own chain
+        // complete, so they wait for the half-1 chain (its commit follows every
+        // earlier MMA; it cannot complete again before this first layer is done)
+        if (hg == 0) {
+          if (!wait_epi_warp(bar(base, B_ACC0 + 1), (acc_n - 1u) & 1u, abort_flag, tw.err)) { ok = false; break; }
+          ptx::tc_fence_after();
+        }
         first_layer(it + 1);
       }
       // the input-Jacobian chain of this tile
