@@ -99,7 +99,7 @@ constexpr int kOffTrig = kOffAiw + kEpiWarps * 32 * 4;          // [16 warps][2 
 constexpr int kOffF = kOffTrig + kEpiWarps * 2 * 24 * 4;        // [4][128] f partials
 constexpr int kOffPart = kOffF + 4 * kTile * 4;                 // 4 partial records
 constexpr int kOffBar = kOffPart + 4 * (int)sizeof(Partial);
-constexpr int kNumBars = 2 * kStages + 8;
+constexpr int kNumBars = 2 * kStages + 10;
 constexpr int kOffSlot = kOffBar + kNumBars * 8;
 constexpr int kSmemBytes = kOffSlot + 16 + 1024;                // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024 - 64, "shared memory budget");
@@ -113,6 +113,12 @@ constexpr int B_FD = 2 * kStages + 4;   // f partials written (512 arrivals)
 constexpr int B_PD = 2 * kStages + 5;   // partial-record parts written (16 warp arrivals)
 constexpr int B_MD = 2 * kStages + 6;   // the merge warp has read them (1 arrival)
 constexpr int B_ACCJ = 2 * kStages + 7; // input-Jacobian chain complete (commit to both CTAs)
+// + half: a tile's first layer written (even CTA, 16 warp arrivals).  Kept apart
+// from B_ED0: a warp arrives for its last reverse step and then for the next
+// tile's first layer with no wait in between that would prove the first phase
+// complete, so on one barrier a fast warp's second arrival could complete the
+// phase that still waits for a slow warp's first.
+constexpr int B_FL0 = 2 * kStages + 8;
 
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
 
@@ -373,6 +379,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     ptx::mbar_init(bar(base, B_PD), kEpiWarps);
     ptx::mbar_init(bar(base, B_MD), 1);
     ptx::mbar_init(bar(base, B_ACCJ), 1);
+    ptx::mbar_init(bar(base, B_FL0 + 0), kEpiWarps);
+    ptx::mbar_init(bar(base, B_FL0 + 1), kEpiWarps);
     ptx::fence_barrier_init();
     ptx::prefetch_tensormap(&map_w);
     ptx::prefetch_tensormap(&map_j);
@@ -485,11 +493,17 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               if (hh == 0) {
                 // input columns [128 pr, 128 pr + 128) come from the previous step's half pr
                 // (both CTAs' epilogues arrive)
-                if (!wait_role(bar(base, B_ED0 + pr), (pr ? eb : ea) & 1u, abort_flag, tw.err)) {
+                // (step 0: the tile's first layer, on its own barriers)
+                const bool ok_w = (s == 0)
+                    ? wait_role(bar(base, B_FL0 + pr), (uint32_t)it & 1u, abort_flag, tw.err)
+                    : wait_role(bar(base, B_ED0 + pr), (pr ? eb : ea) & 1u, abort_flag, tw.err);
+                if (!ok_w) {
                   ok = false;
                   break;
                 }
-                if (pr) ++eb; else ++ea;
+                if (s != 0) {
+                  if (pr) ++eb; else ++ea;
+                }
                 ptx::tc_fence_after();
               }
               // both CTAs' slabs written by TMA: the transaction barrier orders them before the MMAs
@@ -552,16 +566,17 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     // warp.  Every lane's TMEM loads have completed (wait::ld) and are ordered by
     // the tcgen05 fence; its shared-memory stores are made visible to the async
     // proxy (which the tensor core reads through) before the warp synchronises.
-    const uint32_t ed_lead = ptx::mapa_shared(bar(base, B_ED0), 0);
-    auto epi_done = [&](int h) {
+    auto arrive_lead = [&](int b) {
       ptx::tc_fence_before();
       ptx::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
-        if (leader) ptx::mbar_arrive(bar(base, B_ED0 + h));
-        else ptx::mbar_arrive_remote(ed_lead + 8u * (uint32_t)h);
+        if (leader) ptx::mbar_arrive(bar(base, b));
+        else ptx::mbar_arrive_remote(ptx::mapa_shared(bar(base, b), 0));
       }
     };
+    auto epi_done = [&](int h) { arrive_lead(B_ED0 + h); };
+    auto fl_done = [&]() { arrive_lead(B_FL0 + hg); };
     auto load_tile = [&](int it) {
       t = 2 * (cluster + it * nclusters) + (int)rank;
       if (t < ntiles) {
@@ -604,7 +619,38 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         }
         store8c(abuf, c0 + cc, o);
       }
-      epi_done(hg);
+      fl_done();
+    };
+    // With L = 4 and FP16 operands the next tile's h_1 is computed early, in the
+    // slack of the last reverse step, into this warp's z_2 stash columns (read by
+    // then); the tile tail copies it into the A buffer (TMEM -> shared memory, no
+    // arithmetic).  Measured: 1.4 % faster with FP16 operands, 1.7 % slower with
+    // BF16 ones, where the tile tail computes the first layer itself.
+    const bool early_h1 = kF16 && L == 4;
+    const uint32_t t_h1 = t_lane + 256 + (cw >> 1);
+    auto first_layer_tmem = [&]() {
+#pragma unroll 1
+      for (int cc = 0; cc < 64; cc += 16) {
+        uint32_t o[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const uint32_t u = first_layer_u2(s_w1p[(cw + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2);
+          const uint32_t tt = ptx::htanh2(u);
+          o[i] = to_operand<kF16>(ptx::hfma2(u, tt, u));
+        }
+        ptx::tmem_st8(t_h1 + cc / 2, o);
+      }
+      ptx::tmem_wait_st();
+    };
+    auto first_layer_copy = [&](int it) {
+      const uint32_t abuf = base + ((it & 1) ? kOffA1 : kOffA0);
+      uint32_t v[32];
+      ptx::tmem_ld16(t_h1, v);
+      ptx::tmem_ld16(t_h1 + 16, v + 16);
+      ptx::tmem_wait_ld();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) store8c(abuf, cw + 16 * q, v + 8 * q);
+      fl_done();
     };
 
     if (my_tiles > 0) {
@@ -613,6 +659,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     }
     float fpart = 0.f;  // sum of w_o s(z_L) over this thread's 64 columns
     for (int it = 0; it < my_tiles && ok; ++it) {
+      const int cur_wp = wp, cur_start = start, cur_len = len;
+      const bool h1_early = early_h1 && it + 1 < my_tiles;
       for (int s = 0; s < n_steps && ok; ++s) {
         const uint32_t obuf = base + (((it + s + 1) & 1) ? kOffA1 : kOffA0);
         {
@@ -726,14 +774,18 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
             }
             ptx::tmem_wait_st();
           }
+          if (h1_early && s == 2 * L - 4) {
+            // the z_2 stash columns of this warp have been read: the next tile's h_1
+            load_tile(it + 1);
+            first_layer_tmem();
+          }
         }
       }
       if (!ok) break;
 
       // ---- tile tail ------------------------------------------------------------
-      const int cur_wp = wp, cur_start = start, cur_len = len;
       if (it + 1 < my_tiles) {
-        load_tile(it + 1);
+        if (!h1_early) load_tile(it + 1);
         // the next tile's first layer overwrites the A buffer that the last reverse
         // step's chains read: the warps of half 0 have seen only their own chain
         // complete, so they wait for the half-1 chain (its commit follows every
@@ -742,7 +794,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
           if (!wait_epi_warp(bar(base, B_ACC0 + 1), (acc_n - 1u) & 1u, abort_flag, tw.err)) { ok = false; break; }
           ptx::tc_fence_after();
         }
-        first_layer(it + 1);
+        if (h1_early) first_layer_copy(it + 1);
+        else first_layer(it + 1);
       }
       // the input-Jacobian chain of this tile
       if (!wait_epi_warp(bar(base, B_ACCJ), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }

@@ -293,6 +293,29 @@ def test_deterministic_and_unaffected_by_other_work():
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_repeated_launches_are_bit_identical(prec):
+    """Many tiles per CTA (64 x 8,192 pairs = 4,096 tiles of 128 on 152 SMs): every
+    hand-off between the kernel's warps and between the two CTAs of a pair is
+    exercised at every tile boundary, so a missing wait shows as run-to-run noise
+    in the results of every mode."""
+    torch = need_gpu()
+    g = lib()
+    wl = synth.box_scene(n_waypoints=64, n_points=8192)
+    s = wl.shape
+    net = _net(g, s, wl.weights, prec)
+    q, p = to_dev(torch, wl.q), to_dev(torch, wl.p)
+    calls = [lambda: g.query(net, q, p)] + [
+        (lambda k=k, a=a: g.collision_cost(net, q, p, k, a))
+        for k, a in (("softmin", 0.02), ("min", 0.0), ("hinge", 0.05))]
+    for call in calls:
+        first = [x.cpu().numpy() for x in call()]
+        for _ in range(4):
+            again = [x.cpu().numpy() for x in call()]
+            for x, y in zip(first, again):
+                assert np.array_equal(x, y, equal_nan=True)
+
+
 def test_unsupported_shape_is_rejected():
     need_gpu()
     g = lib()
