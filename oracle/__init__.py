@@ -16,9 +16,13 @@ Contents
   robot    synthetic capsule robots, their signed distance f_s (Eq. 1) and
            the brute-force GCDF of Definition 1 over a sampled zero-level set
            (Eq. 8, second form), with the closed-form gradient of Theorem 1.
+  planner  the trajectory optimisation of Sec. IV-A (Eq. 10 with the velocity
+           controls eliminated, the l1 GCDF penalty of Eq. 12) as a fixed
+           number of Levenberg-Marquardt steps preconditioned by the
+           tridiagonal Hessian of the smooth terms (FP64 Cholesky).
   metrics  the relative-error measures used by every parity test.
 
 Every function states the passage it follows.  Parity pins live in
 ``tests/test_oracle_*.py``.
 """
-from . import mlp, reduce, robot, metrics  # noqa: F401
+from . import mlp, reduce, robot, metrics, planner  # noqa: F401
