@@ -62,7 +62,10 @@ enum gcdf_status {
   GCDF_EINVAL = 1,       /* bad shape, NULL or misaligned pointer, bad enum */
   GCDF_ENOMEM = 2,       /* device allocation failed */
   GCDF_ECUDA = 3,        /* a CUDA call or kernel launch failed */
-  GCDF_EUNSUPPORTED = 4  /* valid request this build does not implement */
+  GCDF_EUNSUPPORTED = 4, /* valid request this build does not implement */
+  GCDF_EAGAIN = 5,       /* planning server: the queue is full, try again later */
+  GCDF_PENDING = 6,      /* planning server: the request is not finished yet (poll only) */
+  GCDF_ETIMEOUT = 7      /* a device wait gave up (see gcdf_device_status) */
 };
 
 enum gcdf_precision {
@@ -212,6 +215,133 @@ GCDF_API int gcdf_device_status(gcdf_net *net, int *status);
  * Errors: EINVAL (net NULL, or exactly one event NULL).
  */
 GCDF_API int gcdf_set_profile_events(gcdf_net *net, void *start_event, void *stop_event);
+
+/* ---------------------------------------------------------------------------
+ * Trajectory optimisation with the GCDF collision cost (Sec. IV-A).
+ *
+ * Problem (Eq. 10 with the velocity controls eliminated through the
+ * integrator; the base velocity's norm is |q^t_{i+1} - q^t_i| / dt whatever the
+ * yaw, because a rotation keeps lengths): waypoints q_1 .. q_N, q_1 = q_start
+ * fixed, minimise
+ *   J = (1/dt^2) sum_{i<N} sum_d W_d (q_{i+1,d} - q_{i,d})^2        (control cost)
+ *     + w_goal |q_N - q_goal|^2                                      (tracking cost)
+ *     + mu sum_i sum_j max(0, delta - f(p_j, q_i))                   (l1 GCDF rows, Eq. 12)
+ * with W_d = w_trans for x, y and w_rot for the yaw and the arm joints.
+ * The paper solves its nonlinear program with an external SCP package; this
+ * library replaces it with a fixed number of Levenberg-Marquardt steps
+ * preconditioned by the exact Hessian A of the smooth terms (block-diagonal
+ * over DOFs, tridiagonal over waypoints):
+ *   (A_d + lambda diag(A_d)) s_d = g_d   (FP64 tridiagonal Cholesky, per DOF),
+ *   trial = q - s; accepted when it lowers J (lambda /= 2, floor lambda_min),
+ *   otherwise rejected (lambda *= 4, cap lambda_max).
+ * Each step costs one HINGE collision-cost evaluation of every waypoint over
+ * all points of its problem; the first evaluation is the initial guess (the
+ * straight line from q_start to q_goal).  J and every step are computed in
+ * FP64; the field is queried at the FP32 rounding of the trial.
+ * ------------------------------------------------------------------------- */
+
+typedef struct gcdf_plan_params {
+  float dt;              /* time step (> 0) */
+  float w_trans, w_rot;  /* control-cost weights (> 0) */
+  float w_goal;          /* tracking weight (>= 0) */
+  float mu;              /* penalty weight of the GCDF rows (>= 0) */
+  float delta;           /* safety margin of Eq. (11) */
+  float lambda0, lambda_min, lambda_max;  /* damping: start, floor, cap (>= 0) */
+  int iterations;        /* Levenberg-Marquardt steps (>= 0); iterations + 1 evaluations */
+} gcdf_plan_params;
+
+typedef struct gcdf_plan_problem {
+  int n_waypoints;       /* N >= 2 */
+  const float *q_start;  /* (n)      DEVICE */
+  const float *q_goal;   /* (n)      DEVICE */
+  const float *q_init;   /* (N, n)   DEVICE initial guess, or NULL for the straight line */
+  const float *points;   /* (M, 3)   DEVICE obstacle points of this problem */
+  int n_points;          /* M >= 0 */
+} gcdf_plan_problem;
+
+/*
+ * Optimise n_problems trajectories together with one net: every step is one
+ * batched collision-cost launch over all problems' (waypoint, point) pairs and
+ * one FP64 update launch (one block per problem).  Problems do not interact:
+ * each problem's result is bit-identical to solving it alone.
+ *   q_out     (sum_r N_r, n) DEVICE out: the final iterates, problems in order
+ *   merit_out (n_problems, iterations + 1) DEVICE out or NULL: J of the current
+ *             iterate after each evaluation
+ *   accepted_out (n_problems, iterations + 1) DEVICE out or NULL: 1 where the
+ *             evaluation's trial was accepted (always 1 for the first)
+ * Asynchronous on `stream`.  The problems' point arrays are copied into one
+ * temporary array first; the total pair count sum_r N_r M_r must stay below
+ * 2^31.  Errors: EINVAL (NULL or misaligned pointer, N < 2, bad parameter),
+ * ENOMEM, ECUDA.
+ */
+GCDF_API int gcdf_plan_solve(gcdf_net *net, const gcdf_plan_problem *problems, int n_problems,
+                             const gcdf_plan_params *params, float *q_out, double *merit_out,
+                             unsigned char *accepted_out, gcdf_stream_t stream);
+
+/*
+ * Planning server: a host thread that owns a CUDA stream on the device that
+ * was current at creation and runs the optimisation above for every admitted
+ * request, with continuous batching — requests that arrive while others are
+ * on the GPU are admitted at the next step boundary when a slot and enough of
+ * the device-memory budget are free, and every step processes all admitted
+ * requests (grouped by net) in the same launches.  Requests keep their place
+ * in the queue (first come, first admitted).  A request's result does not
+ * depend on what else runs with it.
+ */
+typedef struct gcdf_server gcdf_server;
+
+typedef struct gcdf_server_desc {
+  size_t hbm_budget_bytes;  /* device memory for admitted requests' points and state */
+  int max_active;           /* requests optimised together at most (>= 1) */
+  int max_queued;           /* submissions waiting for admission at most (>= 0) */
+  gcdf_plan_params params;  /* used for every request */
+} gcdf_server_desc;
+
+typedef struct gcdf_plan_request {
+  gcdf_net *net;            /* the robot's field; nets may differ between requests */
+  int n_waypoints;          /* N >= 2 */
+  const float *q_start;     /* (n)    HOST, copied at submission */
+  const float *q_goal;      /* (n)    HOST, copied at submission */
+  const float *points;      /* (M, 3) HOST, copied at submission */
+  int n_points;             /* M >= 0 */
+} gcdf_plan_request;
+
+typedef struct gcdf_plan_result {
+  float *q;                 /* (N, n) HOST, caller-provided: receives the final iterate */
+  double merit;             /* out: J of the final iterate */
+  int accepted_steps;       /* out: accepted trials */
+  double submit_s, admit_s, done_s;  /* out: server clock (seconds) at submission,
+                                        admission and completion */
+} gcdf_plan_result;
+
+/* Device bytes a request of this size counts against the server's budget
+ * while admitted (its points, optimiser state, its rows of the step arrays and
+ * the fused pass's temporaries).  0 for a NULL net or negative sizes. */
+GCDF_API size_t gcdf_plan_request_bytes(gcdf_net *net, int n_waypoints, int n_points);
+
+/* Start a server.  Errors: EINVAL (bad descriptor), ENOMEM, ECUDA. */
+GCDF_API int gcdf_server_create(const gcdf_server_desc *desc, gcdf_server **out);
+
+/*
+ * Queue a request (non-blocking; the inputs are copied).  *ticket identifies
+ * it.  Errors: EAGAIN (max_queued requests already waiting), EINVAL (bad
+ * request, or one that alone needs more than the budget), ECUDA.
+ */
+GCDF_API int gcdf_plan_submit(gcdf_server *server, const gcdf_plan_request *request, uint64_t *ticket);
+
+/*
+ * GCDF_OK and the result (the ticket is then retired) when the request is
+ * finished; GCDF_PENDING while it waits or runs; EINVAL for an unknown ticket;
+ * ECUDA or ETIMEOUT when the server's device work failed.
+ */
+GCDF_API int gcdf_plan_poll(gcdf_server *server, uint64_t ticket, gcdf_plan_result *result);
+
+/* Server clock in seconds (the clock of gcdf_plan_result). */
+GCDF_API double gcdf_server_clock(gcdf_server *server);
+
+/* Stop the server thread (after the step in progress) and free its memory.
+ * Unfinished requests are dropped.  NULL is a no-op. */
+GCDF_API int gcdf_server_destroy(gcdf_server *server);
 
 /* Message for the last error returned on the calling thread ("" if none). */
 GCDF_API const char *gcdf_last_error(void);

@@ -8,6 +8,8 @@ library's CUDA kernels; if the library is not built, the first call raises.
     net = create_net(n_dof=9, hidden=256, n_layers=4, weights=w, precision="bf16")
     f, g = query(net, q, p)                       # per-pair f and df/dq (Eq. 14, 15)
     c, g, a = collision_cost(net, q, p, "softmin", 0.02)
+    q_opt, merit, acc = plan_solve(net, [problem, ...], PlanParams())   # Sec. IV-A optimiser
+    server = Server(budget_bytes, max_active, max_queued, PlanParams())  # continuous batching
 """
 from __future__ import annotations
 
@@ -160,3 +162,105 @@ def last_error() -> str:
     """gcdf_last_error."""
     m = _lib.load().gcdf_last_error()
     return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------------------
+# Trajectory optimisation (gcdf_plan_solve) and the planning server
+# ---------------------------------------------------------------------------
+
+class PlanParams:
+    """gcdf_plan_params: cost weights, margin, damping and step count."""
+
+    def __init__(self, dt=0.1, w_trans=1.0, w_rot=0.5, w_goal=100.0, mu=1.0, delta=0.05,
+                 lambda0=1.0, lambda_min=1e-6, lambda_max=1e8, iterations=50):
+        self.dt, self.w_trans, self.w_rot, self.w_goal = dt, w_trans, w_rot, w_goal
+        self.mu, self.delta, self.iterations = mu, delta, iterations
+        self.lambda0, self.lambda_min, self.lambda_max = lambda0, lambda_min, lambda_max
+
+    def c(self):
+        return _lib.PlanParams(self.dt, self.w_trans, self.w_rot, self.w_goal, self.mu, self.delta,
+                               self.lambda0, self.lambda_min, self.lambda_max, int(self.iterations))
+
+
+def plan_solve(net: Net, problems, params: PlanParams, history: bool = True, stream=None):
+    """gcdf_plan_solve.  problems: list of dicts with CUDA tensors q_start (n,),
+    q_goal (n,), points (M, 3) and optional q_init (N, n), plus n_waypoints.
+    Returns q (sum N, n) and, with history, merit (R, iters + 1) FP64 and
+    accepted (R, iters + 1) uint8."""
+    lib = _lib.load()
+    R = len(problems)
+    arr = (_lib.PlanProblem * max(R, 1))()
+    rows = 0
+    for r, pr in enumerate(problems):
+        pts = pr["points"]
+        arr[r] = _lib.PlanProblem(int(pr["n_waypoints"]), _ptr(pr["q_start"], name="q_start"),
+                                  _ptr(pr["q_goal"], name="q_goal"), _ptr(pr.get("q_init"), name="q_init"),
+                                  _ptr(pts, name="points") if pts.shape[0] > 0 else None, int(pts.shape[0]))
+        rows += int(pr["n_waypoints"])
+    dev = problems[0]["q_start"].device if R else torch.device("cuda")
+    q = torch.empty(rows, net.n_dof, device=dev, dtype=torch.float32)
+    merit = acc = None
+    if history:
+        merit = torch.empty(R, params.iterations + 1, device=dev, dtype=torch.float64)
+        acc = torch.empty(R, params.iterations + 1, device=dev, dtype=torch.uint8)
+    prm = params.c()
+    _lib.check(lib.gcdf_plan_solve(net.handle, arr, R, ctypes.byref(prm), _ptr(q, name="q_out"),
+                                   None if merit is None else merit.data_ptr(),
+                                   None if acc is None else acc.data_ptr(), _stream(stream)))
+    return q, merit, acc
+
+
+def plan_request_bytes(net: Net, n_waypoints: int, n_points: int) -> int:
+    """gcdf_plan_request_bytes: what one request counts against a server's budget."""
+    return int(_lib.load().gcdf_plan_request_bytes(net.handle, int(n_waypoints), int(n_points)))
+
+
+class Server:
+    """gcdf_server_*: planning requests in, optimised trajectories out, with
+    continuous batching on the device that is current at construction."""
+
+    def __init__(self, budget_bytes: int, max_active: int, max_queued: int, params: PlanParams):
+        self._lib = _lib.load()
+        d = _lib.ServerDesc(int(budget_bytes), int(max_active), int(max_queued), params.c())
+        h = ctypes.c_void_p()
+        _lib.check(self._lib.gcdf_server_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self._shapes = {}
+
+    def submit(self, net: Net, n_waypoints: int, q_start, q_goal, points) -> int:
+        """gcdf_plan_submit with host arrays; returns the ticket, or raises
+        GcdfError with code GCDF_EAGAIN when the queue is full."""
+        qs = np.ascontiguousarray(np.asarray(q_start, dtype=np.float32))
+        qg = np.ascontiguousarray(np.asarray(q_goal, dtype=np.float32))
+        pts = np.ascontiguousarray(np.asarray(points, dtype=np.float32).reshape(-1, 3))
+        rq = _lib.PlanRequest(net.handle, int(n_waypoints), qs.ctypes.data, qg.ctypes.data,
+                              pts.ctypes.data if pts.shape[0] else None, int(pts.shape[0]))
+        t = ctypes.c_uint64(0)
+        _lib.check(self._lib.gcdf_plan_submit(self.handle, ctypes.byref(rq), ctypes.byref(t)))
+        self._shapes[t.value] = (int(n_waypoints), net.n_dof)
+        return t.value
+
+    def poll(self, ticket: int):
+        """gcdf_plan_poll: None while pending, else a dict with q (N, n),
+        merit, accepted_steps and the server-clock times."""
+        N, n = self._shapes[ticket]
+        q = np.empty((N, n), dtype=np.float32)
+        res = _lib.PlanResult(q.ctypes.data, 0.0, 0, 0.0, 0.0, 0.0)
+        rc = self._lib.gcdf_plan_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(res))
+        if rc == _lib.GCDF_PENDING:
+            return None
+        _lib.check(rc)
+        del self._shapes[ticket]
+        return {"q": q, "merit": res.merit, "accepted_steps": res.accepted_steps,
+                "submit_s": res.submit_s, "admit_s": res.admit_s, "done_s": res.done_s}
+
+    def clock(self) -> float:
+        return float(self._lib.gcdf_server_clock(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            self._lib.gcdf_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        self.close()

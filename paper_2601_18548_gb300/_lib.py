@@ -12,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgcdf.so")
 
 GCDF_OK, GCDF_EINVAL, GCDF_ENOMEM, GCDF_ECUDA, GCDF_EUNSUPPORTED = 0, 1, 2, 3, 4
+GCDF_EAGAIN, GCDF_PENDING, GCDF_ETIMEOUT = 5, 6, 7
 GCDF_FP32, GCDF_BF16, GCDF_FP16 = 0, 1, 2
 GCDF_RED_MIN, GCDF_RED_SOFTMIN, GCDF_RED_HINGE = 0, 1, 2
 
@@ -25,6 +26,31 @@ class NetDesc(ctypes.Structure):
     _fields_ = [("n_dof", _i), ("hidden", _i), ("n_hidden_layers", _i), ("precision", _i)]
 
 
+class PlanParams(ctypes.Structure):
+    _fields_ = [("dt", _f), ("w_trans", _f), ("w_rot", _f), ("w_goal", _f), ("mu", _f), ("delta", _f),
+                ("lambda0", _f), ("lambda_min", _f), ("lambda_max", _f), ("iterations", _i)]
+
+
+class PlanProblem(ctypes.Structure):
+    _fields_ = [("n_waypoints", _i), ("q_start", _vp), ("q_goal", _vp), ("q_init", _vp),
+                ("points", _vp), ("n_points", _i)]
+
+
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_active", _i), ("max_queued", _i),
+                ("params", PlanParams)]
+
+
+class PlanRequest(ctypes.Structure):
+    _fields_ = [("net", _vp), ("n_waypoints", _i), ("q_start", _vp), ("q_goal", _vp),
+                ("points", _vp), ("n_points", _i)]
+
+
+class PlanResult(ctypes.Structure):
+    _fields_ = [("q", _vp), ("merit", ctypes.c_double), ("accepted_steps", _i),
+                ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
 SIGNATURES = {
     "gcdf_weight_count": (ctypes.c_size_t, [ctypes.POINTER(NetDesc)]),
     "gcdf_create_net": (_i, [ctypes.POINTER(NetDesc), _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
@@ -34,6 +60,13 @@ SIGNATURES = {
     "gcdf_collision_cost_noalloc": (_i, [_vp, _vp, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _f, _vp, _vp, _vp, _vp]),
     "gcdf_device_status": (_i, [_vp, ctypes.POINTER(_i)]),
     "gcdf_set_profile_events": (_i, [_vp, _vp, _vp]),
+    "gcdf_plan_solve": (_i, [_vp, ctypes.POINTER(PlanProblem), _i, ctypes.POINTER(PlanParams), _vp, _vp, _vp, _vp]),
+    "gcdf_server_create": (_i, [ctypes.POINTER(ServerDesc), ctypes.POINTER(_vp)]),
+    "gcdf_plan_submit": (_i, [_vp, ctypes.POINTER(PlanRequest), ctypes.POINTER(ctypes.c_uint64)]),
+    "gcdf_plan_poll": (_i, [_vp, ctypes.c_uint64, ctypes.POINTER(PlanResult)]),
+    "gcdf_server_clock": (ctypes.c_double, [_vp]),
+    "gcdf_plan_request_bytes": (ctypes.c_size_t, [_vp, _i, _i]),
+    "gcdf_server_destroy": (_i, [_vp]),
     "gcdf_last_error": (ctypes.c_char_p, []),
 }
 

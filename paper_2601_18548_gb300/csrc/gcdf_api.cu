@@ -254,7 +254,82 @@ int run(gcdf_net* net, WorkDesc& w, const float* shift, Temps& tmp, cudaStream_t
   return GCDF_OK;
 }
 
+// Fused pass plus per-waypoint merge for a validated WorkDesc (mode, param set).
+int reduce_call(gcdf_net* net, WorkDesc& w, const float* shift, float* cost, float* grad, int* argmin,
+                cudaStream_t s) {
+  Temps tmp(s);
+  cudaError_t e;
+  Partial* parts = nullptr;
+  if ((e = tmp.get((void**)&parts, (size_t)(w.n_tiles > 0 ? w.n_tiles : 1) * sizeof(Partial))))
+    return cuda_fail(e, "cudaMallocAsync");
+  w.partials = parts;
+  if (w.n_pairs > 0) {
+    const int rc = run(net, w, shift, tmp, s);
+    if (rc) return rc;
+  } else if (w.offsets) {
+    // every list is empty: the merge sees no tiles
+    int* ts = nullptr;
+    if ((e = tmp.get((void**)&ts, (size_t)(w.N + 1) * sizeof(int)))) return cuda_fail(e, "cudaMallocAsync");
+    if ((e = launch_tile_map(w.offsets, w.N, w.tile, ts, s))) return cuda_fail(e, "tile map launch");
+    w.tile_start = ts;
+  } else {
+    w.tiles_per_wp = 0;
+  }
+  if ((e = launch_merge(w, w.N, cost, grad, argmin, s))) return cuda_fail(e, "merge launch");
+  return GCDF_OK;
+}
+
 }  // namespace
+
+namespace gcdf {
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+int net_n_dof(const gcdf_net* net) { return net->n_dof; }
+int net_device(const gcdf_net* net) { return net->device; }
+
+// Device temporaries of the fused pass per waypoint row with M points: the
+// first-layer term, the sines and cosines, the tile prefix and the partial
+// records of its tiles.
+size_t net_step_bytes_per_row(const gcdf_net* net, int M) {
+  const int tile = net->precision == GCDF_FP32 ? fp32_tile_pairs(net->H) : tc_tile_pairs();
+  const size_t tiles = (size_t)(M + tile - 1) / tile + 1;
+  return (size_t)net->H * 4 + (size_t)2 * (net->n_dof - 2) * 4 + 4 + tiles * sizeof(Partial);
+}
+
+// Collision cost over range lists: waypoint i uses points point_base[i] ..
+// point_base[i] + (offsets[i+1] - offsets[i]) - 1 of p (no index array).
+int collision_ranges(gcdf_net* net, const float* q, int N, const float* p, int M, const int* offsets,
+                     const int* point_base, int n_pairs, int reduction, float param, float* cost,
+                     float* grad, cudaStream_t s) {
+  if (N == 0) return GCDF_OK;
+  WorkDesc w;
+  memset(&w, 0, sizeof(w));
+  w.q = q;
+  w.p = p;
+  w.offsets = offsets;
+  w.point_base = point_base;
+  w.N = N;
+  w.M = M;
+  w.n_pairs = n_pairs;
+  w.n_dof = net->n_dof;
+  w.n_ang = net->n_dof - 2;
+  w.tile = net->precision == GCDF_FP32 ? fp32_tile_pairs(net->H) : tc_tile_pairs();
+  w.n_tiles = (int)(((long long)n_pairs + w.tile - 1) / w.tile + N);
+  w.mode = reduction;
+  w.param = param;
+  return reduce_call(net, w, nullptr, cost, grad, nullptr, s);
+}
+
+}  // namespace gcdf
 
 extern "C" {
 
@@ -351,26 +426,8 @@ int gcdf_collision_cost(gcdf_net* net, const float* q, int N, const float* p, in
   if (argmin && !aligned16(argmin)) return fail(GCDF_EINVAL, "argmin not 16-byte aligned");
   w.mode = reduction;
   w.param = param;
-  cudaStream_t s = (cudaStream_t)stream;
-  Temps tmp(s);
-  cudaError_t e;
-  Partial* parts = nullptr;
-  if ((e = tmp.get((void**)&parts, (size_t)(w.n_tiles > 0 ? w.n_tiles : 1) * sizeof(Partial))))
-    return cuda_fail(e, "cudaMallocAsync");
-  w.partials = parts;
-  if (w.n_pairs > 0) {
-    rc = run(net, w, shift, tmp, s);
-    if (rc) return rc;
-  } else if (part_offsets) {
-    // every list is empty: the merge sees no tiles
-    int* ts = nullptr;
-    if ((e = tmp.get((void**)&ts, (size_t)(N + 1) * sizeof(int)))) return cuda_fail(e, "cudaMallocAsync");
-    if ((e = launch_tile_map(part_offsets, N, w.tile, ts, s))) return cuda_fail(e, "tile map launch");
-    w.tile_start = ts;
-  } else {
-    w.tiles_per_wp = 0;
-  }
-  if ((e = launch_merge(w, N, cost, grad, argmin, s))) return cuda_fail(e, "merge launch");
+  rc = reduce_call(net, w, shift, cost, grad, argmin, (cudaStream_t)stream);
+  if (rc) return rc;
   g_err[0] = 0;
   return GCDF_OK;
 }

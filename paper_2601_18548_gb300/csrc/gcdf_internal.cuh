@@ -39,6 +39,8 @@ struct WorkDesc {
   const float* p;        // (M, 3)
   const int* offsets;    // (N + 1) or nullptr (dense)
   const int* idx;        // (n_pairs) or nullptr
+  const int* point_base; // range lists (internal): with offsets and no idx, list position r
+                         // of waypoint i is point point_base[i] + r
   const float* A;        // (N, H) first-layer waypoint term, from the prep kernel
   const float* trig;     // (N, 2 * n_ang): sin, cos of every angle, from the prep kernel
   const int* tile_start; // (N + 1) tile prefix (CSR); nullptr for dense
@@ -82,7 +84,7 @@ __device__ __forceinline__ void pair_at(const WorkDesc& w, int wp, int pos, int&
     k = (long long)wp * w.M + pos;
   } else {
     k = (long long)w.offsets[wp] + pos;
-    j = w.idx[k];
+    j = w.idx ? w.idx[k] : w.point_base[wp] + pos;
   }
 }
 
