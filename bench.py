@@ -9,6 +9,8 @@ value+gradient pairs reduced to 128 costs and gradients.  Inputs are synthetic
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the same workload
+    python bench.py --serve                 # served-planning latency (see run_serve)
+    python bench.py --plan [--plan-problems P]   # batched trajectory optimisation (see run_plan)
 
 Multi-GPU: one process per GPU (torchrun); every rank runs its own replica of
 the workload (weak scaling, no collective on the data path); the time is the
@@ -371,6 +373,193 @@ def run_gpu(args):
     return 0
 
 
+def _serve_requests(rng, pools, rate, duration, h_rng, m_rng):
+    """Poisson arrivals over `duration` seconds: (arrival, n_dof, N, points, q_start, q_goal)."""
+    out, t = [], 0.0
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t > duration:
+            return out
+        n = 9 if rng.random() < 0.5 else 10
+        pts = pools[n][int(rng.integers(len(pools[n])))]
+        N = int(rng.integers(h_rng[0], h_rng[1] + 1))
+        M = int(rng.integers(m_rng[0], m_rng[1] + 1))
+        sm = synth.SplitMix64(int(rng.integers(1 << 62)))
+        qs = synth.random_config(sm, n, -5.0, 5.0).astype(np.float32)
+        qg = synth.random_config(sm, n, -5.0, 5.0).astype(np.float32)
+        out.append((t, n, N, pts[:M], qs, qg))
+
+
+def _lat(lat, span, done, rejected):
+    lat = np.asarray(lat)
+    return {"completed": int(done), "rejected": int(rejected),
+            "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+            "throughput_rps": float(done / span) if span > 0 else None}
+
+
+def _run_server(g, nets, params, reqs, budget, max_active, max_queued):
+    """Replay the arrivals against a planning server; latency = done - submit (server clock)."""
+    srv = g.Server(budget, max_active, max_queued, params)
+    pending, lat, rejected, first, last = {}, [], 0, None, 0.0
+    t0 = time.perf_counter()
+    i = 0
+    try:
+        while i < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and reqs[i][0] <= now:
+                _, n, N, pts, qs, qg = reqs[i]
+                try:
+                    pending[srv.submit(nets[n], N, qs, qg, pts)] = True
+                except g.GcdfError as e:
+                    if e.code != 5:  # GCDF_EAGAIN: shed
+                        raise
+                    rejected += 1
+                i += 1
+            for tk in list(pending):
+                r = srv.poll(tk)
+                if r is not None:
+                    del pending[tk]
+                    lat.append(r["done_s"] - r["submit_s"])
+                    first = r["submit_s"] if first is None else min(first, r["submit_s"])
+                    last = max(last, r["done_s"])
+            time.sleep(0.0005)
+    finally:
+        srv.close()
+    return _lat(lat, last - (first or 0.0), len(lat), rejected)
+
+
+def _run_sequential(g, torch, nets, params, reqs):
+    """The plain per-request path: one gcdf_plan_solve at a time in arrival
+    order (FIFO); each request's service time is measured, its latency is
+    its completion minus its arrival."""
+    clock, lat = 0.0, []
+    for (t, n, N, pts, qs, qg) in reqs:
+        prob = {"n_waypoints": N, "q_start": torch.from_numpy(qs).cuda(), "q_goal": torch.from_numpy(qg).cuda(),
+                "points": torch.from_numpy(np.ascontiguousarray(pts)).cuda()}
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        g.plan_solve(nets[n], [prob], params, history=False)
+        torch.cuda.synchronize()
+        svc = time.perf_counter() - s0
+        clock = max(clock, t) + svc
+        lat.append(clock - t)
+    return _lat(lat, clock - reqs[0][0], len(reqs), 0)
+
+
+def run_serve(args):
+    """Served planning: Poisson arrivals of trajectory-optimisation requests of
+    uneven horizon and point-cloud size, 9- and 10-DOF robots, 50 optimiser
+    steps each.  (A) a mix both paths can finish, the continuously batched
+    BF16 server against the plain FP32 (and BF16) per-request paths; (C) many
+    small requests, where one request at a time is bound by its launches; (B) the
+    offered load of 2,000 requests/s at the full request sizes, which no path
+    sustains on one GPU: served with a bounded queue, shed requests counted."""
+    import torch
+    import paper_2601_18548_gb300 as g
+    params = g.PlanParams(iterations=50)
+    nets = {p: {} for p in ("bf16", "fp32")}
+    for n in (9, 10):
+        shape = synth.NetShape(n, 256, 4)
+        w = synth.he_uniform_weights(shape, seed=0)
+        for p in nets:
+            nets[p][n] = g.create_net(n, 256, 4, w, p)
+    pools = {n: [synth.box_scene(n_waypoints=2, n_points=65536, seed_scene=300 + k, n_dof=n).p.astype(np.float32)
+                 for k in range(4)] for n in (9, 10)}
+    rng = np.random.default_rng(7)
+    reqs_a = _serve_requests(rng, pools, rate=args.serve_rate, duration=args.serve_seconds,
+                             h_rng=(32, 128), m_rng=(1000, 8000))
+    # warm-up: one request through each path
+    _run_sequential(g, torch, nets["bf16"], params, reqs_a[:1])
+    _run_sequential(g, torch, nets["fp32"], params, reqs_a[:1])
+    budget = 120 << 30
+    served = _run_server(g, nets["bf16"], params, reqs_a, budget, 64, 256)
+    fp32_seq = _run_sequential(g, torch, nets["fp32"], params, reqs_a)
+    bf16_seq = _run_sequential(g, torch, nets["bf16"], params, reqs_a)
+    # (C) many small requests: the per-request path is bound by its launches
+    reqs_c = _serve_requests(np.random.default_rng(9), pools, rate=150.0, duration=1.0,
+                             h_rng=(32, 64), m_rng=(500, 2000))
+    served_c = _run_server(g, nets["bf16"], params, reqs_c, budget, 64, 1024)
+    bf16_seq_c = _run_sequential(g, torch, nets["bf16"], params, reqs_c)
+    fp32_seq_c = _run_sequential(g, torch, nets["fp32"], params, reqs_c)
+    reqs_b = _serve_requests(np.random.default_rng(8), pools, rate=2000.0, duration=args.overload_seconds,
+                             h_rng=(32, 256), m_rng=(1000, 65536))
+    overload = _run_server(g, nets["bf16"], params, reqs_b, budget, 64, 64)
+    overload["offered"] = len(reqs_b)
+    line = {
+        "metric": "served plan p50/p99 latency and throughput", "unit": "s / requests per s",
+        "n_gpus": 1, "data": "synthetic",
+        "config": {"arrivals": "Poisson", "steps_per_request": 50, "robots": "9- and 10-DOF, 4 x 256 SiLU",
+                   "budget_bytes": budget,
+                   "mix_A": {"rate_rps": args.serve_rate, "seconds": args.serve_seconds, "requests": len(reqs_a),
+                             "horizon": [32, 128], "points": [1000, 8000]},
+                   "small_C": {"rate_rps": 150.0, "seconds": 1.0, "requests": len(reqs_c), "horizon": [32, 64],
+                               "points": [500, 2000]},
+                   "overload_B": {"rate_rps": 2000.0, "seconds": args.overload_seconds, "horizon": [32, 256],
+                                  "points": [1000, 65536], "max_active": 64, "max_queued": 64}},
+        "A_served_bf16_continuous_batching": served,
+        "A_per_request_fp32": fp32_seq,
+        "A_per_request_bf16": bf16_seq,
+        "C_served_bf16_continuous_batching": served_c,
+        "C_per_request_bf16": bf16_seq_c,
+        "C_per_request_fp32": fp32_seq_c,
+        "B_served_bf16_overload": overload,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_plan(args):
+    """Batched trajectory optimisation: `--plan-problems` problems with horizons
+    uniform in [32, 256] and point clouds uniform in [1k, 64k] from seeded box
+    scenes, half 9-DOF and half 10-DOF robots (one gcdf_plan_solve per net),
+    50 steps each (51 HINGE collision passes).  Timed with CUDA events around
+    the two calls; inputs resident on the device."""
+    import torch
+    import paper_2601_18548_gb300 as g
+    params = g.PlanParams(iterations=50)
+    rng = np.random.default_rng(11)
+    batches, pairs = [], 0
+    for n in (9, 10):
+        shape = synth.NetShape(n, 256, 4)
+        net = g.create_net(n, 256, 4, synth.he_uniform_weights(shape, seed=0), args.precision)
+        pool = [synth.box_scene(n_waypoints=2, n_points=65536, seed_scene=400 + k, n_dof=n).p.astype(np.float32)
+                for k in range(4)]
+        probs = []
+        for _ in range(args.plan_problems // 2):
+            N = int(rng.integers(32, 257))
+            M = int(rng.integers(1000, 65537))
+            sm = synth.SplitMix64(int(rng.integers(1 << 62)))
+            qs = torch.from_numpy(synth.random_config(sm, n, -5.0, 5.0).astype(np.float32)).cuda()
+            qg = torch.from_numpy(synth.random_config(sm, n, -5.0, 5.0).astype(np.float32)).cuda()
+            pts = torch.from_numpy(np.ascontiguousarray(pool[int(rng.integers(4))][:M])).cuda()
+            probs.append({"n_waypoints": N, "q_start": qs, "q_goal": qg, "points": pts})
+            pairs += N * M
+        batches.append((net, probs))
+    warm = g.PlanParams(iterations=1)
+    for net, probs in batches:
+        g.plan_solve(net, probs[:2], warm, history=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for net, probs in batches:
+        q, merit, acc = g.plan_solve(net, probs, params)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    evals = params.iterations + 1
+    n_prob = sum(len(p) for _, p in batches)
+    fpp = flops_per_pair(synth.NetShape(9, 256, 4))
+    line = {"metric": "batched trajectory optimisation", "unit": "problems/s",
+            "value": n_prob / sec, "n_gpus": 1, "dtype": args.precision, "data": "synthetic",
+            "config": {"problems": n_prob, "horizon": [32, 256], "points": [1000, 65536], "robots": "9/10-DOF",
+                       "steps": params.iterations, "evaluations": evals},
+            "seconds": sec, "pairs_per_evaluation": pairs, "pairs_per_s": pairs * evals / sec,
+            "tflops_collision": pairs * evals * fpp / sec / 1e12}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -383,11 +572,21 @@ def main():
     ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch from ncu")
     ap.add_argument("--waypoints", type=int, default=128, help="smaller scenes for profiling only")
     ap.add_argument("--points", type=int, default=16384, help="smaller scenes for profiling only")
+    ap.add_argument("--serve", action="store_true", help="served-planning latency benchmark instead")
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--overload-seconds", type=float, default=1.0)
+    ap.add_argument("--plan", action="store_true", help="batched trajectory-optimisation benchmark instead")
+    ap.add_argument("--plan-problems", type=int, default=64)
     args = ap.parse_args()
     global WAYPOINTS, POINTS
     WAYPOINTS, POINTS = args.waypoints, args.points
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.serve:
+        return run_serve(args)
+    if args.plan:
+        return run_plan(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

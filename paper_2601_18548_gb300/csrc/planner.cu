@@ -12,7 +12,7 @@
 //   off-diagonal  -2 W_d / dt^2,
 // so the damped system (A_d + lambda diag A_d) s = g is solved per DOF by a
 // tridiagonal Cholesky factorisation (one thread per DOF, sequential over
-// the waypoints, FP64).
+// the waypoints, FP64, reciprocal pivots from rsqrt).
 #include <cstring>
 #include <vector>
 
@@ -32,6 +32,7 @@ int collision_ranges(gcdf_net* net, const float* q, int N, const float* p, int M
 namespace {
 
 constexpr int kUpdThreads = 128;
+constexpr int kChunk = 64;  // rows per shared-memory chunk of the tridiagonal solve
 
 // Sum over the block in a fixed tree (deterministic for a fixed block size).
 __device__ double block_sum(double v, double* red) {
@@ -156,39 +157,78 @@ __global__ void __launch_bounds__(kUpdThreads) plan_update_kernel(const PlanTraj
   }
   __syncthreads();
 
-  // next trial: per DOF, (A_d (1 + lambda)) s = g over q_2 .. q_N
-  if (t < n) {
-    const int d = t;
-    const double W = d < 2 ? c.w_trans : c.w_rot;
-    const double sc = 1.0 + s_lam;
-    const double dint = 4.0 * c.dt2inv * W * sc;
-    const double dlast = (2.0 * c.dt2inv * W + 2.0 * c.w_goal) * sc;
-    const double off = -2.0 * c.dt2inv * W;
-    const int m = N - 1;
-    // forward: l_i, y_i (y kept in Qt, l in Ls), rows 1 .. N-1
-    double lp = 0.0, yp = 0.0;
-    for (int i = 0; i < m; ++i) {
-      const double di = (i + 1 == m) ? dlast : dint;
-      const double e = (i == 0) ? 0.0 : off / lp;
-      const double l = sqrt(di - e * e);
-      const double y = (G[(size_t)(i + 1) * n + d] - e * yp) / l;
-      Ls[(size_t)(i + 1) * n + d] = l;
-      Qt[(size_t)(i + 1) * n + d] = y;
-      lp = l;
-      yp = y;
+  // next trial: per DOF, (A_d (1 + lambda)) s = g over q_2 .. q_N by the
+  // Cholesky factor with reciprocal pivots r_i = 1 / l_i (one rsqrt per row, no
+  // divisions).  The rows go through shared memory in chunks loaded by the
+  // whole block, so the per-DOF recurrences never wait on a global load.
+  __shared__ double sg[kChunk][kMaxDof], sy[kChunk][kMaxDof], sr[kChunk][kMaxDof];
+  const int d = t;
+  const double W = d < 2 ? c.w_trans : c.w_rot;
+  const double sc = 1.0 + s_lam;
+  const double dint = 4.0 * c.dt2inv * W * sc;
+  const double dlast = (2.0 * c.dt2inv * W + 2.0 * c.w_goal) * sc;
+  const double off = -2.0 * c.dt2inv * W;
+  const int m = N - 1;  // unknown rows 1 .. N-1
+  // forward: l_i^2 = d_i - e_i^2, e_i = off r_{i-1};  y_i = (g_i - e_i y_{i-1}) r_i
+  double rp = 0.0, yp = 0.0;
+  for (int c0 = 0; c0 < m; c0 += kChunk) {
+    const int cl = min(kChunk, m - c0);
+    for (int e = t; e < cl * n; e += kUpdThreads) {
+      const int i = e / n, dd = e - i * n;
+      sg[i][dd] = G[(size_t)(c0 + i + 1) * n + dd];
     }
-    // backward: x_i = (y_i - e_{i+1} x_{i+1}) / l_i with e_{i+1} = off / l_i
-    double xn = 0.0;
-    for (int i = m - 1; i >= 0; --i) {
-      const size_t r = (size_t)(i + 1) * n + d;
-      const double l = Ls[r];
-      const double x = (i + 1 == m) ? Qt[r] / l : (Qt[r] - (off / l) * xn) / l;
-      xn = x;
-      const double v = Qm[r] - x;
+    __syncthreads();
+    if (d < n) {
+      for (int i = 0; i < cl; ++i) {
+        const int gi = c0 + i;
+        const double di = (gi + 1 == m) ? dlast : dint;
+        const double e = (gi == 0) ? 0.0 : off * rp;
+        const double r = rsqrt(fma(-e, e, di));
+        const double y = fma(-e, yp, sg[i][d]) * r;
+        sr[i][d] = r;
+        sy[i][d] = y;
+        rp = r;
+        yp = y;
+      }
+    }
+    __syncthreads();
+    for (int e = t; e < cl * n; e += kUpdThreads) {
+      const int i = e / n, dd = e - i * n;
+      Ls[(size_t)(c0 + i + 1) * n + dd] = sr[i][dd];
+      Qt[(size_t)(c0 + i + 1) * n + dd] = sy[i][dd];
+    }
+    __syncthreads();
+  }
+  // backward: x_i = (y_i - e_{i+1} x_{i+1}) r_i with e_{i+1} = off r_i; trial = q - x
+  double xn = 0.0;
+  for (int c1 = m; c1 > 0; c1 -= kChunk) {
+    const int c0 = max(0, c1 - kChunk), cl = c1 - c0;
+    for (int e = t; e < cl * n; e += kUpdThreads) {
+      const int i = e / n, dd = e - i * n;
+      sr[i][dd] = Ls[(size_t)(c0 + i + 1) * n + dd];
+      sy[i][dd] = Qt[(size_t)(c0 + i + 1) * n + dd];
+    }
+    __syncthreads();
+    if (d < n) {
+      for (int i = cl - 1; i >= 0; --i) {
+        const double r = sr[i][d];
+        const double x = (c0 + i + 1 == m) ? sy[i][d] * r : fma(-off * r, xn, sy[i][d]) * r;
+        sy[i][d] = x;
+        xn = x;
+      }
+    }
+    __syncthreads();
+    for (int e = t; e < cl * n; e += kUpdThreads) {
+      const int i = e / n, dd = e - i * n;
+      const size_t r = (size_t)(c0 + i + 1) * n + dd;
+      const double v = Qm[r] - sy[i][dd];
       Qt[r] = v;
       Qf[r] = (float)v;
       Qs[r] = (float)v;
     }
+    __syncthreads();
+  }
+  if (d < n) {
     Qt[d] = Qm[d];
     Qf[d] = (float)Qm[d];
     Qs[d] = (float)Qm[d];
@@ -287,36 +327,19 @@ struct Scratch {
 
 }  // namespace
 
-extern "C" int gcdf_plan_solve(gcdf_net* net, const gcdf_plan_problem* problems, int n_problems,
-                               const gcdf_plan_params* params, float* q_out, double* merit_out,
-                               unsigned char* accepted_out, gcdf_stream_t stream) {
-  if (!net) return set_error(GCDF_EINVAL, "net is NULL");
-  int rc = check_plan_params(params);
-  if (rc) return rc;
-  if (n_problems < 0 || (n_problems > 0 && !problems)) return set_error(GCDF_EINVAL, "bad problem list");
-  if (n_problems == 0) { clear_error(); return GCDF_OK; }
-  if (!q_out || !al16(q_out)) return set_error(GCDF_EINVAL, "q_out NULL or not 16-byte aligned");
-  if ((merit_out == nullptr) != (accepted_out == nullptr))
-    return set_error(GCDF_EINVAL, "give both merit_out and accepted_out or neither");
-  int dev = -1;
-  cudaGetDevice(&dev);
-  if (dev != net_device(net)) return set_error(GCDF_EINVAL, "net belongs to device %d, current device is %d",
-                                               net_device(net), dev);
+namespace {
+
+// Problems [0, n_problems) of a batch whose pair count fits one collision pass.
+int solve_chunk(gcdf_net* net, const gcdf_plan_problem* problems, int n_problems, const gcdf_plan_params* params,
+                float* q_out, double* merit_out, unsigned char* accepted_out, gcdf_stream_t stream) {
+  int rc = GCDF_OK;
   const int n = net_n_dof(net);
   long long rows = 0, pts = 0, pairs = 0;
   for (int r = 0; r < n_problems; ++r) {
-    const gcdf_plan_problem& pr = problems[r];
-    if (pr.n_waypoints < 2) return set_error(GCDF_EINVAL, "problem %d: n_waypoints %d < 2", r, pr.n_waypoints);
-    if (pr.n_points < 0) return set_error(GCDF_EINVAL, "problem %d: n_points < 0", r);
-    if (!pr.q_start || !pr.q_goal) return set_error(GCDF_EINVAL, "problem %d: q_start / q_goal NULL", r);
-    if (pr.n_points > 0 && (!pr.points || !al16(pr.points)))
-      return set_error(GCDF_EINVAL, "problem %d: points NULL or not 16-byte aligned", r);
-    rows += pr.n_waypoints;
-    pts += pr.n_points;
-    pairs += (long long)pr.n_waypoints * pr.n_points;
+    rows += problems[r].n_waypoints;
+    pts += problems[r].n_points;
+    pairs += (long long)problems[r].n_waypoints * problems[r].n_points;
   }
-  if (pairs > 0x7fffffffLL || pts > 0x7fffffffLL || rows > 0x7fffffffLL)
-    return set_error(GCDF_EINVAL, "batch too large: %lld pairs (limit 2^31 - 1)", pairs);
   cudaStream_t s = (cudaStream_t)stream;
   Scratch sc(s);
   cudaError_t e;
@@ -398,6 +421,63 @@ extern "C" int gcdf_plan_solve(gcdf_net* net, const gcdf_plan_problem* problems,
   }
   if ((e = launch_plan_output(trajs, n_problems, n, q_out, orow, s)))
     return set_error(GCDF_ECUDA, "plan output launch: %s", cudaGetErrorString(e));
+  return GCDF_OK;
+}
+
+}  // namespace
+
+extern "C" int gcdf_plan_solve(gcdf_net* net, const gcdf_plan_problem* problems, int n_problems,
+                               const gcdf_plan_params* params, float* q_out, double* merit_out,
+                               unsigned char* accepted_out, gcdf_stream_t stream) {
+  if (!net) return set_error(GCDF_EINVAL, "net is NULL");
+  int rc = check_plan_params(params);
+  if (rc) return rc;
+  if (n_problems < 0 || (n_problems > 0 && !problems)) return set_error(GCDF_EINVAL, "bad problem list");
+  if (n_problems == 0) { clear_error(); return GCDF_OK; }
+  if (!q_out || !al16(q_out)) return set_error(GCDF_EINVAL, "q_out NULL or not 16-byte aligned");
+  if ((merit_out == nullptr) != (accepted_out == nullptr))
+    return set_error(GCDF_EINVAL, "give both merit_out and accepted_out or neither");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != net_device(net)) return set_error(GCDF_EINVAL, "net belongs to device %d, current device is %d",
+                                               net_device(net), dev);
+  const int n = net_n_dof(net);
+  const long long kLim = 0x7fffffffLL;
+  for (int r = 0; r < n_problems; ++r) {
+    const gcdf_plan_problem& pr = problems[r];
+    if (pr.n_waypoints < 2) return set_error(GCDF_EINVAL, "problem %d: n_waypoints %d < 2", r, pr.n_waypoints);
+    if (pr.n_points < 0) return set_error(GCDF_EINVAL, "problem %d: n_points < 0", r);
+    if (!pr.q_start || !pr.q_goal) return set_error(GCDF_EINVAL, "problem %d: q_start / q_goal NULL", r);
+    if (pr.n_points > 0 && (!pr.points || !al16(pr.points)))
+      return set_error(GCDF_EINVAL, "problem %d: points NULL or not 16-byte aligned", r);
+    if ((long long)pr.n_waypoints * pr.n_points > kLim)
+      return set_error(GCDF_EINVAL, "problem %d has more than 2^31 - 1 pairs", r);
+  }
+  // consecutive chunks of problems whose pairs, points and rows each stay below
+  // 2^31: one collision pass per step and chunk (problems are independent, so
+  // the chunking changes no result)
+  const int hl = params->iterations + 1;
+  int r0 = 0;
+  long long row0 = 0;
+  while (r0 < n_problems) {
+    long long cr = 0, cp = 0, cq = 0;
+    int r1 = r0;
+    while (r1 < n_problems) {
+      const gcdf_plan_problem& pr = problems[r1];
+      const long long q = (long long)pr.n_waypoints * pr.n_points;
+      if (r1 > r0 && (cq + q > kLim || cp + pr.n_points > kLim || cr + pr.n_waypoints > kLim)) break;
+      cr += pr.n_waypoints;
+      cp += pr.n_points;
+      cq += q;
+      ++r1;
+    }
+    rc = solve_chunk(net, problems + r0, r1 - r0, params, q_out + row0 * n,
+                     merit_out ? merit_out + (size_t)r0 * hl : nullptr,
+                     accepted_out ? accepted_out + (size_t)r0 * hl : nullptr, stream);
+    if (rc) return rc;
+    row0 += cr;
+    r0 = r1;
+  }
   clear_error();
   return GCDF_OK;
 }
