@@ -20,9 +20,12 @@ Contents
            controls eliminated, the l1 GCDF penalty of Eq. 12) as a fixed
            number of Levenberg-Marquardt steps preconditioned by the
            tridiagonal Hessian of the smooth terms (FP64 Cholesky).
+  sparse   the spatial partition of Sec. IV-A (planar range of the reference
+           base), the dense->sparse GCDF Jacobian of Eq. (17)/(18) and the
+           single-step projection of Theorem 1.
   metrics  the relative-error measures used by every parity test.
 
 Every function states the passage it follows.  Parity pins live in
 ``tests/test_oracle_*.py``.
 """
-from . import mlp, reduce, robot, metrics, planner  # noqa: F401
+from . import mlp, reduce, robot, metrics, planner, sparse  # noqa: F401
