@@ -216,6 +216,53 @@ GCDF_API int gcdf_device_status(gcdf_net *net, int *status);
  */
 GCDF_API int gcdf_set_profile_events(gcdf_net *net, void *start_event, void *stop_event);
 
+/*
+ * Single-step projection (Theorem 1, property 2): for every (waypoint, point)
+ * pair, q_z = q_i - f(p_j, q_i) M^{-1} df/dq(p_j, q_i), the configuration on
+ * the point's zero-level set nearest to q_i when f is the exact GCDF.
+ * Arguments as gcdf_query; m_diag (n) DEVICE: the diagonal of M, or NULL for
+ * the identity.  q_out (n_pairs, n) out, stacked order of Eq. (14).
+ */
+GCDF_API int gcdf_project(gcdf_net *net, const float *q, int n_waypoints, const float *p, int n_points,
+                          const int *part_offsets, const int *part_idx, int n_pairs, const float *shift,
+                          const float *m_diag, float *q_out, gcdf_stream_t stream);
+
+/*
+ * Spatial partition (Sec. IV-A): waypoint i considers the obstacle points
+ * within a range of its reference base position b_i.  The paper does not give
+ * the range's shape; here it is planar: I_{M,i} = { j : (p_jx - b_ix)^2 +
+ * (p_jy - b_iy)^2 <= radius^2 }, evaluated in FP64 on the FP32 inputs (each
+ * product and the sum rounded separately), in increasing point order — the
+ * CSR lists gcdf_query and gcdf_collision_cost take.
+ *   base_xy (n_waypoints, 2) DEVICE, p (n_points, 3) DEVICE, radius >= 0
+ *   (INFINITY keeps every point).
+ * gcdf_partition_offsets writes part_offsets (n_waypoints + 1) DEVICE;
+ * part_offsets[n_waypoints] is the list length the caller then allocates for
+ * part_idx, filled by gcdf_partition_indices with the same arguments.
+ * Errors: EINVAL (NULL or misaligned pointer, negative size or radius), ECUDA.
+ */
+GCDF_API int gcdf_partition_offsets(const float *base_xy, int n_waypoints, const float *p, int n_points,
+                                    float radius, int *part_offsets, gcdf_stream_t stream);
+GCDF_API int gcdf_partition_indices(const float *base_xy, int n_waypoints, const float *p, int n_points,
+                                    float radius, const int *part_offsets, int *part_idx, gcdf_stream_t stream);
+
+/*
+ * Dense -> sparse GCDF Jacobian (Eq. 17): row k of the dense gradient block
+ * grad (n_pairs, n) (the Eq. 15 output of gcdf_query) belongs to waypoint i_k;
+ * in the Jacobian of the stacked constraints with respect to the state vector
+ * [x_1; ...; x_N], x_i = [q_i, v_i] in R^{2n}, its n entries sit at columns
+ * 2n i_k .. 2n i_k + n - 1 (P_i of Eq. 18 places I_n at the columns of q_i;
+ * the printed offset 2Nn(i-1) would exceed the 2Nn columns for i >= 2, so the
+ * state stride 2n is used).  Writes the (n_pairs x 2Nn) Jacobian as CSR:
+ * row_ptr (n_pairs + 1, int64) DEVICE, col_idx (n_pairs n) DEVICE, and values
+ * (n_pairs n) DEVICE (a copy of grad; NULL writes the structure only).
+ * part_offsets (N + 1) as for gcdf_query, or NULL for dense lists
+ * (n_pairs = n_waypoints n_points).  Errors: EINVAL, ECUDA.
+ */
+GCDF_API int gcdf_jacobian_scatter(const float *grad, int n_waypoints, int n_dof, const int *part_offsets,
+                                   int n_points, int n_pairs, long long *row_ptr, int *col_idx, float *values,
+                                   gcdf_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Trajectory optimisation with the GCDF collision cost (Sec. IV-A).
  *

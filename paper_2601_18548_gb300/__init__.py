@@ -144,6 +144,54 @@ def collision_cost_noalloc(net: Net, q: torch.Tensor, p: torch.Tensor, reduction
     return cost, grad, amin
 
 
+def project(net: Net, q: torch.Tensor, p: torch.Tensor, part_offsets=None, part_idx=None, shift=None,
+            m_diag=None, out=None, stream=None):
+    """gcdf_project: q_z = q - f M^{-1} df/dq for every pair (Theorem 1), (P, n)."""
+    lib = _lib.load()
+    N, M = q.shape[0], p.shape[0]
+    P = N * M if part_offsets is None else int(part_idx.numel())
+    qz = torch.empty(P, net.n_dof, device=q.device, dtype=torch.float32) if out is None else out
+    _lib.check(lib.gcdf_project(net.handle, _ptr(q, name="q"), N, _ptr(p, name="p"), M,
+                                _ptr(part_offsets, torch.int32, "part_offsets"),
+                                _ptr(part_idx, torch.int32, "part_idx"), P, _ptr(shift, name="shift"),
+                                _ptr(m_diag, name="m_diag"), _ptr(qz, name="q_out"), _stream(stream)))
+    return qz
+
+
+def partition(base_xy: torch.Tensor, p: torch.Tensor, radius: float, stream=None):
+    """gcdf_partition_offsets + gcdf_partition_indices: CSR lists (offsets
+    (N+1,) int32, idx int32) of the points within planar range `radius` of
+    every waypoint's base position (Sec. IV-A).  Reads the list length back
+    (one synchronisation) to size idx."""
+    lib = _lib.load()
+    N, M = base_xy.shape[0], p.shape[0]
+    off = torch.empty(N + 1, device=p.device, dtype=torch.int32)
+    bp, pp = _ptr(base_xy, name="base_xy"), _ptr(p, name="p")
+    _lib.check(lib.gcdf_partition_offsets(bp, N, pp, M, float(radius), _ptr(off, torch.int32, "offsets"),
+                                          _stream(stream)))
+    total = int(off[-1].item())
+    idx = torch.empty(max(total, 4), device=p.device, dtype=torch.int32)
+    _lib.check(lib.gcdf_partition_indices(bp, N, pp, M, float(radius), _ptr(off, torch.int32, "offsets"),
+                                          _ptr(idx, torch.int32, "idx"), _stream(stream)))
+    return off, idx[:total]
+
+
+def jacobian_scatter(grad: torch.Tensor, n_waypoints: int, part_offsets=None, n_points: int = 0,
+                     with_values: bool = True, stream=None):
+    """gcdf_jacobian_scatter: CSR (row_ptr int64, col_idx int32, values) of the
+    (P x 2Nn) Jacobian of Eq. (17) from the dense (P, n) block."""
+    lib = _lib.load()
+    P, n = grad.shape
+    row_ptr = torch.empty(P + 1, device=grad.device, dtype=torch.int64)
+    col = torch.empty(max(P * n, 4), device=grad.device, dtype=torch.int32)
+    val = torch.empty(max(P * n, 4), device=grad.device, dtype=torch.float32) if with_values else None
+    _lib.check(lib.gcdf_jacobian_scatter(_ptr(grad, name="grad"), int(n_waypoints), n,
+                                         _ptr(part_offsets, torch.int32, "part_offsets"), int(n_points), P,
+                                         _ptr(row_ptr, torch.int64, "row_ptr"), _ptr(col, torch.int32, "col_idx"),
+                                         None if val is None else _ptr(val, name="values"), _stream(stream)))
+    return row_ptr, col[: P * n], (None if val is None else val[: P * n])
+
+
 def device_status(net: Net) -> int:
     """gcdf_device_status: 0, or the bits of a bounded device wait that gave up."""
     v = ctypes.c_int(0)

@@ -60,6 +60,10 @@ SIGNATURES = {
     "gcdf_collision_cost_noalloc": (_i, [_vp, _vp, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _f, _vp, _vp, _vp, _vp]),
     "gcdf_device_status": (_i, [_vp, ctypes.POINTER(_i)]),
     "gcdf_set_profile_events": (_i, [_vp, _vp, _vp]),
+    "gcdf_project": (_i, [_vp, _vp, _i, _vp, _i, _vp, _vp, _i, _vp, _vp, _vp, _vp]),
+    "gcdf_partition_offsets": (_i, [_vp, _i, _vp, _i, _f, _vp, _vp]),
+    "gcdf_partition_indices": (_i, [_vp, _i, _vp, _i, _f, _vp, _vp, _vp]),
+    "gcdf_jacobian_scatter": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp, _vp, _vp]),
     "gcdf_plan_solve": (_i, [_vp, ctypes.POINTER(PlanProblem), _i, ctypes.POINTER(PlanParams), _vp, _vp, _vp, _vp]),
     "gcdf_server_create": (_i, [ctypes.POINTER(ServerDesc), ctypes.POINTER(_vp)]),
     "gcdf_plan_submit": (_i, [_vp, ctypes.POINTER(PlanRequest), ctypes.POINTER(ctypes.c_uint64)]),

@@ -12,6 +12,8 @@
 using namespace gcdf;
 
 namespace gcdf {
+cudaError_t launch_project(const float* q, int N, int n, const int* offsets, int M, long long K, const float* f,
+                           const float* m_diag, float* g, cudaStream_t s);
 int fp32_tile_pairs(int H);
 int tc_tile_pairs();
 bool tc_supported(int H, int L, int n_dof);
@@ -406,6 +408,31 @@ int gcdf_query(gcdf_net* net, const float* q, int N, const float* p, int M, cons
   Temps tmp(s);
   rc = run(net, w, shift, tmp, s);
   if (rc) return rc;
+  g_err[0] = 0;
+  return GCDF_OK;
+}
+
+int gcdf_project(gcdf_net* net, const float* q, int N, const float* p, int M, const int* part_offsets,
+                 const int* part_idx, int n_pairs, const float* shift, const float* m_diag, float* q_out,
+                 gcdf_stream_t stream) {
+  WorkDesc w;
+  int rc = check_call(net, q, N, p, M, part_offsets, part_idx, n_pairs, shift, w);
+  if (rc) return rc;
+  if (N == 0 || w.n_pairs == 0) return GCDF_OK;
+  if (!q_out || !aligned16(q_out)) return fail(GCDF_EINVAL, "q_out is NULL or not 16-byte aligned");
+  if (m_diag && !aligned16(m_diag)) return fail(GCDF_EINVAL, "m_diag not 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  Temps tmp(s);
+  cudaError_t e;
+  float* f = nullptr;
+  if ((e = tmp.get((void**)&f, (size_t)w.n_pairs * sizeof(float)))) return cuda_fail(e, "cudaMallocAsync");
+  w.mode = kQuery;
+  w.f_out = f;
+  w.g_out = q_out;  // df/dq lands in q_out and is turned into q_z in place
+  rc = run(net, w, shift, tmp, s);
+  if (rc) return rc;
+  if ((e = launch_project(q, N, net->n_dof, part_offsets, M, w.n_pairs, f, m_diag, q_out, s)))
+    return cuda_fail(e, "projection launch");
   g_err[0] = 0;
   return GCDF_OK;
 }

@@ -1,0 +1,260 @@
+// Constraint-structure kernels around the fused GCDF pass (Sec. IV-A):
+//   partition   per-waypoint lists I_{M,i} of the obstacle points within a
+//               planar range R of the waypoint's reference base position
+//               (count, scan, order-preserving fill);
+//   jacobian    the dense (sum m_i) x n gradient block placed into the sparse
+//               (sum m_i) x 2Nn Jacobian of Eq. (17): P_i of Eq. (18) puts the
+//               n entries of a row of waypoint i at columns 2n(i-1) .. 2n(i-1)+n-1
+//               (the columns of q_i in the state vector [x_1; ...; x_N],
+//               x_i = [q_i, v_i]), written as CSR;
+//   project     the single-step projection of Theorem 1,
+//               q_z = q - f(p, q) M^{-1} grad_q f(p, q), for every pair.
+#include <cstring>
+
+#include "gcdf_internal.cuh"
+
+namespace gcdf {
+
+int set_error(int code, const char* fmt, ...);
+void clear_error();
+int net_n_dof(const gcdf_net* net);
+
+namespace {
+
+constexpr int kPartThreads = 256;
+constexpr int kPerThread = 8;  // consecutive points per thread and tile of the fill
+
+// Inside the planar range: FP64 on the FP32 inputs, each product and the sum
+// rounded separately (no contraction), compared with R * R.
+__device__ __forceinline__ bool in_range(const float* __restrict__ p, int j, double bx, double by, double r2) {
+  const double dx = __dsub_rn((double)p[3 * (size_t)j], bx);
+  const double dy = __dsub_rn((double)p[3 * (size_t)j + 1], by);
+  return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= r2;
+}
+
+__global__ void partition_count_kernel(const float* __restrict__ base, const float* __restrict__ p, int M,
+                                       double r2, int* __restrict__ counts) {
+  __shared__ int red[kPartThreads / 32];
+  const int i = blockIdx.x;
+  const double bx = base[2 * i], by = base[2 * i + 1];
+  int c = 0;
+  for (int j = threadIdx.x; j < M; j += kPartThreads) c += in_range(p, j, bx, by, r2);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < kPartThreads / 32; ++w) s += red[w];
+    counts[i] = s;
+  }
+}
+
+// out[0] = 0, out[k + 1] = in[0] + ... + in[k]; one block.
+__global__ void exclusive_scan_kernel(const int* __restrict__ in, int N, int* __restrict__ out) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x;
+  const int per = (N + blockDim.x - 1) / blockDim.x;
+  const int lo = min(N, t * per), hi = min(N, lo + per);
+  int sum = 0;
+  for (int i = lo; i < hi; ++i) sum += in[i];
+  part[t] = sum;
+  __syncthreads();
+  for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+    const int v = (t >= d) ? part[t - d] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int run = part[t] - sum;
+  if (t == 0) out[0] = 0;
+  for (int i = lo; i < hi; ++i) {
+    run += in[i];
+    out[i + 1] = run;
+  }
+}
+
+// One block per waypoint: tiles of kPartThreads * kPerThread points in order;
+// thread t tests points tile + 8t .. tile + 8t + 7, the block scans the thread
+// counts, so the list keeps increasing point order.
+__global__ void partition_fill_kernel(const float* __restrict__ base, const float* __restrict__ p, int M, double r2,
+                                      const int* __restrict__ offsets, int* __restrict__ idx) {
+  __shared__ int wsum[kPartThreads / 32];
+  __shared__ int s_total;
+  const int i = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const double bx = base[2 * i], by = base[2 * i + 1];
+  int run = offsets[i];
+  for (int tile = 0; tile < M; tile += kPartThreads * kPerThread) {
+    const int j0 = tile + t * kPerThread;
+    unsigned mask = 0;
+#pragma unroll
+    for (int u = 0; u < kPerThread; ++u)
+      if (j0 + u < M && in_range(p, j0 + u, bx, by, r2)) mask |= 1u << u;
+    const int c = __popc(mask);
+    int x = c;  // inclusive warp scan
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += v;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (t == 0) {
+      int s = 0;
+      for (int k = 0; k < kPartThreads / 32; ++k) {
+        const int v = wsum[k];
+        wsum[k] = s;
+        s += v;
+      }
+      s_total = s;
+    }
+    __syncthreads();
+    int pos = run + wsum[w] + x - c;
+    for (int u = 0; u < kPerThread; ++u)
+      if (mask & (1u << u)) idx[pos++] = j0 + u;
+    run += s_total;
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int waypoint_of_row(const int* __restrict__ offsets, int N, int M, long long k) {
+  if (offsets == nullptr) return (int)(k / M);
+  int lo = 0, hi = N;  // largest i with offsets[i] <= k
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (offsets[mid] <= k) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void jacobian_kernel(const float* __restrict__ grad, int N, int n, const int* __restrict__ offsets,
+                                int M, long long K, long long* __restrict__ row_ptr, int* __restrict__ col_idx,
+                                float* __restrict__ values) {
+  const long long total = K * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e / n;
+    const int d = (int)(e - k * n);
+    const int i = waypoint_of_row(offsets, N, M, k);
+    col_idx[e] = 2 * n * i + d;
+    if (values) values[e] = grad[e];
+    if (d == 0) row_ptr[k] = e;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) row_ptr[K] = total;
+}
+
+// g holds df/dq of every pair on entry and the projected configuration on exit.
+__global__ void project_kernel(const float* __restrict__ q, int N, int n, const int* __restrict__ offsets, int M,
+                               long long K, const float* __restrict__ f, const float* __restrict__ m_diag,
+                               float* __restrict__ g) {
+  const long long total = K * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e / n;
+    const int d = (int)(e - k * n);
+    const int i = waypoint_of_row(offsets, N, M, k);
+    const float gd = m_diag ? g[e] / m_diag[d] : g[e];
+    g[e] = fmaf(-f[k], gd, q[(size_t)i * n + d]);
+  }
+}
+
+int grid_for(long long work, int threads, int num_sms) {
+  const long long b = (work + threads - 1) / threads;
+  const long long cap = (long long)num_sms * 16;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+int check_partition(const float* base_xy, int N, const float* p, int M, float radius, const int* offsets) {
+  if (N < 0 || M < 0) return set_error(GCDF_EINVAL, "negative size (n_waypoints %d, n_points %d)", N, M);
+  if (N > 0 && (!base_xy || !al16(base_xy))) return set_error(GCDF_EINVAL, "base_xy NULL or not 16-byte aligned");
+  if (M > 0 && (!p || !al16(p))) return set_error(GCDF_EINVAL, "p NULL or not 16-byte aligned");
+  if (!offsets || !al16(offsets)) return set_error(GCDF_EINVAL, "part_offsets NULL or not 16-byte aligned");
+  if (!(radius >= 0.f)) return set_error(GCDF_EINVAL, "radius must be >= 0 (got %g)", (double)radius);
+  return GCDF_OK;
+}
+
+}  // namespace
+
+// used by gcdf_project (gcdf_api.cu): the in-place projection of a query's output
+cudaError_t launch_project(const float* q, int N, int n, const int* offsets, int M, long long K, const float* f,
+                           const float* m_diag, float* g, cudaStream_t s) {
+  if (K == 0) return cudaSuccess;
+  project_kernel<<<grid_for(K * n, 256, sms()), 256, 0, s>>>(q, N, n, offsets, M, K, f, m_diag, g);
+  return cudaGetLastError();
+}
+
+}  // namespace gcdf
+
+using namespace gcdf;
+
+extern "C" {
+
+int gcdf_partition_offsets(const float* base_xy, int n_waypoints, const float* p, int n_points, float radius,
+                           int* part_offsets, gcdf_stream_t stream) {
+  int rc = check_partition(base_xy, n_waypoints, p, n_points, radius, part_offsets);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (n_waypoints == 0) {
+    e = cudaMemsetAsync(part_offsets, 0, sizeof(int), s);
+    if (e != cudaSuccess) return set_error(GCDF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    clear_error();
+    return GCDF_OK;
+  }
+  int* counts = nullptr;
+  if ((e = cudaMallocAsync((void**)&counts, (size_t)n_waypoints * sizeof(int), s)))
+    return set_error(e == cudaErrorMemoryAllocation ? GCDF_ENOMEM : GCDF_ECUDA, "cudaMallocAsync: %s",
+                     cudaGetErrorString(e));
+  const double r2 = (double)radius * (double)radius;
+  partition_count_kernel<<<n_waypoints, kPartThreads, 0, s>>>(base_xy, p, n_points, r2, counts);
+  exclusive_scan_kernel<<<1, 1024, 0, s>>>(counts, n_waypoints, part_offsets);
+  e = cudaGetLastError();
+  cudaFreeAsync(counts, s);
+  if (e != cudaSuccess) return set_error(GCDF_ECUDA, "partition launch: %s", cudaGetErrorString(e));
+  clear_error();
+  return GCDF_OK;
+}
+
+int gcdf_partition_indices(const float* base_xy, int n_waypoints, const float* p, int n_points, float radius,
+                           const int* part_offsets, int* part_idx, gcdf_stream_t stream) {
+  int rc = check_partition(base_xy, n_waypoints, p, n_points, radius, part_offsets);
+  if (rc) return rc;
+  if (n_waypoints == 0 || n_points == 0) { clear_error(); return GCDF_OK; }
+  if (!part_idx || !al16(part_idx)) return set_error(GCDF_EINVAL, "part_idx NULL or not 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  const double r2 = (double)radius * (double)radius;
+  partition_fill_kernel<<<n_waypoints, kPartThreads, 0, s>>>(base_xy, p, n_points, r2, part_offsets, part_idx);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(GCDF_ECUDA, "partition launch: %s", cudaGetErrorString(e));
+  clear_error();
+  return GCDF_OK;
+}
+
+int gcdf_jacobian_scatter(const float* grad, int n_waypoints, int n_dof, const int* part_offsets, int n_points,
+                          int n_pairs, long long* row_ptr, int* col_idx, float* values, gcdf_stream_t stream) {
+  if (n_waypoints < 0 || n_points < 0 || n_pairs < 0 || n_dof < 1 || n_dof > kMaxDof)
+    return set_error(GCDF_EINVAL, "bad sizes");
+  const long long K = part_offsets ? (long long)n_pairs : (long long)n_waypoints * n_points;
+  if ((long long)2 * n_waypoints * n_dof > 0x7fffffffLL) return set_error(GCDF_EINVAL, "2 N n exceeds 2^31 - 1");
+  if (!row_ptr || !al16(row_ptr)) return set_error(GCDF_EINVAL, "row_ptr NULL or not 16-byte aligned");
+  if (K > 0 && (!col_idx || !al16(col_idx))) return set_error(GCDF_EINVAL, "col_idx NULL or not 16-byte aligned");
+  if (K > 0 && values && (!grad || !al16(grad) || !al16(values)))
+    return set_error(GCDF_EINVAL, "grad / values NULL or not 16-byte aligned");
+  if (part_offsets && !al16(part_offsets)) return set_error(GCDF_EINVAL, "part_offsets not 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  jacobian_kernel<<<grid_for(K * n_dof, 256, sms()), 256, 0, s>>>(grad, n_waypoints, n_dof, part_offsets,
+                                                                  n_points, K, row_ptr, col_idx, values);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(GCDF_ECUDA, "jacobian launch: %s", cudaGetErrorString(e));
+  clear_error();
+  return GCDF_OK;
+}
+
+}  // extern "C"
