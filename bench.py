@@ -11,6 +11,7 @@ value+gradient pairs reduced to 128 costs and gradients.  Inputs are synthetic
     python bench.py --impl reference ...   # the FP64 CPU oracle on the same workload
     python bench.py --serve                 # served-planning latency (see run_serve)
     python bench.py --plan [--plan-problems P]   # batched trajectory optimisation (see run_plan)
+    python bench.py --aux                   # partition, Jacobian scatter, projection kernels
 
 Multi-GPU: one process per GPU (torchrun); every rank runs its own replica of
 the workload (weak scaling, no collective on the data path); the time is the
@@ -560,6 +561,94 @@ def run_plan(args):
     return 0
 
 
+def _time_events(fn, reps=20, flush=None):
+    """Median device time (ms) of fn() over reps calls, CUDA events on the
+    current stream, optional L2 flush between calls."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def run_aux(args):
+    """Constraint-structure kernels at the largest sizes of the request mix:
+    the spatial partition (256 waypoints x 65,536 points), the dense->sparse
+    Jacobian (2,097,152 rows x 9) and the single-step projection of the box
+    scene (128 x 16,384 pairs, BF16 field).  L2 flushed between calls; the
+    bound of each is HBM or L2 traffic, reported against the measured copy
+    bandwidth."""
+    import torch
+    import paper_2601_18548_gb300 as g
+    from paper_2601_18548_gb300 import _lib
+    peaks, src = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    flush = torch.empty(64 << 20, device="cuda", dtype=torch.float32)
+    lib = _lib.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    out = {}
+    # partition: every waypoint reads the (x, y) of every point (the cloud stays in L2)
+    N, M, R = 256, 65536, 1.5
+    r = synth.SplitMix64(71)
+    base = torch.from_numpy(np.ascontiguousarray(synth.uniform_points(r, N, [-5, -5, 0], [5, 5, 0])[:, :2]
+                                                 .astype(np.float32))).cuda()
+    pts = torch.from_numpy(synth.box_scene(n_waypoints=2, n_points=M, seed_scene=72).p.astype(np.float32)).cuda()
+    off = torch.empty(N + 1, device="cuda", dtype=torch.int32)
+    lib.gcdf_partition_offsets(base.data_ptr(), N, pts.data_ptr(), M, R, off.data_ptr(), stream)
+    torch.cuda.synchronize()
+    total = int(off[-1].item())
+    idx = torch.empty(max(total, 4), device="cuda", dtype=torch.int32)
+
+    def part():
+        lib.gcdf_partition_offsets(base.data_ptr(), N, pts.data_ptr(), M, R, off.data_ptr(), stream)
+        lib.gcdf_partition_indices(base.data_ptr(), N, pts.data_ptr(), M, R, off.data_ptr(), idx.data_ptr(), stream)
+    ms = _time_events(part, flush=flush)
+    out["partition"] = {"waypoints": N, "points": M, "radius_m": R, "listed_pairs": total, "ms": ms,
+                        "tests_per_s": 2 * N * M / (ms / 1e3),
+                        "note": "two passes (count, fill) over N x M planar distance tests; the 786 KB cloud is "
+                                "read from L2 by every waypoint, DRAM sees it once"}
+    # Jacobian scatter: read grad (P n 4 B), write values (P n 4 B), col_idx (P n 4 B), row_ptr (8 B per row)
+    P, n = 128 * 16384, 9
+    grad = torch.randn(P, n, device="cuda")
+    rp = torch.empty(P + 1, device="cuda", dtype=torch.int64)
+    col = torch.empty(P * n, device="cuda", dtype=torch.int32)
+    val = torch.empty(P * n, device="cuda", dtype=torch.float32)
+    ms = _time_events(lambda: lib.gcdf_jacobian_scatter(grad.data_ptr(), 128, n, None, 16384, P, rp.data_ptr(),
+                                                        col.data_ptr(), val.data_ptr(), stream), flush=flush)
+    byts = P * n * 12 + (P + 1) * 8
+    out["jacobian_scatter"] = {"rows": P, "n": n, "ms": ms, "bytes": byts, "achieved_gbs": byts / ms / 1e6,
+                               "peak_gbs": hbm, "frac": byts / ms / 1e6 / hbm, "bound": "hbm"}
+    # projection of the scene: the fused query plus the in-place q - f M^-1 g pass
+    wl = synth.box_scene()
+    s_ = wl.shape
+    net = g.create_net(s_.n_dof, s_.hidden, s_.n_layers, wl.weights, "bf16")
+    q = torch.from_numpy(wl.q).cuda()
+    p = torch.from_numpy(wl.p).cuda()
+    qz = torch.empty(wl.n_pairs, s_.n_dof, device="cuda")
+    fbuf = torch.empty(wl.n_pairs, device="cuda")
+    ms_q = _time_events(lambda: g.query(net, q, p, out=(fbuf, qz)), flush=flush)
+    ms_p = _time_events(lambda: g.project(net, q, p, out=qz), flush=flush)
+    # the projection pass alone: read f (4 B) and g (4 n B), write q_z (4 n B) per pair
+    byts = wl.n_pairs * (4 + 8 * s_.n_dof)
+    extra = max(ms_p - ms_q, 1e-6)
+    out["projection"] = {"pairs": wl.n_pairs, "ms_query": ms_q, "ms_project": ms_p,
+                         "pairs_per_s": wl.n_pairs / (ms_p / 1e3), "projection_pass_ms": ms_p - ms_q,
+                         "projection_pass_gbs": byts / extra / 1e6, "peak_gbs": hbm,
+                         "frac": byts / extra / 1e6 / hbm, "bound": "hbm"}
+    print(json.dumps({"metric": "constraint-structure kernels", "peaks": src, "n_gpus": 1,
+                      "data": "synthetic", "l2": "flushed between calls (256 MiB write)", **out}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -578,6 +667,7 @@ def main():
     ap.add_argument("--overload-seconds", type=float, default=1.0)
     ap.add_argument("--plan", action="store_true", help="batched trajectory-optimisation benchmark instead")
     ap.add_argument("--plan-problems", type=int, default=64)
+    ap.add_argument("--aux", action="store_true", help="partition / Jacobian / projection kernels instead")
     args = ap.parse_args()
     global WAYPOINTS, POINTS
     WAYPOINTS, POINTS = args.waypoints, args.points
@@ -587,6 +677,8 @@ def main():
         return run_serve(args)
     if args.plan:
         return run_plan(args)
+    if args.aux:
+        return run_aux(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -116,7 +116,7 @@ __global__ void partition_fill_kernel(const float* __restrict__ base, const floa
 }
 
 __device__ __forceinline__ int waypoint_of_row(const int* __restrict__ offsets, int N, int M, long long k) {
-  if (offsets == nullptr) return (int)(k / M);
+  if (offsets == nullptr) return k < 0x7fffffffLL ? (int)k / M : (int)(k / M);
   int lo = 0, hi = N;  // largest i with offsets[i] <= k
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -125,34 +125,56 @@ __device__ __forceinline__ int waypoint_of_row(const int* __restrict__ offsets, 
   return lo;
 }
 
-__global__ void jacobian_kernel(const float* __restrict__ grad, int N, int n, const int* __restrict__ offsets,
-                                int M, long long K, long long* __restrict__ row_ptr, int* __restrict__ col_idx,
-                                float* __restrict__ values) {
-  const long long total = K * n;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long k = e / n;
-    const int d = (int)(e - k * n);
-    const int i = waypoint_of_row(offsets, N, M, k);
-    col_idx[e] = 2 * n * i + d;
-    if (values) values[e] = grad[e];
-    if (d == 0) row_ptr[k] = e;
+constexpr int kRowsPerBlock = 256;  // rows of one block of the Jacobian / projection passes
+
+// A block takes kRowsPerBlock consecutive rows: each thread looks up one row's
+// waypoint, then the block streams the rows' n entries with coalesced loads
+// and stores (element e of the block's range is row e / n, entry e % n).
+__global__ void __launch_bounds__(kRowsPerBlock) jacobian_kernel(
+    const float* __restrict__ grad, int N, int n, const int* __restrict__ offsets, int M, long long K,
+    long long* __restrict__ row_ptr, int* __restrict__ col_idx, float* __restrict__ values) {
+  __shared__ int s_col[kRowsPerBlock];
+  for (long long k0 = (long long)blockIdx.x * kRowsPerBlock; k0 < K; k0 += (long long)gridDim.x * kRowsPerBlock) {
+    const int rows = (int)min((long long)kRowsPerBlock, K - k0);
+    if ((int)threadIdx.x < rows) {
+      const long long k = k0 + threadIdx.x;
+      s_col[threadIdx.x] = 2 * n * waypoint_of_row(offsets, N, M, k);
+      row_ptr[k] = k * n;
+    }
+    __syncthreads();
+    const long long e0 = k0 * n;
+    for (int el = threadIdx.x; el < rows * n; el += kRowsPerBlock) {
+      const int r = el / n, d = el - r * n;
+      col_idx[e0 + el] = s_col[r] + d;
+      if (values) values[e0 + el] = grad[e0 + el];
+    }
+    __syncthreads();
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) row_ptr[K] = total;
+  if (blockIdx.x == 0 && threadIdx.x == 0) row_ptr[K] = K * n;
 }
 
 // g holds df/dq of every pair on entry and the projected configuration on exit.
-__global__ void project_kernel(const float* __restrict__ q, int N, int n, const int* __restrict__ offsets, int M,
-                               long long K, const float* __restrict__ f, const float* __restrict__ m_diag,
-                               float* __restrict__ g) {
-  const long long total = K * n;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long k = e / n;
-    const int d = (int)(e - k * n);
-    const int i = waypoint_of_row(offsets, N, M, k);
-    const float gd = m_diag ? g[e] / m_diag[d] : g[e];
-    g[e] = fmaf(-f[k], gd, q[(size_t)i * n + d]);
+__global__ void __launch_bounds__(kRowsPerBlock) project_kernel(
+    const float* __restrict__ q, int N, int n, const int* __restrict__ offsets, int M, long long K,
+    const float* __restrict__ f, const float* __restrict__ m_diag, float* __restrict__ g) {
+  __shared__ int s_wp[kRowsPerBlock];
+  __shared__ float s_f[kRowsPerBlock];
+  __shared__ float s_minv[kMaxDof];
+  if ((int)threadIdx.x < n) s_minv[threadIdx.x] = m_diag ? 1.0f / m_diag[threadIdx.x] : 1.0f;
+  for (long long k0 = (long long)blockIdx.x * kRowsPerBlock; k0 < K; k0 += (long long)gridDim.x * kRowsPerBlock) {
+    const int rows = (int)min((long long)kRowsPerBlock, K - k0);
+    if ((int)threadIdx.x < rows) {
+      const long long k = k0 + threadIdx.x;
+      s_wp[threadIdx.x] = waypoint_of_row(offsets, N, M, k);
+      s_f[threadIdx.x] = f[k];
+    }
+    __syncthreads();
+    float* gb = g + k0 * n;
+    for (int el = threadIdx.x; el < rows * n; el += kRowsPerBlock) {
+      const int r = el / n, d = el - r * n;
+      gb[el] = fmaf(-s_f[r], gb[el] * s_minv[d], q[(size_t)s_wp[r] * n + d]);
+    }
+    __syncthreads();
   }
 }
 
@@ -186,7 +208,7 @@ int check_partition(const float* base_xy, int N, const float* p, int M, float ra
 cudaError_t launch_project(const float* q, int N, int n, const int* offsets, int M, long long K, const float* f,
                            const float* m_diag, float* g, cudaStream_t s) {
   if (K == 0) return cudaSuccess;
-  project_kernel<<<grid_for(K * n, 256, sms()), 256, 0, s>>>(q, N, n, offsets, M, K, f, m_diag, g);
+  project_kernel<<<grid_for(K, kRowsPerBlock, sms()), kRowsPerBlock, 0, s>>>(q, N, n, offsets, M, K, f, m_diag, g);
   return cudaGetLastError();
 }
 
@@ -249,7 +271,7 @@ int gcdf_jacobian_scatter(const float* grad, int n_waypoints, int n_dof, const i
     return set_error(GCDF_EINVAL, "grad / values NULL or not 16-byte aligned");
   if (part_offsets && !al16(part_offsets)) return set_error(GCDF_EINVAL, "part_offsets not 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
-  jacobian_kernel<<<grid_for(K * n_dof, 256, sms()), 256, 0, s>>>(grad, n_waypoints, n_dof, part_offsets,
+  jacobian_kernel<<<grid_for(K, kRowsPerBlock, sms()), kRowsPerBlock, 0, s>>>(grad, n_waypoints, n_dof, part_offsets,
                                                                   n_points, K, row_ptr, col_idx, values);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(GCDF_ECUDA, "jacobian launch: %s", cudaGetErrorString(e));
