@@ -23,9 +23,12 @@ Contents
   sparse   the spatial partition of Sec. IV-A (planar range of the reference
            base), the dense->sparse GCDF Jacobian of Eq. (17)/(18) and the
            single-step projection of Theorem 1.
+  fit      per-sample field values and their vector-Jacobian products with
+           respect to the weights and q, for fitting with the distance loss
+           of Table I.
   metrics  the relative-error measures used by every parity test.
 
 Every function states the passage it follows.  Parity pins live in
 ``tests/test_oracle_*.py``.
 """
-from . import mlp, reduce, robot, metrics, planner, sparse  # noqa: F401
+from . import mlp, reduce, robot, metrics, planner, sparse, fit  # noqa: F401
