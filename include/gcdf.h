@@ -264,6 +264,34 @@ GCDF_API int gcdf_jacobian_scatter(const float *grad, int n_waypoints, int n_dof
                                    gcdf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Differentiable fit (Sec. III-C; distance loss of Table I).  An FP32 net
+ * given by its flat weights in DEVICE memory (layout of gcdf_weight_count,
+ * e.g. FP32 master weights being trained), evaluated per SAMPLE (q_b, p_b)
+ * rather than over a waypoint x point grid, with the vector-Jacobian products
+ * a training step needs.  Every product is a hand-written FP32 GEMM; the
+ * reductions over the batch (weight and bias gradients) are summed in a fixed
+ * order, so results are deterministic.  Temporaries: the activations and
+ * s'(z) of every layer (2 L batch x hidden floats) and a 64-chunk partials
+ * array, from cudaMallocAsync on the stream.
+ * ------------------------------------------------------------------------- */
+
+typedef struct gcdf_fit_desc {
+  int n_dof;            /* n, 3 .. 12 */
+  int hidden;           /* H, 1 .. 4096 */
+  int n_hidden_layers;  /* L, 1 .. 16 */
+} gcdf_fit_desc;
+
+/* f (batch,) DEVICE out: f(q_b, p_b) for q (batch, n) and p (batch, 3) DEVICE. */
+GCDF_API int gcdf_fit_forward(const gcdf_fit_desc *desc, const float *weights, const float *q, const float *p,
+                              int batch, float *f, gcdf_stream_t stream);
+
+/* For g_f (batch,) DEVICE = dL/df_b: dweights (gcdf_weight_count) DEVICE out =
+ * sum_b g_b df_b/dweights (written, not accumulated) and, unless NULL,
+ * dq (batch, n) DEVICE out = g_b df_b/dq_b. */
+GCDF_API int gcdf_fit_vjp(const gcdf_fit_desc *desc, const float *weights, const float *q, const float *p,
+                          int batch, const float *g_f, float *dweights, float *dq, gcdf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Trajectory optimisation with the GCDF collision cost (Sec. IV-A).
  *
  * Problem (Eq. 10 with the velocity controls eliminated through the

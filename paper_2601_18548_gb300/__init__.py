@@ -312,3 +312,51 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+# ---------------------------------------------------------------------------
+# Differentiable fit (gcdf_fit_forward / gcdf_fit_vjp)
+# ---------------------------------------------------------------------------
+
+def fit_forward(shape, weights: torch.Tensor, q: torch.Tensor, p: torch.Tensor, stream=None) -> torch.Tensor:
+    """gcdf_fit_forward: f (B,) per sample; shape = (n_dof, hidden, n_layers)."""
+    d = _lib.FitDesc(*[int(x) for x in shape])
+    f = torch.empty(q.shape[0], device=q.device, dtype=torch.float32)
+    _lib.check(_lib.load().gcdf_fit_forward(ctypes.byref(d), _ptr(weights, name="weights"), _ptr(q, name="q"),
+                                            _ptr(p, name="p"), int(q.shape[0]), _ptr(f, name="f"), _stream(stream)))
+    return f
+
+
+def fit_vjp(shape, weights, q, p, g_f, want_dq=True, stream=None):
+    """gcdf_fit_vjp: (dweights, dq or None) for the upstream gradient g_f (B,)."""
+    d = _lib.FitDesc(*[int(x) for x in shape])
+    dw = torch.empty_like(weights)
+    dq = torch.empty_like(q) if want_dq else None
+    _lib.check(_lib.load().gcdf_fit_vjp(ctypes.byref(d), _ptr(weights, name="weights"), _ptr(q, name="q"),
+                                        _ptr(p, name="p"), int(q.shape[0]), _ptr(g_f.contiguous(), name="g_f"),
+                                        _ptr(dw, name="dweights"), None if dq is None else _ptr(dq, name="dq"),
+                                        _stream(stream)))
+    return dw, dq
+
+
+class FieldFunction(torch.autograd.Function):
+    """f(q_b, p_b; weights) as an autograd.Function: the forward and both
+    vector-Jacobian products (weights and q) run in libgcdf's kernels."""
+
+    @staticmethod
+    def forward(ctx, weights, q, p, shape):
+        ctx.save_for_backward(weights, q, p)
+        ctx.shape = shape
+        return fit_forward(shape, weights.detach(), q.detach(), p)
+
+    @staticmethod
+    def backward(ctx, g_f):
+        weights, q, p = ctx.saved_tensors
+        dw, dq = fit_vjp(ctx.shape, weights.detach(), q.detach(), p, g_f.detach().float(),
+                         want_dq=ctx.needs_input_grad[1])
+        return dw, dq, None, None
+
+
+def field(weights: torch.Tensor, q: torch.Tensor, p: torch.Tensor, shape) -> torch.Tensor:
+    """Differentiable per-sample field values (weights: flat FP32 CUDA tensor)."""
+    return FieldFunction.apply(weights, q, p, tuple(shape))

@@ -26,6 +26,10 @@ class NetDesc(ctypes.Structure):
     _fields_ = [("n_dof", _i), ("hidden", _i), ("n_hidden_layers", _i), ("precision", _i)]
 
 
+class FitDesc(ctypes.Structure):
+    _fields_ = [("n_dof", _i), ("hidden", _i), ("n_hidden_layers", _i)]
+
+
 class PlanParams(ctypes.Structure):
     _fields_ = [("dt", _f), ("w_trans", _f), ("w_rot", _f), ("w_goal", _f), ("mu", _f), ("delta", _f),
                 ("lambda0", _f), ("lambda_min", _f), ("lambda_max", _f), ("iterations", _i)]
@@ -64,6 +68,8 @@ SIGNATURES = {
     "gcdf_partition_offsets": (_i, [_vp, _i, _vp, _i, _f, _vp, _vp]),
     "gcdf_partition_indices": (_i, [_vp, _i, _vp, _i, _f, _vp, _vp, _vp]),
     "gcdf_jacobian_scatter": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp, _vp, _vp]),
+    "gcdf_fit_forward": (_i, [ctypes.POINTER(FitDesc), _vp, _vp, _vp, _i, _vp, _vp]),
+    "gcdf_fit_vjp": (_i, [ctypes.POINTER(FitDesc), _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp]),
     "gcdf_plan_solve": (_i, [_vp, ctypes.POINTER(PlanProblem), _i, ctypes.POINTER(PlanParams), _vp, _vp, _vp, _vp]),
     "gcdf_server_create": (_i, [ctypes.POINTER(ServerDesc), ctypes.POINTER(_vp)]),
     "gcdf_plan_submit": (_i, [_vp, ctypes.POINTER(PlanRequest), ctypes.POINTER(ctypes.c_uint64)]),

@@ -1,0 +1,386 @@
+// Differentiable fit of the field (Sec. III-C, distance loss of Table I):
+// per-sample values f(q_b, p_b) of an FP32 net given by its flat weights, and
+// the vector-Jacobian products with respect to the weights and q for an
+// upstream gradient g_b = dL/df_b.
+//
+//   forward   v = [p, x, y, sin a, cos a, ...]; z_1 = W_1 v + b_1; h_l = s(z_l);
+//             z_{l+1} = W_{l+1} h_l + b_{l+1}; f = w_o . h_L + b_o
+//   backward  delta_L = g w_o * s'(z_L); delta_{l-1} = (delta_l W_l) * s'(z_{l-1});
+//             dW_l = delta_l^T h_{l-1}; db_l = delta_l^T 1; dw_o = h_L^T g; db_o = g^T 1;
+//             dv = delta_1 W_1 -> dq (sin/cos chain rule)
+//
+// Every product is one strided FP32 GEMM kernel (128 x 128 tiles, 8 x 8
+// outputs per thread); products that reduce over the batch (the weight and
+// bias gradients) split the batch into chunks whose partial tiles are summed
+// in a fixed order, so the gradients are deterministic.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "gcdf_internal.cuh"
+
+namespace gcdf {
+
+int set_error(int code, const char* fmt, ...);
+void clear_error();
+
+namespace {
+
+constexpr int kBM = 128, kBN = 128, kBK = 8, kGemmThreads = 256;
+
+// C[m, n] (row-major, ldc) = sum_k A(m, k) B(k, n) over k in this block's
+// chunk [z kc, min(K, (z + 1) kc)); with z > 0 chunks the block writes its
+// partial tile to C + z M ldc.
+__global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const float* __restrict__ A, long long sam, long long sak,
+                                                            const float* __restrict__ B, long long sbk,
+                                                            long long sbn, float* __restrict__ C, int ldc, int M,
+                                                            int N, int K, int kc) {
+  __shared__ __align__(16) float As[kBK][kBM];
+  __shared__ __align__(16) float Bs[kBK][kBN];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  const int k_lo = blockIdx.z * kc, k_hi = min(K, k_lo + kc);
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  const bool a_kfast = (sak == 1), b_nfast = (sbn == 1);
+  for (int k0 = k_lo; k0 < k_hi; k0 += kBK) {
+#pragma unroll
+    for (int r = 0; r < (kBK * kBM) / kGemmThreads; ++r) {
+      const int e = threadIdx.x + r * kGemmThreads;
+      const int mm = a_kfast ? e / kBK : e % kBM;
+      const int kk = a_kfast ? e % kBK : e / kBM;
+      const int m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < M && k < k_hi) ? A[(long long)m * sam + (long long)k * sak] : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < (kBK * kBN) / kGemmThreads; ++r) {
+      const int e = threadIdx.x + r * kGemmThreads;
+      const int nn = b_nfast ? e % kBN : e / kBK;
+      const int kk = b_nfast ? e / kBN : e % kBK;
+      const int n = n0 + nn, k = k0 + kk;
+      Bs[kk][nn] = (n < N && k < k_hi) ? B[(long long)k * sbk + (long long)n * sbn] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float* Cz = C + (long long)blockIdx.z * M * ldc;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+      if (n < N) Cz[(long long)m * ldc + n] = acc[i][j];
+    }
+  }
+}
+
+// C = sum over z of the partial tiles, in increasing z.
+__global__ void sum_partials_kernel(const float* __restrict__ P, int splits, int M, int N, int ldp,
+                                    float* __restrict__ C, int ldc) {
+  const long long total = (long long)M * N;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(e / N), n = (int)(e - (long long)m * N);
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += P[((long long)z * M + m) * ldp + n];
+    C[(long long)m * ldc + n] = s;
+  }
+}
+
+// v = [p, x, y, sin a_1, cos a_1, ...] per sample.
+__global__ void encode_kernel(const float* __restrict__ q, const float* __restrict__ p, int B, int n, int d_in,
+                              float* __restrict__ X) {
+  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x) {
+    float* x = X + b * d_in;
+    const float* qb = q + b * n;
+    x[0] = p[3 * b];
+    x[1] = p[3 * b + 1];
+    x[2] = p[3 * b + 2];
+    x[3] = qb[0];
+    x[4] = qb[1];
+    for (int a = 0; a < n - 2; ++a) {
+      float s, c;
+      sincosf(qb[2 + a], &s, &c);
+      x[5 + 2 * a] = s;
+      x[6 + 2 * a] = c;
+    }
+  }
+}
+
+// z += b (per column); h = s(z) in place; s'(z) -> S.
+__global__ void bias_silu_kernel(float* __restrict__ Z, const float* __restrict__ bias, long long rows, int H,
+                                 float* __restrict__ S) {
+  const long long total = rows * H;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const float z = Z[e] + bias[e % H];
+    const float sg = 1.f / (1.f + expf(-z));
+    Z[e] = z * sg;
+    S[e] = sg * (1.f + z * (1.f - sg));
+  }
+}
+
+__global__ void add_scalar_kernel(float* __restrict__ x, long long n, const float* __restrict__ c) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    x[e] += *c;
+}
+
+// delta_L = g w_o * S_L
+__global__ void seed_kernel(const float* __restrict__ g, const float* __restrict__ wo, const float* __restrict__ S,
+                            long long rows, int H, float* __restrict__ D) {
+  const long long total = rows * H;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    D[e] = g[e / H] * wo[e % H] * S[e];
+}
+
+__global__ void mul_kernel(float* __restrict__ D, const float* __restrict__ S, long long total) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    D[e] *= S[e];
+}
+
+__global__ void fill_kernel(float* __restrict__ x, long long n, float v) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    x[e] = v;
+}
+
+// dq from dv: x, y direct; angle a: cos a dv[sin a] - sin a dv[cos a]
+__global__ void dq_kernel(const float* __restrict__ q, const float* __restrict__ dV, int B, int n, int d_in,
+                          float* __restrict__ dq) {
+  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x) {
+    const float* v = dV + b * d_in;
+    float* o = dq + b * n;
+    o[0] = v[3];
+    o[1] = v[4];
+    for (int a = 0; a < n - 2; ++a) {
+      float s, c;
+      sincosf(q[b * n + 2 + a], &s, &c);
+      o[2 + a] = c * v[5 + 2 * a] - s * v[6 + 2 * a];
+    }
+  }
+}
+
+int grid1(long long work) {
+  const long long b = (work + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
+struct Ws {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Ws(cudaStream_t st) : s(st) {}
+  template <class T>
+  cudaError_t get(T** out, size_t count) {
+    size_t bytes = count * sizeof(T);
+    cudaError_t e = cudaMallocAsync((void**)out, bytes < 16 ? 16 : bytes, s);
+    if (e == cudaSuccess) ptrs.push_back(*out);
+    return e;
+  }
+  ~Ws() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+};
+
+// C (M x N, ldc) = A(m, k) B(k, n) summed over K; the batch-length reductions
+// (large K, few output tiles) go through `splits` chunks and the partials array.
+cudaError_t gemm(const float* A, long long sam, long long sak, const float* B, long long sbk, long long sbn,
+                 float* C, int ldc, int M, int N, int K, float* partials, size_t partial_floats, cudaStream_t s) {
+  if (M == 0 || N == 0) return cudaSuccess;
+  const int tm = (M + kBM - 1) / kBM, tn = (N + kBN - 1) / kBN;
+  int splits = 1;
+  if ((long long)tm * tn < 2 * 152 && K > 4096 && partials) {
+    splits = (int)std::min<long long>(64, (K + 1023) / 1024);
+    while (splits > 1 && (size_t)splits * M * N > partial_floats) --splits;
+  }
+  const int kc = ((K + splits - 1) / splits + kBK - 1) / kBK * kBK;
+  splits = (K + kc - 1) / kc;
+  if (splits < 1) splits = 1;
+  dim3 grid(tn, tm, splits);
+  if (splits == 1) {
+    gemm_kernel<<<grid, kGemmThreads, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, kc);
+  } else {
+    gemm_kernel<<<grid, kGemmThreads, 0, s>>>(A, sam, sak, B, sbk, sbn, partials, N, M, N, K, kc);
+    sum_partials_kernel<<<grid1((long long)M * N), 256, 0, s>>>(partials, splits, M, N, N, C, ldc);
+  }
+  return cudaGetLastError();
+}
+
+bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+struct Shape {
+  int n, H, L, d_in;
+  size_t off_out;  // offset of w_o in the flat layout
+  size_t total;
+  size_t off(int l) const {  // offset of W_l (l = 1 .. L)
+    if (l == 1) return 0;
+    return (size_t)H * d_in + H + (size_t)(l - 2) * ((size_t)H * H + H);
+  }
+  int fan_in(int l) const { return l == 1 ? d_in : H; }
+};
+
+int check(const gcdf_fit_desc* d, const float* w, const float* q, const float* p, int B, Shape& sh) {
+  if (!d) return set_error(GCDF_EINVAL, "desc is NULL");
+  if (d->n_dof < 3 || d->n_dof > kMaxDof || d->hidden < 1 || d->hidden > 4096 || d->n_hidden_layers < 1 ||
+      d->n_hidden_layers > 16)
+    return set_error(GCDF_EINVAL, "bad shape (n_dof %d, hidden %d, layers %d)", d->n_dof, d->hidden,
+                     d->n_hidden_layers);
+  if (B < 0) return set_error(GCDF_EINVAL, "batch %d < 0", B);
+  if (B > 0 && (!w || !q || !p || !al16(w) || !al16(q) || !al16(p)))
+    return set_error(GCDF_EINVAL, "weights, q or p NULL or not 16-byte aligned");
+  sh.n = d->n_dof;
+  sh.H = d->hidden;
+  sh.L = d->n_hidden_layers;
+  sh.d_in = 3 + 2 + 2 * (sh.n - 2);
+  sh.off_out = sh.off(sh.L + 1);
+  sh.total = sh.off_out + sh.H + 1;
+  return GCDF_OK;
+}
+
+// Forward pass storing h_l (Hs[l], l = 0 .. L, Hs[0] = v) and s'(z_l) (Ss[l - 1]).
+int forward(const Shape& sh, const float* w, const float* q, const float* p, int B, float** Hs, float** Ss, float* f,
+            float* partials, size_t pfl, cudaStream_t s) {
+  cudaError_t e;
+  encode_kernel<<<grid1(B), 256, 0, s>>>(q, p, B, sh.n, sh.d_in, Hs[0]);
+  for (int l = 1; l <= sh.L; ++l) {
+    const int K = sh.fan_in(l);
+    const float* W = w + sh.off(l);
+    // Z (B x H) = H_{l-1} (B x K) W^T
+    if ((e = gemm(Hs[l - 1], K, 1, W, 1, K, Hs[l], sh.H, B, sh.H, K, nullptr, 0, s)))
+      return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+    bias_silu_kernel<<<grid1((long long)B * sh.H), 256, 0, s>>>(Hs[l], W + (size_t)sh.H * K, B, sh.H, Ss[l - 1]);
+  }
+  if (f) {
+    // f (B x 1) = H_L w_o + b_o
+    if ((e = gemm(Hs[sh.L], sh.H, 1, w + sh.off_out, 1, 1, f, 1, B, 1, sh.H, nullptr, 0, s)))
+      return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+    add_scalar_kernel<<<grid1(B), 256, 0, s>>>(f, B, w + sh.off_out + sh.H);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit forward launch: %s", cudaGetErrorString(e));
+  return GCDF_OK;
+}
+
+}  // namespace
+}  // namespace gcdf
+
+using namespace gcdf;
+
+extern "C" {
+
+int gcdf_fit_forward(const gcdf_fit_desc* desc, const float* weights, const float* q, const float* p, int batch,
+                     float* f, gcdf_stream_t stream) {
+  Shape sh;
+  int rc = check(desc, weights, q, p, batch, sh);
+  if (rc) return rc;
+  if (batch == 0) { clear_error(); return GCDF_OK; }
+  if (!f || !al16(f)) return set_error(GCDF_EINVAL, "f NULL or not 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  Ws ws(s);
+  float* Hs[18];
+  float* Ss[17];
+  cudaError_t e;
+  if ((e = ws.get(&Hs[0], (size_t)batch * sh.d_in))) return set_error(GCDF_ENOMEM, "cudaMallocAsync");
+  // two alternating activation buffers suffice without a backward pass
+  float *h0, *h1, *sc;
+  if ((e = ws.get(&h0, (size_t)batch * sh.H)) || (e = ws.get(&h1, (size_t)batch * sh.H)) ||
+      (e = ws.get(&sc, (size_t)batch * sh.H)))
+    return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  for (int l = 1; l <= sh.L; ++l) {
+    Hs[l] = (l & 1) ? h0 : h1;
+    Ss[l - 1] = sc;
+  }
+  rc = forward(sh, weights, q, p, batch, Hs, Ss, f, nullptr, 0, s);
+  if (rc) return rc;
+  clear_error();
+  return GCDF_OK;
+}
+
+int gcdf_fit_vjp(const gcdf_fit_desc* desc, const float* weights, const float* q, const float* p, int batch,
+                 const float* g_f, float* dweights, float* dq, gcdf_stream_t stream) {
+  Shape sh;
+  int rc = check(desc, weights, q, p, batch, sh);
+  if (rc) return rc;
+  if (!dweights || !al16(dweights)) return set_error(GCDF_EINVAL, "dweights NULL or not 16-byte aligned");
+  if (dq && !al16(dq)) return set_error(GCDF_EINVAL, "dq not 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (batch == 0) {
+    if ((e = cudaMemsetAsync(dweights, 0, sh.total * sizeof(float), s)))
+      return set_error(GCDF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    clear_error();
+    return GCDF_OK;
+  }
+  if (!g_f || !al16(g_f)) return set_error(GCDF_EINVAL, "g_f NULL or not 16-byte aligned");
+  Ws ws(s);
+  float* Hs[18];
+  float* Ss[17];
+  float *D0, *D1, *ones, *partials;
+  const size_t pfl = (size_t)64 * sh.H * (sh.H > sh.d_in ? sh.H : sh.d_in);
+  if ((e = ws.get(&Hs[0], (size_t)batch * sh.d_in))) return set_error(GCDF_ENOMEM, "cudaMallocAsync");
+  for (int l = 1; l <= sh.L; ++l)
+    if ((e = ws.get(&Hs[l], (size_t)batch * sh.H)) || (e = ws.get(&Ss[l - 1], (size_t)batch * sh.H)))
+      return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  const size_t dcols = (size_t)(sh.H > sh.d_in ? sh.H : sh.d_in);
+  if ((e = ws.get(&D0, (size_t)batch * dcols)) || (e = ws.get(&D1, (size_t)batch * dcols)) ||
+      (e = ws.get(&ones, (size_t)batch)) ||
+      (e = ws.get(&partials, pfl)))
+    return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  rc = forward(sh, weights, q, p, batch, Hs, Ss, nullptr, partials, pfl, s);
+  if (rc) return rc;
+  fill_kernel<<<grid1(batch), 256, 0, s>>>(ones, batch, 1.f);
+  const int H = sh.H;
+  float* dwo = dweights + sh.off_out;
+  // dw_o (H x 1) = H_L^T g;  db_o = g^T 1
+  if ((e = gemm(Hs[sh.L], 1, H, g_f, 1, 1, dwo, 1, H, 1, batch, partials, pfl, s)) ||
+      (e = gemm(g_f, 1, 1, ones, 1, 1, dwo + H, 1, 1, 1, batch, partials, pfl, s)))
+    return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+  // delta_L = g w_o * s'(z_L)
+  float* D = D1;
+  seed_kernel<<<grid1((long long)batch * H), 256, 0, s>>>(g_f, weights + sh.off_out, Ss[sh.L - 1], batch, H, D);
+  for (int l = sh.L; l >= 1; --l) {
+    const int K = sh.fan_in(l);
+    const float* W = weights + sh.off(l);
+    float* dW = dweights + sh.off(l);
+    // dW_l (H x K) = delta^T (H x B) H_{l-1} (B x K);  db_l = delta^T 1
+    if ((e = gemm(D, 1, H, Hs[l - 1], K, 1, dW, K, H, K, batch, partials, pfl, s)) ||
+        (e = gemm(D, 1, H, ones, 1, 1, dW + (size_t)H * K, 1, H, 1, batch, partials, pfl, s)))
+      return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+    if (l > 1 || dq) {
+      // back (B x K) = delta (B x H) W_l (H x K)
+      float* back = (D == D1) ? D0 : D1;  // never the buffer it reads
+      if ((e = gemm(D, H, 1, W, K, 1, back, K, batch, K, H, nullptr, 0, s)))
+        return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+      if (l > 1) {
+        mul_kernel<<<grid1((long long)batch * K), 256, 0, s>>>(back, Ss[l - 2], (long long)batch * K);
+        D = back;
+      } else {
+        dq_kernel<<<grid1(batch), 256, 0, s>>>(q, back, batch, sh.n, sh.d_in, dq);
+      }
+    }
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit backward launch: %s", cudaGetErrorString(e));
+  clear_error();
+  return GCDF_OK;
+}
+
+}  // extern "C"

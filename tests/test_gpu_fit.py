@@ -1,0 +1,82 @@
+"""Differentiable fit (gcdf_fit_forward / gcdf_fit_vjp and the autograd
+Function) against the FP64 oracle of oracle/fit.py."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fit, metrics
+
+from _helpers import lib, need_gpu, small_net, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(n_dof, B, seed):
+    r = synth.SplitMix64(seed)
+    q = np.stack([synth.random_config(r, n_dof, -2.0, 2.0) for _ in range(B)]).astype(np.float32)
+    p = synth.uniform_points(r, B, [-2, -2, 0], [2, 2, 2]).astype(np.float32)
+    return q, p
+
+
+@pytest.mark.parametrize("n,H,L,B", [(10, 512, 5, 2048), (9, 256, 4, 1000), (3, 96, 2, 333), (12, 64, 1, 5000)])
+def test_forward_and_vjp_match_the_oracle(n, H, L, B):
+    torch = need_gpu()
+    g = lib()
+    shape, w = small_net(n, hidden=H, n_layers=L)
+    q, p = _batch(n, B, n * 100 + B)
+    gf = np.random.default_rng(B).normal(size=B).astype(np.float32)
+    wd = to_dev(torch, np.asarray(w, np.float32))
+    f = g.fit_forward((n, H, L), wd, to_dev(torch, q), to_dev(torch, p)).cpu().numpy()
+    f_ref, _ = fit.forward(n, H, L, w, q.astype(np.float64), p.astype(np.float64))
+    assert metrics.rel_err_scalar(f, f_ref).max() <= 1e-5
+    dw, dq = g.fit_vjp((n, H, L), wd, to_dev(torch, q), to_dev(torch, p), to_dev(torch, gf))
+    dw_ref, dq_ref = fit.vjp(n, H, L, w, q.astype(np.float64), p.astype(np.float64), gf.astype(np.float64))
+    dw = dw.cpu().numpy()
+    # the whole gradient, and each block of the flat layout on its own scale
+    assert np.linalg.norm(dw - dw_ref) <= 1e-5 * np.linalg.norm(dw_ref)
+    lay, _ = fit._layers(n, H, L, w)
+    for (off, o, i) in lay:
+        blk = slice(off, off + o * i + o)
+        assert np.linalg.norm(dw[blk] - dw_ref[blk]) <= 1e-5 * np.linalg.norm(dw_ref[blk])
+    assert metrics.rel_err_vector(dq.cpu().numpy(), dq_ref).max() <= 1e-5
+
+
+def test_vjp_is_deterministic_and_autograd_agrees():
+    torch = need_gpu()
+    g = lib()
+    n, H, L, B = 9, 128, 3, 4096
+    shape, w = small_net(n, hidden=H, n_layers=L)
+    q, p = _batch(n, B, 7)
+    wd = to_dev(torch, np.asarray(w, np.float32)).requires_grad_(True)
+    qd = to_dev(torch, q).requires_grad_(True)
+    pd = to_dev(torch, p)
+    gf = to_dev(torch, np.random.default_rng(1).normal(size=B).astype(np.float32))
+    a = g.fit_vjp((n, H, L), wd.detach(), qd.detach(), pd, gf)
+    b = g.fit_vjp((n, H, L), wd.detach(), qd.detach(), pd, gf)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    f = g.field(wd, qd, pd, (n, H, L))
+    (f * gf).sum().backward()
+    assert torch.equal(wd.grad, a[0]) and torch.equal(qd.grad, a[1])
+
+
+def test_fit_lowers_the_distance_loss():
+    """Teacher-student fit with the distance loss of Table I: 40 Adam steps on
+    the flat FP32 weights through the autograd Function."""
+    torch = need_gpu()
+    g = lib()
+    n, H, L, B = 9, 128, 3, 8192
+    _, w_teacher = small_net(n, hidden=H, n_layers=L, seed=1)
+    _, w0 = small_net(n, hidden=H, n_layers=L, seed=2)
+    q, p = _batch(n, B, 9)
+    qd, pd = to_dev(torch, q), to_dev(torch, p)
+    target = g.fit_forward((n, H, L), to_dev(torch, np.asarray(w_teacher, np.float32)), qd, pd)
+    wd = to_dev(torch, np.asarray(w0, np.float32)).requires_grad_(True)
+    opt = torch.optim.Adam([wd], lr=2e-3)
+    losses = []
+    for _ in range(40):
+        opt.zero_grad()
+        loss = ((g.field(wd, qd, pd, (n, H, L)) - target) ** 2).mean()
+        loss.backward()
+        opt.step()
+        losses.append(float(loss.detach()))
+    assert losses[-1] < 0.5 * losses[0]
