@@ -12,6 +12,7 @@ value+gradient pairs reduced to 128 costs and gradients.  Inputs are synthetic
     python bench.py --serve                 # served-planning latency (see run_serve)
     python bench.py --plan [--plan-problems P]   # batched trajectory optimisation (see run_plan)
     python bench.py --aux                   # partition, Jacobian scatter, projection kernels
+    python bench.py --fit                   # differentiable-fit training step (see run_fit)
 
 Multi-GPU: one process per GPU (torchrun); every rank runs its own replica of
 the workload (weak scaling, no collective on the data path); the time is the
@@ -649,6 +650,45 @@ def run_aux(args):
     return 0
 
 
+def run_fit(args):
+    """One training step of the differentiable fit (distance loss of Table I):
+    forward of every sample, the loss gradient, and the vector-Jacobian
+    product with respect to the flat FP32 weights — 10-DOF net, 5 hidden
+    layers of 512, SiLU, batch 65,536 (the differentiable-fit configuration),
+    synthetic samples and targets.  Timed with CUDA events; inputs resident."""
+    import torch
+    import paper_2601_18548_gb300 as g
+    n, H, L, B = 10, 512, 5, args.fit_batch
+    shape = synth.NetShape(n, H, L)
+    w = torch.from_numpy(synth.he_uniform_weights(shape, seed=0)).cuda()
+    r = synth.SplitMix64(91)
+    q = torch.from_numpy(np.stack([synth.random_config(r, n, -3.0, 3.0) for _ in range(B)]).astype(np.float32)).cuda()
+    p = torch.from_numpy(synth.uniform_points(r, B, [-3, -3, 0], [3, 3, 2]).astype(np.float32)).cuda()
+    target = torch.zeros(B, device="cuda")
+
+    def step():
+        f = g.fit_forward((n, H, L), w, q, p)
+        gf = (2.0 / B) * (f - target)
+        return g.fit_vjp((n, H, L), w, q, p, gf, want_dq=False)
+    ms = _time_events(step, reps=args.steps if args.steps < 20 else 10)
+    d_in = 3 + 2 + 2 * (n - 2)
+    # GEMM FLOPs: forward (d_in H + (L-1) H^2 + H) x 2 per sample, twice (the
+    # forward and the forward inside the VJP), weight gradients the same
+    # again, back-products (L-1) H^2 x 2
+    fwd = 2 * (d_in * H + (L - 1) * H * H + H)
+    flops = B * (2 * fwd + fwd + 2 * (L - 1) * H * H)
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+    line = {"metric": "differentiable fit training step", "unit": "samples/s", "value": B / (ms / 1e3),
+            "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"net": "10-DOF 5 x 512 SiLU", "batch": B, "loss": "distance (Table I)"},
+            "ms_per_step": ms,
+            "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / (ms / 1e3) / 1e12 / peak,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (derived)"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -668,6 +708,8 @@ def main():
     ap.add_argument("--plan", action="store_true", help="batched trajectory-optimisation benchmark instead")
     ap.add_argument("--plan-problems", type=int, default=64)
     ap.add_argument("--aux", action="store_true", help="partition / Jacobian / projection kernels instead")
+    ap.add_argument("--fit", action="store_true", help="differentiable-fit training step instead")
+    ap.add_argument("--fit-batch", type=int, default=65536)
     args = ap.parse_args()
     global WAYPOINTS, POINTS
     WAYPOINTS, POINTS = args.waypoints, args.points
@@ -679,6 +721,8 @@ def main():
         return run_plan(args)
     if args.aux:
         return run_aux(args)
+    if args.fit:
+        return run_fit(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
