@@ -332,6 +332,10 @@ def run_gpu(args):
         peak = float(peaks["bf16_tflops"])
         bound, punit = "tensor", "TFLOP/s"
         peak_note = f"bf16 dense burst, {peak_src} (fp16 dense rate is the same)"
+    elif args.precision == "fp8":
+        peak = 2.0 * float(peaks["bf16_tflops"])
+        bound, punit = "tensor", "TFLOP/s"
+        peak_note = f"fp8 dense = 2 x bf16 dense burst {peak_src} (nominal ratio 4.5 / 2.25 PFLOP/s)"
     else:
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         bound, punit = "alu", "TFLOP/s"
@@ -351,7 +355,7 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"bf16": "bf16", "fp16": "f16", "fp32": "f32"}[args.precision],
+        "dtype": {"bf16": "bf16", "fp16": "f16", "fp8": "e4m3", "fp32": "f32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": wl.name + "_softmin_T0.02", "n_waypoints": int(q.shape[0]),
                    "n_points": int(p.shape[0]), "pairs_per_step": P, "net": "9-DOF 4x256 SiLU",
@@ -695,7 +699,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp8", "fp32"])
     ap.add_argument("--ref-budget", type=float, default=12.0, help="seconds of oracle work per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch from ncu")

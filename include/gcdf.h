@@ -71,8 +71,11 @@ enum gcdf_status {
 enum gcdf_precision {
   GCDF_FP32 = 0, /* FP32 weights and activations on CUDA cores */
   GCDF_BF16 = 1, /* BF16 weights and activations, FP32 accumulation, tcgen05 tensor cores */
-  GCDF_FP16 = 2  /* FP16 weights and activations, FP32 accumulation, same tensor-core kernel;
+  GCDF_FP16 = 2, /* FP16 weights and activations, FP32 accumulation, same tensor-core kernel;
                     three more mantissa bits than BF16 at the same throughput, range +-65504 */
+  GCDF_FP8 = 3   /* FP8 E4M3 weights (one scale per layer: max |W_l| / 448) and activations, FP32
+                    accumulation, tcgen05 kind::f8f6f4; reverse-sweep operands carry a factor 64;
+                    the epilogue arithmetic and the stash stay FP16 */
 };
 
 enum gcdf_reduction {
@@ -83,8 +86,8 @@ enum gcdf_reduction {
 
 typedef struct gcdf_net_desc {
   int n_dof;           /* n: x, y, then n - 2 angles; 3 <= n <= 12 */
-  int hidden;          /* H: hidden width; FP32: 64, 128, 256 or 512; BF16/FP16: 256 */
-  int n_hidden_layers; /* L: number of SiLU layers, >= 2 (FP32: <= 5, BF16/FP16: <= 4) */
+  int hidden;          /* H: hidden width; FP32: 64, 128, 256 or 512; BF16/FP16/FP8: 256 */
+  int n_hidden_layers; /* L: number of SiLU layers, >= 2 (FP32: <= 5, BF16/FP16/FP8: <= 4) */
   int precision;       /* enum gcdf_precision */
 } gcdf_net_desc;
 

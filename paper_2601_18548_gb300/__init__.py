@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import GcdfError  # noqa: F401
 
-_PREC = {"fp32": _lib.GCDF_FP32, "bf16": _lib.GCDF_BF16, "fp16": _lib.GCDF_FP16}
+_PREC = {"fp32": _lib.GCDF_FP32, "bf16": _lib.GCDF_BF16, "fp16": _lib.GCDF_FP16, "fp8": _lib.GCDF_FP8}
 _RED = {"min": _lib.GCDF_RED_MIN, "softmin": _lib.GCDF_RED_SOFTMIN, "hinge": _lib.GCDF_RED_HINGE}
 
 

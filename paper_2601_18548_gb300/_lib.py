@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libgcdf.so")
 
 GCDF_OK, GCDF_EINVAL, GCDF_ENOMEM, GCDF_ECUDA, GCDF_EUNSUPPORTED = 0, 1, 2, 3, 4
 GCDF_EAGAIN, GCDF_PENDING, GCDF_ETIMEOUT = 5, 6, 7
-GCDF_FP32, GCDF_BF16, GCDF_FP16 = 0, 1, 2
+GCDF_FP32, GCDF_BF16, GCDF_FP16, GCDF_FP8 = 0, 1, 2, 3
 GCDF_RED_MIN, GCDF_RED_SOFTMIN, GCDF_RED_HINGE = 0, 1, 2
 
 # Every function the header declares, with (restype, argtypes).

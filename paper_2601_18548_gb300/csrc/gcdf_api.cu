@@ -66,7 +66,7 @@ int shape_check(const gcdf_net_desc* d) {
   if (!d) return fail(GCDF_EINVAL, "desc is NULL");
   if (d->n_dof < 3 || d->n_dof > kMaxDof) return fail(GCDF_EINVAL, "n_dof %d outside [3, %d]", d->n_dof, kMaxDof);
   if (d->n_hidden_layers < 2) return fail(GCDF_EINVAL, "n_hidden_layers %d < 2", d->n_hidden_layers);
-  if (d->precision != GCDF_FP32 && d->precision != GCDF_BF16 && d->precision != GCDF_FP16)
+  if (d->precision != GCDF_FP32 && d->precision != GCDF_BF16 && d->precision != GCDF_FP16 && d->precision != GCDF_FP8)
     return fail(GCDF_EINVAL, "unknown precision %d", d->precision);
   if (d->hidden <= 0 || d->hidden > 512 || d->hidden % 32)
     return fail(GCDF_EINVAL, "hidden %d must be a positive multiple of 32, at most 512", d->hidden);
@@ -122,9 +122,11 @@ int build_fp32_images(gcdf_net* net, const float* w) {
 
 int build_tc_images(gcdf_net* net, const float* w) {
   const int H = net->H, L = net->L;
-  const bool f16 = net->precision == GCDF_FP16;
+  const int fmt = net->precision == GCDF_FP8 ? 2 : (net->precision == GCDF_FP16 ? 1 : 0);
+  // 16-bit elements (FP8 uses the first half of the same buffer)
   std::vector<uint16_t> image(tc_image_elems(H, L, net->d_q));
-  tc_build_image(w, H, L, net->d_q, net->d_in, f16, image.data());
+  memset(net->tcw.fp8_scale, 0, sizeof(net->tcw.fp8_scale));
+  tc_build_image(w, H, L, net->d_q, net->d_in, fmt, image.data(), net->tcw.fp8_scale);
   std::vector<float> bias((size_t)(L - 1) * H), w1p((size_t)H * 3);
   size_t off = (size_t)H * net->d_in + H;
   for (int l = 0; l < L - 1; ++l) {
@@ -138,8 +140,8 @@ int build_tc_images(gcdf_net* net, const float* w) {
   if ((rc = dev_alloc_copy(&net->tc_bias, bias.data(), bias.size()))) return rc;
   if ((rc = dev_alloc_copy(&net->tc_w1p, w1p.data(), w1p.size()))) return rc;
   TcWeights& tw = net->tcw;
-  if (tc_encode_maps(net->slabs, H, L, net->d_q, f16, tw)) return fail(GCDF_ECUDA, "cuTensorMapEncodeTiled failed");
-  tw.f16 = f16 ? 1 : 0;
+  if (tc_encode_maps(net->slabs, H, L, net->d_q, fmt, tw)) return fail(GCDF_ECUDA, "cuTensorMapEncodeTiled failed");
+  tw.fmt = fmt;
   tw.bias = net->tc_bias;
   tw.W1p = net->tc_w1p;
   tw.wout = net->w_dev + net->off_wout;

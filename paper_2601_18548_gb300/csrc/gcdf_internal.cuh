@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 #include "../../include/gcdf.h"
@@ -212,13 +213,15 @@ struct TcWeights {
   const float* wout;           // [H]
   float bout;
   int H, L, d_q, nj;
-  int f16;                     // operand format: 1 = FP16, 0 = BF16
+  int fmt;                     // operand format: 0 = BF16, 1 = FP16, 2 = FP8 E4M3
+  float fp8_scale[8];          // FP8: weight scales, forward layers 2..L, reverse layers, W_1q
   int* err;                    // device status word (set when a bounded wait gives up)
 };
 cudaError_t launch_tc(const WorkDesc& w, const TcWeights& tw, int num_sms, cudaStream_t s);
 size_t tc_image_elems(int H, int L, int d_q);
-void tc_build_image(const float* W, int H, int L, int d_q, int d_in, bool f16, uint16_t* out);
-int tc_encode_maps(const uint16_t* image, int H, int L, int d_q, bool f16, TcWeights& tw);
+// Operand image (16-bit elements, or bytes for FP8) and, for FP8, the scales.
+void tc_build_image(const float* W, int H, int L, int d_q, int d_in, int fmt, void* out, float* scales);
+int tc_encode_maps(const void* image, int H, int L, int d_q, int fmt, TcWeights& tw);
 int tc_nj(int d_q);
 
 }  // namespace gcdf

@@ -169,6 +169,7 @@ __device__ __forceinline__ int total_tiles(const WorkDesc& w) {
 
 constexpr uint32_t kOne2 = 0x3C003C00u;   // (1.0, 1.0) in FP16
 constexpr uint32_t kHalf2 = 0x38003800u;  // (0.5, 0.5) in FP16
+constexpr float kGradScale8 = 64.f;         // FP8 reverse operands hold 64 g (E4M3 normals start at 2^-6)
 
 // Packed SiLU of u = z / 2: returns s(z) and 2 s'(z) for two values.
 __device__ __forceinline__ void silu2(uint32_t u, uint32_t& h, uint32_t& s2) {
@@ -177,9 +178,10 @@ __device__ __forceinline__ void silu2(uint32_t u, uint32_t& h, uint32_t& s2) {
   s2 = ptx::hfma2(h, ptx::hsub2(kOne2, t), ptx::hadd2(kOne2, t));
 }
 
-template <bool kF16>
+template <int kFmt>
 __device__ __forceinline__ uint32_t to_operand(uint32_t f16pair) {
-  return kF16 ? f16pair : ptx::f16x2_to_bf16x2(f16pair);
+  // BF16 converts here; FP16 is the operand; FP8 is converted where it is stored
+  return kFmt == 0 ? ptx::f16x2_to_bf16x2(f16pair) : f16pair;
 }
 
 // u_1 = z_1 / 2 for columns c, c+1 of this thread's pair in packed FP16:
@@ -328,10 +330,16 @@ __device__ __forceinline__ void warp_combine_quads(int mode, float T, const Part
   out[lane] = acc;
 }
 
-template <bool kF16>
+// kFmt: operand format, 0 = BF16, 1 = FP16, 2 = FP8 E4M3 (per-layer scales).
+template <int kFmt>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
                 const __grid_constant__ CUtensorMap map_j, const TcWeights tw) {
+  constexpr bool kF16 = kFmt == 1;
+  constexpr bool kF8 = kFmt == 2;
+  // 16-bit operands: a K = 128 stage is two 64-element slabs of 128-byte rows;
+  // FP8: one 128-element slab (the shared-memory map is the same, half used)
+  constexpr int kSlabsPerStage = kF8 ? 1 : 2;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t base = (ptx::smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - ptx::smem_u32(smem_raw));
@@ -395,7 +403,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     s_w1p[i] = make_uint4(ptx::pack_f16x2(0.5f * tw.W1p[3 * c], 0.5f * tw.W1p[3 * c + 3]),
                           ptx::pack_f16x2(0.5f * tw.W1p[3 * c + 1], 0.5f * tw.W1p[3 * c + 4]),
                           ptx::pack_f16x2(0.5f * tw.W1p[3 * c + 2], 0.5f * tw.W1p[3 * c + 5]), 0u);
-    s_woh[i] = ptx::pack_f16x2(0.5f * tw.wout[c], 0.5f * tw.wout[c + 1]);
+    const float gs = kF8 ? 0.5f * kGradScale8 : 0.5f;  // FP8 gradient operands carry x64
+    s_woh[i] = ptx::pack_f16x2(gs * tw.wout[c], gs * tw.wout[c + 1]);
   }
   for (int i = tid; i < (L - 1) * (kH / 2); i += kThreads) {
     const int l = i / (kH / 2), c = 2 * (i % (kH / 2));
@@ -423,9 +432,10 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         const int st = pst;
         if (g >= kStages && !wait_role(bar(base, B_EMPTY0 + st), puse ^ 1u, abort_flag, tw.err)) return false;
         const uint32_t fb = full_lead + 8u * (uint32_t)st;
-        if (leader) ptx::mbar_arrive_expect_tx(bar(base, B_FULL0 + st), 4u * slab_bytes);  // 2 slabs x 2 CTAs
+        // slabs x 2 CTAs
+        if (leader) ptx::mbar_arrive_expect_tx(bar(base, B_FULL0 + st), 2u * kSlabsPerStage * slab_bytes);
         ptx::tma_load_2d_pair(base + kOffRing + st * kStageBytes, map, x0, y, fb);
-        ptx::tma_load_2d_pair(base + kOffRing + st * kStageBytes + kSlabBytes, map, x0 + 64, y, fb);
+        if (!kF8) ptx::tma_load_2d_pair(base + kOffRing + st * kStageBytes + kSlabBytes, map, x0 + 64, y, fb);
         ++g;
         if (++pst == kStages) { pst = 0; puse ^= 1u; }
         return true;
@@ -453,8 +463,9 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
   } else if (warp == 1) {
     // ================= MMA issuer (even CTA, for both) =================
     if (lane == 0 && my_tiles > 0 && leader) {
-      const uint32_t id128 = ptx::idesc_f16kind(2 * kTile, kHalf, kF16);
-      const uint32_t idj = ptx::idesc_f16kind(2 * kTile, nj, kF16);
+      // (E4M3 x E4M3 has the format code 0 of FP16 x FP16 in the same fields)
+      const uint32_t id128 = ptx::idesc_f16kind(2 * kTile, kHalf, kF16 || kF8);
+      const uint32_t idj = ptx::idesc_f16kind(2 * kTile, nj, kF16 || kF8);
       long long g = 0;         // stages consumed
       int cst = 0;             // ring stage of g
       uint32_t cph = 0;        // its FULL phase parity
@@ -469,12 +480,19 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       // one stage: K = 128 of a chain (8 MMAs of K = 16), then release the stage in both CTAs
       auto stage_mmas = [&](uint32_t dtm, uint64_t da, uint32_t idd, bool first) {
         const uint64_t db = dRing + (uint64_t)(cst * (kStageBytes >> 4));
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
+        // 32 bytes of K per MMA: K = 16 of 16-bit operands over two slabs, K = 32 of FP8 over one
+        if constexpr (kF8) {
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
-            ptx::mma_pair(dtm, da + (uint64_t)(q * (kTile * 128 >> 4) + 2 * ks),
-                          db + (uint64_t)(q * (kSlabBytes >> 4) + 2 * ks), idd, (first && q == 0 && ks == 0) ? 0u : 1u);
+            ptx::mma_pair_f8(dtm, da + (uint64_t)(2 * ks), db + (uint64_t)(2 * ks), idd, (first && ks == 0) ? 0u : 1u);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              ptx::mma_pair(dtm, da + (uint64_t)(q * (kTile * 128 >> 4) + 2 * ks),
+                            db + (uint64_t)(q * (kSlabBytes >> 4) + 2 * ks), idd, (first && q == 0 && ks == 0) ? 0u : 1u);
+        }
         ptx::mma_commit_pair(bar(base, B_EMPTY0 + cst));
         ++g;
         if (++cst == kStages) { cst = 0; cph ^= 1u; }
@@ -508,7 +526,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               }
               // both CTAs' slabs written by TMA: the transaction barrier orders them before the MMAs
               if (!wait_role(bar(base, B_FULL0 + cst), cph, abort_flag, tw.err)) { ok = false; break; }
-              stage_mmas(dtm, dAbuf + (uint64_t)((2 * pr) * (kTile * 128) >> 4), idd, pr == 0);
+              stage_mmas(dtm, dAbuf + (uint64_t)((kSlabsPerStage * pr) * (kTile * 128) >> 4), idd, pr == 0);
             }
             if (ok) ptx::mma_commit_pair(bar(base, jstep ? B_ACCJ : B_ACC0 + hh));
           }
@@ -557,9 +575,17 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     auto aoff = [&](int c0, int q) -> uint32_t {
       return (c0 >> 6) * (kTile * 128) + rbase + (((((c0 & 63) >> 3) + q) ^ r7) << 4);
     };
+    // columns c0 .. c0 + 15 (eight FP16 / BF16 pairs) of this row
     auto store8c = [&](uint32_t abuf, int c0, const uint32_t* o) {
-      ptx::st_shared_v4(abuf + aoff(c0, 0), o[0], o[1], o[2], o[3]);
-      ptx::st_shared_v4(abuf + aoff(c0, 1), o[4], o[5], o[6], o[7]);
+      if constexpr (kF8) {
+        // 16 FP8 columns = one 16-byte chunk of a 128-element row
+        const uint32_t off = (c0 >> 7) * (kTile * 128) + rbase + ((((c0 & 127) >> 4) ^ r7) << 4);
+        ptx::st_shared_v4(abuf + off, ptx::e4m3x4(o[0], o[1]), ptx::e4m3x4(o[2], o[3]), ptx::e4m3x4(o[4], o[5]),
+                          ptx::e4m3x4(o[6], o[7]));
+      } else {
+        ptx::st_shared_v4(abuf + aoff(c0, 0), o[0], o[1], o[2], o[3]);
+        ptx::st_shared_v4(abuf + aoff(c0, 1), o[4], o[5], o[6], o[7]);
+      }
     };
     // the half's epilogue is done in this warp: release the accumulator half and
     // the A-buffer columns it wrote to the even CTA's MMA issuer, one arrival per
@@ -615,7 +641,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         for (int i = 0; i < 8; ++i) {
           const uint32_t u = first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2);
           const uint32_t tt = ptx::htanh2(u);
-          o[i] = to_operand<kF16>(ptx::hfma2(u, tt, u));
+          o[i] = to_operand<kFmt>(ptx::hfma2(u, tt, u));
         }
         store8c(abuf, c0 + cc, o);
       }
@@ -636,7 +662,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         for (int i = 0; i < 8; ++i) {
           const uint32_t u = first_layer_u2(s_w1p[(cw + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2);
           const uint32_t tt = ptx::htanh2(u);
-          o[i] = to_operand<kF16>(ptx::hfma2(u, tt, u));
+          o[i] = to_operand<kFmt>(ptx::hfma2(u, tt, u));
         }
         ptx::tmem_st8(t_h1 + cc / 2, o);
       }
@@ -673,6 +699,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
           if (s < L - 2) {
             // middle forward layer l = s + 2: h_l -> A, 2 s'(z_l) -> stash
             const uint32_t t_st = t_lane + 256 + 128 * s + (c0 >> 1);
+            const float sc = kF8 ? tw.fp8_scale[s] : 1.f;  // FP8: the layer's weight scale
             const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + s * (kH / 2) + (c0 >> 1));
             // two 16-column chunks are loaded at once, so the second load's
             // latency hides behind the first chunk's arithmetic
@@ -690,10 +717,11 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               uint32_t o[8], st2[8];
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                const uint32_t zp = ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+                const uint32_t zp = kF8 ? ptx::pack_f16x2(sc * __uint_as_float(v[2 * i]), sc * __uint_as_float(v[2 * i + 1]))
+                                        : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
                 uint32_t hh;
                 silu2(ptx::hfma2(zp, kHalf2, bh[i]), hh, st2[i]);
-                o[i] = to_operand<kF16>(hh);
+                o[i] = to_operand<kFmt>(hh);
               }
               store8c(obuf, c0 + cc, o);
               ptx::tmem_st8(t_st + cc / 2, st2);
@@ -703,6 +731,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
           } else if (s == L - 2) {
             // last forward layer: f partial (FP32 sum), g_L = w_o s'(z_L) -> A
             fpart = 0.f;
+            const float sc = kF8 ? tw.fp8_scale[L - 2] : 1.f;
             const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + (L - 2) * (kH / 2) + (c0 >> 1));
 #pragma unroll 1
             for (int cc = 0; cc < 64; cc += 16) {
@@ -717,12 +746,13 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               uint32_t o[8];
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                const uint32_t zp = ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+                const uint32_t zp = kF8 ? ptx::pack_f16x2(sc * __uint_as_float(v[2 * i]), sc * __uint_as_float(v[2 * i + 1]))
+                                        : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
                 uint32_t hh, s2;
                 silu2(ptx::hfma2(zp, kHalf2, bh[i]), hh, s2);
                 const float2 wo = *reinterpret_cast<const float2*>(s_wo + c0 + cc + 2 * i);
                 fpart = fmaf(wo.x, ptx::f16lo(hh), fmaf(wo.y, ptx::f16hi(hh), fpart));
-                o[i] = to_operand<kF16>(ptx::hmul2(wh[i], s2));
+                o[i] = to_operand<kFmt>(ptx::hmul2(wh[i], s2));
               }
               store8c(obuf, c0 + cc, o);
             }
@@ -731,6 +761,9 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
           } else {
             // reverse step: g_{l-1} = acc * 2 s'(z_{l-1}), acc = (W_l^T / 2) g_l
             const int lm1 = 2 * L - 2 - s;
+            // FP8: acc = (64 / s_rev) (W^T / 2) g, so acc * s_rev is the next
+            // operand already carrying its x64
+            const float sc = kF8 ? tw.fp8_scale[L - 1 + (2 * L - 3 - s)] : 1.f;
             // 2 s'(z_1) sits in the stash columns of z_{L-1} when there is a stash
             const int lsrc = (lm1 >= 2) ? lm1 : (L - 1);
             const bool stashed = lm1 >= 2 || L >= 3;
@@ -750,8 +783,9 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               uint32_t o[8];
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                const uint32_t ap = ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-                o[i] = to_operand<kF16>(ptx::hmul2(ap, d2[i]));
+                const uint32_t ap = kF8 ? ptx::pack_f16x2(sc * __uint_as_float(v[2 * i]), sc * __uint_as_float(v[2 * i + 1]))
+                                        : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+                o[i] = to_operand<kFmt>(ptx::hmul2(ap, d2[i]));
               }
               store8c(obuf, c0 + cc, o);
             }
@@ -813,6 +847,14 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       const float fval = s_f[row] + s_f[kTile + row] + s_f[2 * kTile + row] + s_f[3 * kTile + row] + tw.bout;
       ptx::tmem_wait_ld();
       const float* tr = trigw + (it & 1) * 24;
+      if (kF8) {  // J = (s_J / 64) x the accumulator of FP8 W_1q^T and the x64 operand
+        const float js = tw.fp8_scale[2 * L - 2] * (1.f / kGradScale8);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          jv[m][0] = __float_as_uint(js * __uint_as_float(jv[m][0]));
+          jv[m][1] = __float_as_uint(js * __uint_as_float(jv[m][1]));
+        }
+      }
       float dqm[3];
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
@@ -880,14 +922,19 @@ EncodeTiledFn get_encode() {
   return fn;
 }
 
-int encode_2d(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows, bool f16) {
+// Row-major operand image, 128-byte swizzled boxes of one 128-byte row width
+// (64 16-bit or 128 FP8 elements) by box_rows rows.
+int encode_2d(CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows, int fmt) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return 1;
+  const int eb = fmt == 2 ? 1 : 2;
   cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t gstride[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)cols * eb};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / eb), (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+  const CUtensorMapDataType dt = fmt == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                 : (fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  CUresult r = enc(m, dt, 2,
                    const_cast<void*>(ptr), gdim, gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : 2;
@@ -921,33 +968,72 @@ size_t tc_image_elems(int H, int L, int d_q) {
   return (size_t)2 * (L - 1) * H * H + (size_t)tc_nj(d_q) * H;
 }
 
-void tc_build_image(const float* W, int H, int L, int d_q, int d_in, bool f16, uint16_t* out) {
+uint8_t to_e4m3(float x) { return (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3); }
+
+float max_abs(const float* x, size_t n, size_t stride) {
+  float m = 0.f;
+  for (size_t i = 0; i < n; ++i) m = fmaxf(m, fabsf(x[i * stride]));
+  return m;
+}
+
+void tc_build_image(const float* W, int H, int L, int d_q, int d_in, int fmt, void* out_v, float* scales) {
+  const bool f8 = fmt == 2;
+  uint16_t* out = static_cast<uint16_t*>(out_v);
+  uint8_t* out8 = static_cast<uint8_t*>(out_v);
   size_t off = (size_t)H * d_in + H;
   for (int m = 0; m < L - 1; ++m) {
     const float* Wl = W + off;
-    uint16_t* fwd = out + (size_t)m * H * H;
-    uint16_t* rev = out + (size_t)(L - 1 + m) * H * H;
+    const size_t f0 = (size_t)m * H * H, r0 = (size_t)(L - 1 + m) * H * H;
+    // FP8: W_l = s W8 with s = max |W_l| / 448; the reverse operand W_l^T / 2
+    // uses the same bytes transposed with scale s / 2
+    float sc = 1.f;
+    if (f8) {
+      const float mx = max_abs(Wl, (size_t)H * H, 1);
+      sc = mx > 0.f ? mx / 448.f : 1.f;
+      scales[m] = sc;
+      scales[L - 1 + m] = 0.5f * sc;
+    }
     for (int o = 0; o < H; ++o)
       for (int i = 0; i < H; ++i) {
-        fwd[(size_t)o * H + i] = to_bits(Wl[(size_t)o * H + i], f16);
-        rev[(size_t)i * H + o] = to_bits(0.5f * Wl[(size_t)o * H + i], f16);
+        const float v = Wl[(size_t)o * H + i];
+        if (f8) {
+          const uint8_t b = to_e4m3(v / sc);
+          out8[f0 + (size_t)o * H + i] = b;
+          out8[r0 + (size_t)i * H + o] = b;
+        } else {
+          out[f0 + (size_t)o * H + i] = to_bits(v, fmt == 1);
+          out[r0 + (size_t)i * H + o] = to_bits(0.5f * v, fmt == 1);
+        }
       }
     off += (size_t)H * H + H;
   }
-  uint16_t* J = out + (size_t)2 * (L - 1) * H * H;
+  const size_t j0 = (size_t)2 * (L - 1) * H * H;
   const int nj = tc_nj(d_q);
+  float js = 1.f;
+  if (f8) {
+    float mx = 0.f;
+    for (int d = 0; d < d_q; ++d) mx = fmaxf(mx, max_abs(W + 3 + d, (size_t)H, (size_t)d_in));
+    js = mx > 0.f ? mx / 448.f : 1.f;
+    scales[2 * (L - 1)] = js;
+  }
   for (int d = 0; d < nj; ++d)
-    for (int c = 0; c < H; ++c) J[(size_t)d * H + c] = to_bits(d < d_q ? W[(size_t)c * d_in + 3 + d] : 0.f, f16);
+    for (int c = 0; c < H; ++c) {
+      const float v = d < d_q ? W[(size_t)c * d_in + 3 + d] : 0.f;
+      if (f8) out8[j0 + (size_t)d * H + c] = to_e4m3(v / js);
+      else out[j0 + (size_t)d * H + c] = to_bits(v, fmt == 1);
+    }
 }
 
-int tc_encode_maps(const uint16_t* image, int H, int L, int d_q, bool f16, TcWeights& tw) {
-  // boxes: one CTA's share of a chain (kRowsCta weight rows, nj / 2 Jacobian rows) x 64 columns
-  int rc = encode_2d(&tw.map_w, image, 2 * (L - 1) * H, H, kRowsCta, f16);
+int tc_encode_maps(const void* image, int H, int L, int d_q, int fmt, TcWeights& tw) {
+  // boxes: one CTA's share of a chain (kRowsCta weight rows, nj / 2 Jacobian rows) x 128 bytes
+  int rc = encode_2d(&tw.map_w, image, 2 * (L - 1) * H, H, kRowsCta, fmt);
   if (rc) return rc;
-  return encode_2d(&tw.map_j, image + (size_t)2 * (L - 1) * H * H, tc_nj(d_q), H, tc_nj(d_q) / 2, f16);
+  const size_t eb = fmt == 2 ? 1 : 2;
+  return encode_2d(&tw.map_j, static_cast<const uint8_t*>(image) + (size_t)2 * (L - 1) * H * H * eb, tc_nj(d_q), H,
+                   tc_nj(d_q) / 2, fmt);
 }
 
-template <bool kF16>
+template <int kFmt>
 cudaError_t launch_tc_t(const WorkDesc& w, const TcWeights& tw, int num_sms, cudaStream_t s) {
   // clusters of 2 CTAs (one per SM); as many as can be resident at once, each
   // looping over pair tiles
@@ -968,10 +1054,10 @@ cudaError_t launch_tc_t(const WorkDesc& w, const TcWeights& tw, int num_sms, cud
   cfg.numAttrs = 1;
   int mc = cached ? max_clusters[dev] : 0;
   if (mc <= 0) {
-    cudaError_t e = cudaFuncSetAttribute(tc_fused_kernel<kF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(tc_fused_kernel<kFmt>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     cfg.gridDim = dim3(2);
-    e = cudaOccupancyMaxActiveClusters(&mc, (void*)tc_fused_kernel<kF16>, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&mc, (void*)tc_fused_kernel<kFmt>, &cfg);
     if (e != cudaSuccess) return e;
     if (mc <= 0) return cudaErrorLaunchOutOfResources;
     if (cached) max_clusters[dev] = mc;
@@ -980,11 +1066,12 @@ cudaError_t launch_tc_t(const WorkDesc& w, const TcWeights& tw, int num_sms, cud
   const int npt = (w.n_tiles + 1) / 2;
   if (npt <= 0) return cudaSuccess;
   cfg.gridDim = dim3(2 * (npt < mc ? npt : mc));
-  return cudaLaunchKernelEx(&cfg, tc_fused_kernel<kF16>, w, tw.map_w, tw.map_j, tw);
+  return cudaLaunchKernelEx(&cfg, tc_fused_kernel<kFmt>, w, tw.map_w, tw.map_j, tw);
 }
 
 cudaError_t launch_tc(const WorkDesc& w, const TcWeights& tw, int num_sms, cudaStream_t s) {
-  return tw.f16 ? launch_tc_t<true>(w, tw, num_sms, s) : launch_tc_t<false>(w, tw, num_sms, s);
+  if (tw.fmt == 2) return launch_tc_t<2>(w, tw, num_sms, s);
+  return tw.fmt == 1 ? launch_tc_t<1>(w, tw, num_sms, s) : launch_tc_t<0>(w, tw, num_sms, s);
 }
 
 }  // namespace gcdf

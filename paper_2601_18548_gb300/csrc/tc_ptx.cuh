@@ -130,6 +130,15 @@ __device__ __forceinline__ void mma_pair(uint32_t d_tmem, uint64_t a_desc, uint6
       ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// The same with FP8 (E4M3) operands on both sides: K = 32 per instruction,
+// the same shared-memory descriptors (128-byte K-major rows).
+__device__ __forceinline__ void mma_pair_f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // Arrive once on the barrier at offset `bar` in both CTAs of the pair when every
 // tcgen05 operation issued so far by this thread completes.
 __device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
@@ -247,6 +256,15 @@ __device__ __forceinline__ uint32_t htanh2(uint32_t a) {
 }
 // FP16 pair -> BF16 pair (through FP32; exact widening, one rounding)
 __device__ __forceinline__ uint32_t f16x2_to_bf16x2(uint32_t v) { return pack_bf16x2(f16lo(v), f16hi(v)); }
+// Four FP16 values (two f16x2 words, low halves first) -> four E4M3 bytes in
+// the same order, rounded to nearest even and saturated to +-448.
+__device__ __forceinline__ uint32_t e4m3x4(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("{\n .reg .b16 lo, hi;\n cvt.rn.satfinite.e4m3x2.f16x2 lo, %1;\n cvt.rn.satfinite.e4m3x2.f16x2 hi, %2;\n"
+      " mov.b32 %0, {lo, hi};\n}\n"
+      : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
 
 }  // namespace ptx
 }  // namespace gcdf

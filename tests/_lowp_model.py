@@ -104,3 +104,71 @@ def lowp_eval(n_dof, H, L, weights, q_rows, p_rows, shift_rows=None, fmt="bf16")
     dq[:, :2] = denc[:, :2]
     dq[:, 2:] = np.cos(ang) * denc[:, 2::2] - np.sin(ang) * denc[:, 3::2]
     return f, dq
+
+
+def round_e4m3(x):
+    """Round to FP8 E4M3 (3 mantissa bits, normals from 2^-6 with spacing
+    2^(e-3), subnormal spacing 2^-9), nearest even, saturated to +-448."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    _, e = np.frexp(a)                       # a = m 2^e, m in [0.5, 1)
+    sp = np.where(a >= 2.0 ** -6, np.ldexp(1.0, e - 4), 2.0 ** -9)
+    r = np.minimum(np.round(a / sp) * sp, 448.0)
+    return np.where(np.isnan(x), x, np.sign(x) * r)
+
+
+def _fp8_weight(W):
+    """Per-layer scale s = max |W| / 448 (FP32) and the dequantised E4M3 weights."""
+    W32 = np.asarray(W, dtype=np.float32)
+    s = np.float32(np.max(np.abs(W32))) / np.float32(448.0)
+    return round_e4m3((W32 / s).astype(np.float64)) * np.float64(s)
+
+
+def lowp_eval_fp8(n_dof, H, L, weights, q_rows, p_rows):
+    """As lowp_eval for FP8 E4M3 operands: weights with one scale per layer
+    (the reverse operand W^T / 2 uses the same bytes with half the scale),
+    activations rounded FP16 -> E4M3, reverse operands 64 g rounded FP16 ->
+    E4M3 (64 = the kernel's gradient-operand factor), W_1q with its own scale;
+    epilogue arithmetic in FP16 as for the 16-bit formats."""
+    lay = _layers(n_dof, H, L, weights)
+    q = np.asarray(q_rows, dtype=np.float64)
+    p = np.asarray(p_rows, dtype=np.float64)
+    ang = q[:, 2:]
+    enc = np.empty((q.shape[0], 2 * ang.shape[1]))
+    enc[:, 0::2] = np.sin(ang)
+    enc[:, 1::2] = np.cos(ang)
+    W1, b1 = lay[0]
+    A = np.concatenate([q[:, :2], enc], 1) @ W1[:, 3:].T + b1
+    w1h = round_f16(0.5 * W1[:, 0:3])
+    p16 = round_f16(p)
+    u1 = round_f16(0.5 * A)
+    for d in range(3):
+        u1 = round_f16(w1h[None, :, d] * p16[:, d:d + 1] + u1)
+    h1, s2_1 = _silu_f16(u1)
+    h = round_e4m3(h1)
+    stash, Wq = {}, {}
+    for l in range(1, L):
+        Wq[l] = _fp8_weight(lay[l][0])
+    for l in range(1, L - 1):
+        zp = round_f16(h @ Wq[l].T)
+        u = round_f16(zp * 0.5 + round_f16(0.5 * lay[l][1]))
+        hl, stash[l] = _silu_f16(u)
+        h = round_e4m3(hl)
+    zp = round_f16(h @ Wq[L - 1].T)
+    u = round_f16(zp * 0.5 + round_f16(0.5 * lay[L - 1][1]))
+    hL, s2L = _silu_f16(u)
+    wo, bo = lay[L]
+    f = hL @ wo[0] + bo[0]
+    g = round_e4m3(round_f16(round_f16(32.0 * wo[0])[None, :] * s2L)) / 64.0
+    for l in range(L - 1, 0, -1):
+        acc64 = round_f16(64.0 * (g @ (0.5 * Wq[l])))
+        d2 = stash[l - 1] if l - 1 >= 1 else s2_1
+        g = round_e4m3(round_f16(acc64 * d2)) / 64.0
+    W1q = np.asarray(W1[:, 3:], dtype=np.float32)
+    sj = np.float32(np.max(np.abs(W1q))) / np.float32(448.0)
+    W1q_q = round_e4m3((W1q / sj).astype(np.float64)) * np.float64(sj)
+    denc = g @ W1q_q
+    dq = np.empty((q.shape[0], n_dof))
+    dq[:, :2] = denc[:, :2]
+    dq[:, 2:] = np.cos(ang) * denc[:, 2::2] - np.sin(ang) * denc[:, 3::2]
+    return f, dq
