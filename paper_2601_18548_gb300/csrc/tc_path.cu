@@ -783,9 +783,15 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               uint32_t o[8];
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                const uint32_t ap = kF8 ? ptx::pack_f16x2(sc * __uint_as_float(v[2 * i]), sc * __uint_as_float(v[2 * i + 1]))
-                                        : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-                o[i] = to_operand<kFmt>(ptx::hmul2(ap, d2[i]));
+                if constexpr (kFmt == 0) {
+                  // BF16: the product in FP32, one rounding to BF16 (one pack instead of two)
+                  o[i] = ptx::pack_bf16x2(__uint_as_float(v[2 * i]) * ptx::f16lo(d2[i]),
+                                          __uint_as_float(v[2 * i + 1]) * ptx::f16hi(d2[i]));
+                } else {
+                  const uint32_t ap = kF8 ? ptx::pack_f16x2(sc * __uint_as_float(v[2 * i]), sc * __uint_as_float(v[2 * i + 1]))
+                                          : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+                  o[i] = to_operand<kFmt>(ptx::hmul2(ap, d2[i]));
+                }
               }
               store8c(obuf, c0 + cc, o);
             }

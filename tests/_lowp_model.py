@@ -9,7 +9,8 @@ tcgen05 kernel does:
     the first layer u_1 = A_i / 2 + (W_1p / 2) p (the point and the halved
     weights in FP16, one fused multiply-add per coordinate), u = z / 2,
     t = tanh(u), s = u + u t, 2 s' = s (1 - t) + (1 + t), g_L = (w_o / 2) 2 s',
-    and the reverse product acc * 2 s';
+    and, for FP16 operands, the reverse product acc * 2 s' (BF16 operands form
+    it in FP32 from the FP32 accumulator and round once, to BF16);
   * the stash 2 s'(z_2..z_{L-1}) (FP16);
   * the per-waypoint term A_i, the output sum f = w_o . s(z_L) + b_o and every
     matrix accumulation at high precision.
@@ -96,9 +97,9 @@ def lowp_eval(n_dof, H, L, weights, q_rows, p_rows, shift_rows=None, fmt="bf16")
     f = hL @ wo[0] + bo[0]
     g = R(round_f16(round_f16(0.5 * wo[0])[None, :] * s2L))
     for l in range(L - 1, 0, -1):  # reverse through W_{l+1} (0-based l)
-        acc = round_f16(g @ R(0.5 * lay[l][0]))
+        acc = g @ R(0.5 * lay[l][0])
         d2 = stash[l - 1] if l - 1 >= 1 else s2_1
-        g = R(round_f16(acc * d2))
+        g = R(acc * d2) if fmt == "bf16" else R(round_f16(round_f16(acc) * d2))
     denc = g @ R(W1[:, 3:])
     dq = np.empty((q.shape[0], n_dof))
     dq[:, :2] = denc[:, :2]
