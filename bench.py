@@ -492,6 +492,11 @@ def run_serve(args):
                              h_rng=(32, 256), m_rng=(1000, 65536))
     overload = _run_server(g, nets["bf16"], params, reqs_b, budget, 64, 64)
     overload["offered"] = len(reqs_b)
+    # the same offered load with the partitions of Sec. IV-A: every waypoint
+    # only considers the points within 1.5 m (planar) of its reference base
+    params_p = g.PlanParams(iterations=50, partition_radius=1.5)
+    overload_p = _run_server(g, nets["bf16"], params_p, reqs_b, budget, 64, 64)
+    overload_p["offered"] = len(reqs_b)
     line = {
         "metric": "served plan p50/p99 latency and throughput", "unit": "s / requests per s",
         "n_gpus": 1, "data": "synthetic",
@@ -510,6 +515,7 @@ def run_serve(args):
         "C_per_request_bf16": bf16_seq_c,
         "C_per_request_fp32": fp32_seq_c,
         "B_served_bf16_overload": overload,
+        "B_served_bf16_overload_partition_1.5m": overload_p,
     }
     print(json.dumps(line))
     return 0

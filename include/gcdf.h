@@ -313,8 +313,8 @@ GCDF_API int gcdf_fit_vjp(const gcdf_fit_desc *desc, const float *weights, const
  *   trial = q - s; accepted when it lowers J (lambda /= 2, floor lambda_min),
  *   otherwise rejected (lambda *= 4, cap lambda_max).
  * Each step costs one HINGE collision-cost evaluation of every waypoint over
- * all points of its problem; the first evaluation is the initial guess (the
- * straight line from q_start to q_goal).  J and every step are computed in
+ * all points of its problem (or its partition, see partition_radius); the first
+ * evaluation is the initial guess (the straight line from q_start to q_goal).  J and every step are computed in
  * FP64; the field is queried at the FP32 rounding of the trial.
  * ------------------------------------------------------------------------- */
 
@@ -326,6 +326,9 @@ typedef struct gcdf_plan_params {
   float delta;           /* safety margin of Eq. (11) */
   float lambda0, lambda_min, lambda_max;  /* damping: start, floor, cap (>= 0) */
   int iterations;        /* Levenberg-Marquardt steps (>= 0); iterations + 1 evaluations */
+  float partition_radius; /* > 0: waypoint i only considers the points within this planar range of
+                             its reference base position, the (x, y) of the initial guess (the
+                             partitions of Sec. IV-A, as gcdf_partition_*); 0: every point */
 } gcdf_plan_params;
 
 typedef struct gcdf_plan_problem {
@@ -347,9 +350,10 @@ typedef struct gcdf_plan_problem {
  *             iterate after each evaluation
  *   accepted_out (n_problems, iterations + 1) DEVICE out or NULL: 1 where the
  *             evaluation's trial was accepted (always 1 for the first)
- * Asynchronous on `stream`.  The problems' point arrays are copied into one
- * temporary array first; the total pair count sum_r N_r M_r must stay below
- * 2^31.  Errors: EINVAL (NULL or misaligned pointer, N < 2, bad parameter),
+ * Asynchronous on `stream`, except that with partition_radius > 0 the list
+ * length is read back once per 2^31-pair chunk.  The problems' point arrays are
+ * copied into one temporary array first; batches above 2^31 pairs are split
+ * into chunks.  Errors: EINVAL (NULL or misaligned pointer, N < 2, bad parameter),
  * ENOMEM, ECUDA.
  */
 GCDF_API int gcdf_plan_solve(gcdf_net *net, const gcdf_plan_problem *problems, int n_problems,

@@ -23,6 +23,9 @@ the waypoints,
 
     (A_d + lambda diag(A_d)) s_d = g_d   for every DOF d,   Q_trial = Q - s,
 
+(with a partition radius R > 0 waypoint i only considers the points within
+planar range R of its reference base, the (x, y) of the initial guess),
+
 solved by a tridiagonal Cholesky factorisation in FP64.  A trial that lowers
 J is accepted and lambda is halved (floor lambda_min); otherwise lambda is
 multiplied by 4 (cap lambda_max).  A fixed number of steps, each one
@@ -40,6 +43,7 @@ import dataclasses
 import numpy as np
 
 from . import reduce as red
+from . import sparse
 
 
 @dataclasses.dataclass
@@ -54,6 +58,7 @@ class Params:
     lam_min: float = 1e-6
     lam_max: float = 1e8
     iters: int = 50
+    partition_radius: float = 0.0   # > 0: per-waypoint point lists (Sec. IV-A partitions)
 
 
 def smooth_weights(n_dof, prm: Params) -> np.ndarray:
@@ -136,10 +141,11 @@ def straight_line(q_start, q_goal, N):
 class Field:
     """The collision term through the FP64 MLP oracle (Eq. 11 rows, HINGE)."""
 
-    def __init__(self, n_dof, hidden, n_layers, weights, points):
+    def __init__(self, n_dof, hidden, n_layers, weights, points, offsets=None, idx=None):
         self.shape = (n_dof, hidden, n_layers)
         self.weights = np.asarray(weights)
         self.points = np.asarray(points, dtype=np.float64).reshape(-1, 3)
+        self.offsets, self.idx = offsets, idx
 
     def hinge(self, Q, delta):
         n_dof, H, L = self.shape
@@ -147,7 +153,8 @@ class Field:
         if self.points.shape[0] == 0:
             return np.zeros(N), np.zeros((N, n_dof))
         q32 = np.asarray(Q, dtype=np.float32).astype(np.float64)
-        c, g, _ = red.collision_cost(n_dof, H, L, self.weights, q32, self.points, red.HINGE, delta)
+        c, g, _ = red.collision_cost(n_dof, H, L, self.weights, q32, self.points, red.HINGE, delta,
+                                     self.offsets, self.idx)
         return c, g
 
 
@@ -165,6 +172,11 @@ def plan(q_start, q_goal, N, field: Field, prm: Params, q_init=None):
     Q = straight_line(q_start, q_goal, N) if q_init is None else np.array(q_init, dtype=np.float64)
     Q[0] = np.asarray(q_start, np.float64)
     n = Q.shape[1]
+    if prm.partition_radius > 0:
+        # lists around the reference bases: the (x, y) of the initial guess as the
+        # field sees it (FP32)
+        off, idx = sparse.partition(Q.astype(np.float32)[:, :2], field.points, prm.partition_radius)
+        field = Field(*field.shape, field.weights, field.points, off, idx)
     diag, off = smooth_hessian_tridiag(N, n, prm)
     J, G = total_cost_grad(Q, q_goal, field, prm)
     lam = prm.lam0

@@ -220,14 +220,16 @@ class PlanParams:
     """gcdf_plan_params: cost weights, margin, damping and step count."""
 
     def __init__(self, dt=0.1, w_trans=1.0, w_rot=0.5, w_goal=100.0, mu=1.0, delta=0.05,
-                 lambda0=1.0, lambda_min=1e-6, lambda_max=1e8, iterations=50):
+                 lambda0=1.0, lambda_min=1e-6, lambda_max=1e8, iterations=50, partition_radius=0.0):
         self.dt, self.w_trans, self.w_rot, self.w_goal = dt, w_trans, w_rot, w_goal
         self.mu, self.delta, self.iterations = mu, delta, iterations
         self.lambda0, self.lambda_min, self.lambda_max = lambda0, lambda_min, lambda_max
+        self.partition_radius = partition_radius
 
     def c(self):
         return _lib.PlanParams(self.dt, self.w_trans, self.w_rot, self.w_goal, self.mu, self.delta,
-                               self.lambda0, self.lambda_min, self.lambda_max, int(self.iterations))
+                               self.lambda0, self.lambda_min, self.lambda_max, int(self.iterations),
+                               float(self.partition_radius))
 
 
 def plan_solve(net: Net, problems, params: PlanParams, history: bool = True, stream=None):

@@ -32,7 +32,8 @@ class FitDesc(ctypes.Structure):
 
 class PlanParams(ctypes.Structure):
     _fields_ = [("dt", _f), ("w_trans", _f), ("w_rot", _f), ("w_goal", _f), ("mu", _f), ("delta", _f),
-                ("lambda0", _f), ("lambda_min", _f), ("lambda_max", _f), ("iterations", _i)]
+                ("lambda0", _f), ("lambda_min", _f), ("lambda_max", _f), ("iterations", _i),
+                ("partition_radius", _f)]
 
 
 class PlanProblem(ctypes.Structure):

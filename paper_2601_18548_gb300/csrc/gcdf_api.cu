@@ -310,9 +310,10 @@ size_t net_step_bytes_per_row(const gcdf_net* net, int M) {
 }
 
 // Collision cost over range lists: waypoint i uses points point_base[i] ..
-// point_base[i] + (offsets[i+1] - offsets[i]) - 1 of p (no index array).
+// point_base[i] + (offsets[i+1] - offsets[i]) - 1 of p (no index array), or,
+// with idx, the CSR lists offsets / idx.
 int collision_ranges(gcdf_net* net, const float* q, int N, const float* p, int M, const int* offsets,
-                     const int* point_base, int n_pairs, int reduction, float param, float* cost,
+                     const int* point_base, const int* idx, int n_pairs, int reduction, float param, float* cost,
                      float* grad, cudaStream_t s) {
   if (N == 0) return GCDF_OK;
   WorkDesc w;
@@ -320,7 +321,8 @@ int collision_ranges(gcdf_net* net, const float* q, int N, const float* p, int M
   w.q = q;
   w.p = p;
   w.offsets = offsets;
-  w.point_base = point_base;
+  w.idx = idx;
+  w.point_base = idx ? nullptr : point_base;
   w.N = N;
   w.M = M;
   w.n_pairs = n_pairs;

@@ -26,8 +26,12 @@ void clear_error();
 int net_n_dof(const gcdf_net* net);
 int net_device(const gcdf_net* net);
 int collision_ranges(gcdf_net* net, const float* q, int N, const float* p, int M, const int* offsets,
-                     const int* point_base, int n_pairs, int reduction, float param, float* cost,
+                     const int* point_base, const int* idx, int n_pairs, int reduction, float param, float* cost,
                      float* grad, cudaStream_t s);
+cudaError_t launch_partition_offsets(const float* base, int bstride, int rows, const float* p, const int* pbegin,
+                                     const int* plen, float radius, int* counts, int* offsets, cudaStream_t s);
+cudaError_t launch_partition_indices(const float* base, int bstride, int rows, const float* p, const int* pbegin,
+                                     const int* plen, float radius, const int* offsets, int* idx, cudaStream_t s);
 
 namespace {
 
@@ -273,7 +277,7 @@ int check_plan_params(const gcdf_plan_params* p) {
   if (!p) return set_error(GCDF_EINVAL, "params is NULL");
   if (!(p->dt > 0.f) || !(p->w_trans > 0.f) || !(p->w_rot > 0.f) || !(p->w_goal >= 0.f) || !(p->mu >= 0.f) ||
       !(p->delta == p->delta) || !(p->lambda0 >= 0.f) || !(p->lambda_min >= 0.f) ||
-      !(p->lambda_max >= p->lambda_min) || p->iterations < 0)
+      !(p->lambda_max >= p->lambda_min) || p->iterations < 0 || !(p->partition_radius >= 0.f))
     return set_error(GCDF_EINVAL, "bad planner parameters");
   return GCDF_OK;
 }
@@ -291,10 +295,31 @@ PlanConsts plan_consts(const gcdf_plan_params* p) {
   return c;
 }
 
+int plan_partition(const float* base, int bstride, int rows, const float* points, const int* pbegin,
+                   const int* plen, float radius, int* offsets, int** idx, long long* n_pairs, cudaStream_t s) {
+  cudaError_t e;
+  int* counts = nullptr;
+  if ((e = cudaMallocAsync((void**)&counts, (size_t)(rows > 0 ? rows : 1) * sizeof(int), s)))
+    return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  e = launch_partition_offsets(base, bstride, rows, points, pbegin, plen, radius, counts, offsets, s);
+  cudaFreeAsync(counts, s);
+  if (e != cudaSuccess) return set_error(GCDF_ECUDA, "partition launch: %s", cudaGetErrorString(e));
+  int total = 0;
+  if ((e = cudaMemcpyAsync(&total, offsets + rows, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return set_error(GCDF_ECUDA, "partition read-back: %s", cudaGetErrorString(e));
+  if ((e = cudaMallocAsync((void**)idx, (size_t)(total > 0 ? total : 1) * sizeof(int), s)))
+    return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  if ((e = launch_partition_indices(base, bstride, rows, points, pbegin, plen, radius, offsets, *idx, s)))
+    return set_error(GCDF_ECUDA, "partition launch: %s", cudaGetErrorString(e));
+  *n_pairs = total;
+  return GCDF_OK;
+}
+
 int plan_step(gcdf_net* net, const PlanStep& ps, const PlanArrays& a, const PlanConsts& c, float delta,
               cudaStream_t s) {
-  int rc = collision_ranges(net, a.Qf, ps.n_rows, ps.points, ps.n_points, ps.offsets, ps.point_base, ps.n_pairs,
-                            GCDF_RED_HINGE, delta, const_cast<float*>(a.ccost), const_cast<float*>(a.cgrad), s);
+  int rc = collision_ranges(net, a.Qf, ps.n_rows, ps.points, ps.n_points, ps.offsets, ps.point_base, ps.idx,
+                            ps.n_pairs, GCDF_RED_HINGE, delta, const_cast<float*>(a.ccost), const_cast<float*>(a.cgrad), s);
   if (rc) return rc;
   cudaError_t e = launch_plan_update(ps.trajs, ps.n_traj, a, c, s);
   if (e != cudaSuccess) return set_error(GCDF_ECUDA, "plan update launch: %s", cudaGetErrorString(e));
@@ -415,7 +440,27 @@ int solve_chunk(gcdf_net* net, const gcdf_plan_problem* problems, int n_problems
   ps.n_points = (int)pts;
   ps.offsets = offsets;
   ps.point_base = pbase;
+  ps.idx = nullptr;
   ps.n_pairs = (int)pairs;
+  int* part_idx = nullptr;
+  if (params->partition_radius > 0.f) {
+    // lists around the reference bases: the (x, y) of the initial guess, which
+    // the init kernel has just written (FP32) to the step rows
+    std::vector<int> h_len((size_t)rows);
+    for (long long i = 0; i < rows; ++i) h_len[i] = h_off[i + 1] - h_off[i];
+    int *plen = nullptr, *poff = nullptr;
+    if ((e = sc.get(&plen, (size_t)rows)) || (e = sc.get(&poff, (size_t)rows + 1)))
+      return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+    if ((e = cudaMemcpyAsync(plen, h_len.data(), h_len.size() * sizeof(int), cudaMemcpyHostToDevice, s)))
+      return set_error(GCDF_ECUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e));
+    long long np = 0;
+    if ((rc = plan_partition(Qs, n, (int)rows, P, pbase, plen, params->partition_radius, poff, &part_idx, &np, s)))
+      return rc;
+    sc.ptrs.push_back(part_idx);
+    ps.offsets = poff;
+    ps.idx = part_idx;
+    ps.n_pairs = (int)np;
+  }
   for (int k = 0; k <= params->iterations; ++k) {
     if ((rc = plan_step(net, ps, a, c, params->delta, s))) return rc;
   }

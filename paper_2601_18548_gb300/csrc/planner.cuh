@@ -58,6 +58,7 @@ struct PlanStep {
   int n_points;
   const int* offsets;     // (n_rows + 1) pair offsets of the rows' point ranges
   const int* point_base;  // (n_rows) first point of each row's range
+  const int* idx;         // partition lists (CSR with offsets) or nullptr: the ranges above
   int n_pairs;
 };
 
@@ -72,6 +73,11 @@ cudaError_t launch_plan_output(const PlanTraj* trajs, int n_traj, int n, float* 
 size_t plan_state_bytes(int N, int n);
 int check_plan_params(const gcdf_plan_params* p);
 PlanConsts plan_consts(const gcdf_plan_params* p);
+// Partition lists of the step's rows around their reference bases (row i at
+// base + i * bstride), each over its own point range; fills ps.offsets-like
+// arrays: offsets (n_rows + 1) on the device, returns the list length.
+int plan_partition(const float* base, int bstride, int rows, const float* points, const int* pbegin,
+                   const int* plen, float radius, int* offsets, int** idx, long long* n_pairs, cudaStream_t s);
 // One evaluation + update of every trajectory of the step.
 int plan_step(gcdf_net* net, const PlanStep& ps, const PlanArrays& a, const PlanConsts& c, float delta,
               cudaStream_t s);

@@ -55,6 +55,7 @@ struct Req {
   void* dmem = nullptr;
   PlanTraj tr{};      // host image of its table entry (wp0 set per rebuild)
   float* d_pts = nullptr;
+  float* d_ref = nullptr;  // the initial trajectory (FP32): reference bases of the partition
   // result
   std::vector<float> q;
   double merit = 0;
@@ -69,6 +70,8 @@ struct Group {        // admitted requests that share a net
   PlanTraj* trajs = nullptr;
   PlanArrays a{};
   PlanStep ps{};
+  int* part_idx = nullptr;  // partition lists of the step (with partition_radius > 0)
+  int* part_off = nullptr;
 };
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -106,7 +109,7 @@ namespace {
 // state, its rows of the step arrays and the fused pass's per-row temporaries.
 size_t request_bytes(const gcdf_net* net, int N, int M, int n) {
   const size_t state = plan_state_bytes(N, n);
-  const size_t pts = (size_t)M * 12 * 2;             // own copy + step copy
+  const size_t pts = (size_t)M * 12 * 2 + (size_t)N * n * 4;  // own copy + step copy, reference trajectory
   const size_t rows = (size_t)N * (2 * n * 4 + 4 + 8);  // step Qf, cgrad, ccost, offsets, base
   const size_t pass = (size_t)N * net_step_bytes_per_row(net, M);
   return align256(state) + align256(pts) + rows + pass + 3 * 256;
@@ -125,7 +128,7 @@ int fail_server(gcdf_server* s, int code, const char* what, cudaError_t e) {
 int admit(gcdf_server* s, Req* r) {
   const int n = r->n, N = r->N;
   const size_t b_state = align256(plan_state_bytes(N, n));
-  const size_t b_in = align256((size_t)(2 * n) * 4) + align256((size_t)r->M * 12);
+  const size_t b_in = align256((size_t)(2 * n) * 4) + align256((size_t)r->M * 12) + align256((size_t)N * n * 4);
   cudaError_t e = cudaMallocAsync(&r->dmem, b_state + b_in + 256, s->stream);
   if (e != cudaSuccess) return fail_server(s, GCDF_ENOMEM, "cudaMallocAsync", e);
   char* p = (char*)r->dmem;
@@ -148,6 +151,8 @@ int admit(gcdf_server* s, Req* r) {
   t.q_init = nullptr;
   p += align256((size_t)(2 * n) * 4);
   r->d_pts = (float*)p;
+  p += align256((size_t)r->M * 12);
+  r->d_ref = (float*)p;
   if ((e = cudaMemcpyAsync(qsg, r->qs.data(), n * 4, cudaMemcpyHostToDevice, s->stream)) ||
       (e = cudaMemcpyAsync(qsg + n, r->qg.data(), n * 4, cudaMemcpyHostToDevice, s->stream)) ||
       (r->M > 0 && (e = cudaMemcpyAsync(r->d_pts, r->pts.data(), (size_t)r->M * 12, cudaMemcpyHostToDevice,
@@ -159,7 +164,11 @@ int admit(gcdf_server* s, Req* r) {
 
 void free_group(gcdf_server* s, Group& g) {
   if (g.dmem) cudaFreeAsync(g.dmem, s->stream);
+  if (g.part_idx) cudaFreeAsync(g.part_idx, s->stream);
+  if (g.part_off) cudaFreeAsync(g.part_off, s->stream);
   g.dmem = nullptr;
+  g.part_idx = nullptr;
+  g.part_off = nullptr;
 }
 
 // Step arrays of one group: rows of all its trajectories back to back.
@@ -220,7 +229,37 @@ int build_group(gcdf_server* s, Group& g, const gcdf_plan_params& prm) {
   g.ps.n_points = (int)pts;
   g.ps.offsets = off;
   g.ps.point_base = pb;
+  g.ps.idx = nullptr;
   g.ps.n_pairs = (int)pairs;
+  if (prm.partition_radius > 0.f) {
+    // the reference bases of every row (each request's initial trajectory) and
+    // each row's point count, then the lists over the rows' point ranges
+    float* base = nullptr;
+    int* plen = nullptr;
+    if ((e = cudaMallocAsync(&base, (size_t)(rows > 0 ? rows : 1) * n * 4, s->stream)) ||
+        (e = cudaMallocAsync(&plen, (size_t)(rows > 0 ? rows : 1) * 4, s->stream)) ||
+        (e = cudaMallocAsync(&g.part_off, (size_t)(rows + 1) * 4, s->stream)))
+      return fail_server(s, GCDF_ENOMEM, "cudaMallocAsync", e);
+    std::vector<int> h_len;
+    long long r0 = 0;
+    for (Req* r : g.reqs) {
+      if ((e = cudaMemcpyAsync(base + r0 * n, r->d_ref, (size_t)r->N * n * 4, cudaMemcpyDeviceToDevice, s->stream)))
+        return fail_server(s, GCDF_ECUDA, "cudaMemcpyAsync", e);
+      for (int i = 0; i < r->N; ++i) h_len.push_back(r->M);
+      r0 += r->N;
+    }
+    if ((e = cudaMemcpyAsync(plen, h_len.data(), h_len.size() * 4, cudaMemcpyHostToDevice, s->stream)))
+      return fail_server(s, GCDF_ECUDA, "cudaMemcpyAsync", e);
+    long long np = 0;
+    const int rc = plan_partition(base, n, (int)rows, P, pb, plen, prm.partition_radius, g.part_off, &g.part_idx, &np,
+                                  s->stream);
+    cudaFreeAsync(base, s->stream);
+    cudaFreeAsync(plen, s->stream);
+    if (rc) return fail_server(s, rc, "partition", cudaGetLastError());
+    g.ps.offsets = g.part_off;
+    g.ps.idx = g.part_idx;
+    g.ps.n_pairs = (int)np;
+  }
   return GCDF_OK;
 }
 
@@ -269,6 +308,11 @@ void worker_loop(gcdf_server* s) {
         return;
       }
       cudaFreeAsync(d_tr, s->stream);
+      // the initial trajectory, whose (x, y) are the partition's reference bases
+      if ((e = cudaMemcpyAsync(r->d_ref, r->tr.Qf, (size_t)r->N * r->n * 4, cudaMemcpyDeviceToDevice, s->stream))) {
+        fail_server(s, GCDF_ECUDA, "cudaMemcpyAsync", e);
+        return;
+      }
       s->dirty = true;
     }
     // 2. step arrays

@@ -32,13 +32,27 @@ __device__ __forceinline__ bool in_range(const float* __restrict__ p, int j, dou
   return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= r2;
 }
 
-__global__ void partition_count_kernel(const float* __restrict__ base, const float* __restrict__ p, int M,
-                                       double r2, int* __restrict__ counts) {
+// Row i tests points [begin_i, begin_i + len_i) of p (pbegin / plen NULL: all
+// M points) against its base (x, y) at base + i * bstride; listed indices are
+// indices into p.
+struct RowRanges {
+  const float* base;
+  int bstride;
+  const int* pbegin;
+  const int* plen;
+  int M;
+  __device__ int begin(int i) const { return pbegin ? pbegin[i] : 0; }
+  __device__ int len(int i) const { return plen ? plen[i] : M; }
+};
+
+__global__ void partition_count_kernel(RowRanges rr, const float* __restrict__ p, double r2,
+                                       int* __restrict__ counts) {
   __shared__ int red[kPartThreads / 32];
   const int i = blockIdx.x;
-  const double bx = base[2 * i], by = base[2 * i + 1];
+  const double bx = rr.base[(size_t)i * rr.bstride], by = rr.base[(size_t)i * rr.bstride + 1];
+  const int b0 = rr.begin(i), m = rr.len(i);
   int c = 0;
-  for (int j = threadIdx.x; j < M; j += kPartThreads) c += in_range(p, j, bx, by, r2);
+  for (int j = threadIdx.x; j < m; j += kPartThreads) c += in_range(p, b0 + j, bx, by, r2);
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
   __syncthreads();
@@ -76,19 +90,20 @@ __global__ void exclusive_scan_kernel(const int* __restrict__ in, int N, int* __
 // One block per waypoint: tiles of kPartThreads * kPerThread points in order;
 // thread t tests points tile + 8t .. tile + 8t + 7, the block scans the thread
 // counts, so the list keeps increasing point order.
-__global__ void partition_fill_kernel(const float* __restrict__ base, const float* __restrict__ p, int M, double r2,
+__global__ void partition_fill_kernel(RowRanges rr, const float* __restrict__ p, double r2,
                                       const int* __restrict__ offsets, int* __restrict__ idx) {
   __shared__ int wsum[kPartThreads / 32];
   __shared__ int s_total;
   const int i = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const double bx = base[2 * i], by = base[2 * i + 1];
+  const double bx = rr.base[(size_t)i * rr.bstride], by = rr.base[(size_t)i * rr.bstride + 1];
+  const int b0 = rr.begin(i), M = rr.len(i);
   int run = offsets[i];
   for (int tile = 0; tile < M; tile += kPartThreads * kPerThread) {
     const int j0 = tile + t * kPerThread;
     unsigned mask = 0;
 #pragma unroll
     for (int u = 0; u < kPerThread; ++u)
-      if (j0 + u < M && in_range(p, j0 + u, bx, by, r2)) mask |= 1u << u;
+      if (j0 + u < M && in_range(p, b0 + j0 + u, bx, by, r2)) mask |= 1u << u;
     const int c = __popc(mask);
     int x = c;  // inclusive warp scan
     for (int o = 1; o < 32; o <<= 1) {
@@ -109,7 +124,7 @@ __global__ void partition_fill_kernel(const float* __restrict__ base, const floa
     __syncthreads();
     int pos = run + wsum[w] + x - c;
     for (int u = 0; u < kPerThread; ++u)
-      if (mask & (1u << u)) idx[pos++] = j0 + u;
+      if (mask & (1u << u)) idx[pos++] = b0 + j0 + u;
     run += s_total;
     __syncthreads();
   }
@@ -204,6 +219,25 @@ int check_partition(const float* base_xy, int N, const float* p, int M, float ra
 
 }  // namespace
 
+// Partition of `rows` rows with per-row point ranges (planner): counts into
+// `counts` (rows), offsets (rows + 1); then the indices.
+cudaError_t launch_partition_offsets(const float* base, int bstride, int rows, const float* p, const int* pbegin,
+                                     const int* plen, float radius, int* counts, int* offsets, cudaStream_t s) {
+  if (rows == 0) return cudaMemsetAsync(offsets, 0, sizeof(int), s);
+  const double r2 = (double)radius * (double)radius;
+  partition_count_kernel<<<rows, kPartThreads, 0, s>>>(RowRanges{base, bstride, pbegin, plen, 0}, p, r2, counts);
+  exclusive_scan_kernel<<<1, 1024, 0, s>>>(counts, rows, offsets);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_partition_indices(const float* base, int bstride, int rows, const float* p, const int* pbegin,
+                                     const int* plen, float radius, const int* offsets, int* idx, cudaStream_t s) {
+  if (rows == 0) return cudaSuccess;
+  const double r2 = (double)radius * (double)radius;
+  partition_fill_kernel<<<rows, kPartThreads, 0, s>>>(RowRanges{base, bstride, pbegin, plen, 0}, p, r2, offsets, idx);
+  return cudaGetLastError();
+}
+
 // used by gcdf_project (gcdf_api.cu): the in-place projection of a query's output
 cudaError_t launch_project(const float* q, int N, int n, const int* offsets, int M, long long K, const float* f,
                            const float* m_diag, float* g, cudaStream_t s) {
@@ -235,7 +269,8 @@ int gcdf_partition_offsets(const float* base_xy, int n_waypoints, const float* p
     return set_error(e == cudaErrorMemoryAllocation ? GCDF_ENOMEM : GCDF_ECUDA, "cudaMallocAsync: %s",
                      cudaGetErrorString(e));
   const double r2 = (double)radius * (double)radius;
-  partition_count_kernel<<<n_waypoints, kPartThreads, 0, s>>>(base_xy, p, n_points, r2, counts);
+  partition_count_kernel<<<n_waypoints, kPartThreads, 0, s>>>(RowRanges{base_xy, 2, nullptr, nullptr, n_points}, p,
+                                                              r2, counts);
   exclusive_scan_kernel<<<1, 1024, 0, s>>>(counts, n_waypoints, part_offsets);
   e = cudaGetLastError();
   cudaFreeAsync(counts, s);
@@ -252,7 +287,8 @@ int gcdf_partition_indices(const float* base_xy, int n_waypoints, const float* p
   if (!part_idx || !al16(part_idx)) return set_error(GCDF_EINVAL, "part_idx NULL or not 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   const double r2 = (double)radius * (double)radius;
-  partition_fill_kernel<<<n_waypoints, kPartThreads, 0, s>>>(base_xy, p, n_points, r2, part_offsets, part_idx);
+  partition_fill_kernel<<<n_waypoints, kPartThreads, 0, s>>>(RowRanges{base_xy, 2, nullptr, nullptr, n_points}, p,
+                                                             r2, part_offsets, part_idx);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(GCDF_ECUDA, "partition launch: %s", cudaGetErrorString(e));
   clear_error();

@@ -16,11 +16,12 @@ pytestmark = pytest.mark.gpu
 
 def _params(g, iters, **kw):
     base = dict(dt=0.1, w_trans=1.0, w_rot=0.5, w_goal=100.0, mu=1.0, delta=0.05,
-                lambda0=1.0, lambda_min=1e-6, lambda_max=1e8, iterations=iters)
+                lambda0=1.0, lambda_min=1e-6, lambda_max=1e8, iterations=iters, partition_radius=0.0)
     base.update(kw)
     return g.PlanParams(**base), pl.Params(lam0=base["lambda0"], lam_min=base["lambda_min"],
                                            lam_max=base["lambda_max"], iters=iters,
-                                           **{k: base[k] for k in ("dt", "w_trans", "w_rot", "w_goal", "mu", "delta")})
+                                           **{k: base[k] for k in ("dt", "w_trans", "w_rot", "w_goal", "mu", "delta",
+                                                                   "partition_radius")})
 
 
 def _scene_problem(seed, N, M, n_dof=9):
@@ -33,14 +34,16 @@ def _dev_problem(torch, qs, qg, pts, N):
             "points": to_dev(torch, pts.reshape(-1, 3))}
 
 
-def test_plan_matches_oracle_step_by_step_fp32():
+@pytest.mark.parametrize("radius", [0.0, 2.0])
+def test_plan_matches_oracle_step_by_step_fp32(radius):
     """FP32 field: the merit after every evaluation and every accept/reject
-    decision follow the FP64 oracle (up to the first near-tie, if any)."""
+    decision follow the FP64 oracle (up to the first near-tie, if any), with
+    every point or with the partition lists of radius 2 m."""
     torch = need_gpu()
     g = lib()
     shape, w = small_net(9)
     net = g.create_net(9, shape.hidden, shape.n_layers, w, "fp32")
-    gp, op = _params(g, 8, mu=0.5)
+    gp, op = _params(g, 8, mu=0.5, partition_radius=radius)
     probs = [_scene_problem(3, 12, 96), _scene_problem(5, 9, 64)]
     q, merit, acc = g.plan_solve(net, [_dev_problem(torch, *p) for p in probs], gp)
     q, merit, acc = q.cpu().numpy(), merit.cpu().numpy(), acc.cpu().numpy()
@@ -141,17 +144,19 @@ def _wait(srv, tickets, timeout=120.0):
     return out
 
 
-def test_server_results_equal_solving_alone_in_a_mix():
+@pytest.mark.parametrize("radius", [0.0, 2.5])
+def test_server_results_equal_solving_alone_in_a_mix(radius):
     """Requests of uneven size and two robots (9 and 10 DOF) submitted while
     others run: each result is bit-identical to gcdf_plan_solve of that
-    request alone (continuous batching does not change any result)."""
+    request alone (continuous batching does not change any result), with and
+    without partition lists."""
     torch = need_gpu()
     g = lib()
     nets = {}
     for n in (9, 10):
         shape, w = small_net(n)
         nets[n] = g.create_net(n, shape.hidden, shape.n_layers, w, "bf16")
-    gp, _ = _params(g, 10)
+    gp, _ = _params(g, 10, partition_radius=radius)
     reqs = [(9, _scene_problem(20, 32, 900)), (10, _scene_problem(21, 48, 400, n_dof=10)),
             (9, _scene_problem(22, 17, 1500)), (10, _scene_problem(23, 64, 256, n_dof=10)),
             (9, _scene_problem(24, 40, 3000))]

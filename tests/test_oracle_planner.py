@@ -152,3 +152,15 @@ def test_plan_at_rest_stays_at_rest():
     Q, hist = pl.plan(q, q, 9, field, pl.Params(iters=3))
     assert np.array_equal(Q, np.tile(q.astype(np.float64), (9, 1)))
     assert hist["merit"][-1] == 0.0
+
+
+def test_partition_with_an_unbounded_radius_changes_nothing_and_keeps_the_merit_monotone():
+    n = 9
+    shape, w = small_net(n)
+    wl = synth.box_scene(n_waypoints=10, n_points=80)
+    field = pl.Field(n, shape.hidden, shape.n_layers, w, wl.p)
+    Q0, h0 = pl.plan(wl.q[0], wl.q[-1], 10, field, pl.Params(iters=5, mu=0.5))
+    Q1, h1 = pl.plan(wl.q[0], wl.q[-1], 10, field, pl.Params(iters=5, mu=0.5, partition_radius=1e9))
+    assert np.array_equal(Q0, Q1) and h0["merit"] == h1["merit"]
+    Q2, h2 = pl.plan(wl.q[0], wl.q[-1], 10, field, pl.Params(iters=5, mu=0.5, partition_radius=1.5))
+    assert np.all(np.diff(h2["merit"]) <= 0.0)
