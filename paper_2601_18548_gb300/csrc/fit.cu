@@ -6,13 +6,14 @@
 //   forward   v = [p, x, y, sin a, cos a, ...]; z_1 = W_1 v + b_1; h_l = s(z_l);
 //             z_{l+1} = W_{l+1} h_l + b_{l+1}; f = w_o . h_L + b_o
 //   backward  delta_L = g w_o * s'(z_L); delta_{l-1} = (delta_l W_l) * s'(z_{l-1});
-//             dW_l = delta_l^T h_{l-1}; db_l = delta_l^T 1; dw_o = h_L^T g; db_o = g^T 1;
+//             dW_l = delta_l^T h_{l-1}; db_l = sum_b delta_l; dw_o = h_L^T g; db_o = sum_b g;
 //             dv = delta_1 W_1 -> dq (sin/cos chain rule)
 //
-// Every product is one strided FP32 GEMM kernel (128 x 128 tiles, 8 x 8
-// outputs per thread); products that reduce over the batch (the weight and
-// bias gradients) split the batch into chunks whose partial tiles are summed
-// in a fixed order, so the gradients are deterministic.
+// Every matrix product is one strided FP32 GEMM kernel (128 x 128 tiles, 8 x 8
+// outputs per thread); the vector products (the output f, the bias and
+// output-weight gradients) are a warp-per-row dot and a column reduction.
+// Whatever reduces over the batch (weight and bias gradients) splits it into
+// chunks whose partials are summed in a fixed order: deterministic gradients.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -105,6 +106,32 @@ __global__ void sum_partials_kernel(const float* __restrict__ P, int splits, int
   }
 }
 
+// out[c] = sum_b X[b, c] w_b (w NULL: 1) over the rows of one of `chunks`
+// consecutive row chunks: partial[chunk, c] (thread = column, coalesced rows).
+__global__ void colsum_kernel(const float* __restrict__ X, int rows, int C, const float* __restrict__ w, int chunks,
+                              float* __restrict__ partial) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const int per = (rows + chunks - 1) / chunks;
+  const int r0 = blockIdx.y * per, r1 = min(rows, r0 + per);
+  float s = 0.f;
+  for (int b = r0; b < r1; ++b) s = fmaf(X[(long long)b * C + c], w ? w[b] : 1.f, s);
+  partial[(long long)blockIdx.y * C + c] = s;
+}
+
+// f_b = X[b, :] . v + *c0, one warp per row (lane-strided sums, fixed butterfly).
+__global__ void rowdot_kernel(const float* __restrict__ X, int rows, int C, const float* __restrict__ v,
+                              const float* __restrict__ c0, float* __restrict__ f) {
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= rows) return;
+  const float* x = X + warp * C;
+  float s = 0.f;
+  for (int c = lane; c < C; c += 32) s = fmaf(x[c], v[c], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) f[warp] = s + *c0;
+}
+
 // v = [p, x, y, sin a_1, cos a_1, ...] per sample.
 __global__ void encode_kernel(const float* __restrict__ q, const float* __restrict__ p, int B, int n, int d_in,
                               float* __restrict__ X) {
@@ -138,11 +165,6 @@ __global__ void bias_silu_kernel(float* __restrict__ Z, const float* __restrict_
   }
 }
 
-__global__ void add_scalar_kernel(float* __restrict__ x, long long n, const float* __restrict__ c) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    x[e] += *c;
-}
-
 // delta_L = g w_o * S_L
 __global__ void seed_kernel(const float* __restrict__ g, const float* __restrict__ wo, const float* __restrict__ S,
                             long long rows, int H, float* __restrict__ D) {
@@ -156,11 +178,6 @@ __global__ void mul_kernel(float* __restrict__ D, const float* __restrict__ S, l
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x)
     D[e] *= S[e];
-}
-
-__global__ void fill_kernel(float* __restrict__ x, long long n, float v) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    x[e] = v;
 }
 
 // dq from dv: x, y direct; angle a: cos a dv[sin a] - sin a dv[cos a]
@@ -224,6 +241,17 @@ cudaError_t gemm(const float* A, long long sam, long long sak, const float* B, l
   return cudaGetLastError();
 }
 
+// out (C) = X^T w over the batch (w NULL: column sums), in a fixed order.
+cudaError_t colsum(const float* X, int rows, int C, const float* w, float* out, float* partials, size_t pfl,
+                   cudaStream_t s) {
+  int chunks = 64;
+  while (chunks > 1 && (size_t)chunks * C > pfl) --chunks;
+  dim3 grid((C + 255) / 256, chunks);
+  colsum_kernel<<<grid, 256, 0, s>>>(X, rows, C, w, chunks, partials);
+  sum_partials_kernel<<<grid1(C), 256, 0, s>>>(partials, chunks, 1, C, C, out, C);
+  return cudaGetLastError();
+}
+
 bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 struct Shape {
@@ -269,10 +297,9 @@ int forward(const Shape& sh, const float* w, const float* q, const float* p, int
     bias_silu_kernel<<<grid1((long long)B * sh.H), 256, 0, s>>>(Hs[l], W + (size_t)sh.H * K, B, sh.H, Ss[l - 1]);
   }
   if (f) {
-    // f (B x 1) = H_L w_o + b_o
-    if ((e = gemm(Hs[sh.L], sh.H, 1, w + sh.off_out, 1, 1, f, 1, B, 1, sh.H, nullptr, 0, s)))
-      return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
-    add_scalar_kernel<<<grid1(B), 256, 0, s>>>(f, B, w + sh.off_out + sh.H);
+    // f (B) = H_L w_o + b_o
+    rowdot_kernel<<<(int)(((long long)B * 32 + 255) / 256), 256, 0, s>>>(Hs[sh.L], B, sh.H, w + sh.off_out,
+                                                                      w + sh.off_out + sh.H, f);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit forward launch: %s", cudaGetErrorString(e));
@@ -333,7 +360,7 @@ int gcdf_fit_vjp(const gcdf_fit_desc* desc, const float* weights, const float* q
   Ws ws(s);
   float* Hs[18];
   float* Ss[17];
-  float *D0, *D1, *ones, *partials;
+  float *D0, *D1, *partials;
   const size_t pfl = (size_t)64 * sh.H * (sh.H > sh.d_in ? sh.H : sh.d_in);
   if ((e = ws.get(&Hs[0], (size_t)batch * sh.d_in))) return set_error(GCDF_ENOMEM, "cudaMallocAsync");
   for (int l = 1; l <= sh.L; ++l)
@@ -341,18 +368,18 @@ int gcdf_fit_vjp(const gcdf_fit_desc* desc, const float* weights, const float* q
       return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
   const size_t dcols = (size_t)(sh.H > sh.d_in ? sh.H : sh.d_in);
   if ((e = ws.get(&D0, (size_t)batch * dcols)) || (e = ws.get(&D1, (size_t)batch * dcols)) ||
-      (e = ws.get(&ones, (size_t)batch)) ||
+
       (e = ws.get(&partials, pfl)))
     return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
   rc = forward(sh, weights, q, p, batch, Hs, Ss, nullptr, partials, pfl, s);
   if (rc) return rc;
-  fill_kernel<<<grid1(batch), 256, 0, s>>>(ones, batch, 1.f);
+
   const int H = sh.H;
   float* dwo = dweights + sh.off_out;
-  // dw_o (H x 1) = H_L^T g;  db_o = g^T 1
-  if ((e = gemm(Hs[sh.L], 1, H, g_f, 1, 1, dwo, 1, H, 1, batch, partials, pfl, s)) ||
-      (e = gemm(g_f, 1, 1, ones, 1, 1, dwo + H, 1, 1, 1, batch, partials, pfl, s)))
-    return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+  // dw_o (H) = H_L^T g;  db_o = g^T 1
+  if ((e = colsum(Hs[sh.L], batch, H, g_f, dwo, partials, pfl, s)) ||
+      (e = colsum(g_f, batch, 1, nullptr, dwo + H, partials, pfl, s)))
+    return set_error(GCDF_ECUDA, "colsum: %s", cudaGetErrorString(e));
   // delta_L = g w_o * s'(z_L)
   float* D = D1;
   seed_kernel<<<grid1((long long)batch * H), 256, 0, s>>>(g_f, weights + sh.off_out, Ss[sh.L - 1], batch, H, D);
@@ -362,7 +389,7 @@ int gcdf_fit_vjp(const gcdf_fit_desc* desc, const float* weights, const float* q
     float* dW = dweights + sh.off(l);
     // dW_l (H x K) = delta^T (H x B) H_{l-1} (B x K);  db_l = delta^T 1
     if ((e = gemm(D, 1, H, Hs[l - 1], K, 1, dW, K, H, K, batch, partials, pfl, s)) ||
-        (e = gemm(D, 1, H, ones, 1, 1, dW + (size_t)H * K, 1, H, 1, batch, partials, pfl, s)))
+        (e = colsum(D, batch, H, nullptr, dW + (size_t)H * K, partials, pfl, s)))
       return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
     if (l > 1 || dq) {
       // back (B x K) = delta (B x H) W_l (H x K)
