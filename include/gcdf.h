@@ -62,7 +62,7 @@ enum gcdf_status {
   GCDF_EINVAL = 1,       /* bad shape, NULL or misaligned pointer, bad enum */
   GCDF_ENOMEM = 2,       /* device allocation failed */
   GCDF_ECUDA = 3,        /* a CUDA call or kernel launch failed */
-  GCDF_EUNSUPPORTED = 4, /* valid request this build does not implement */
+  GCDF_EUNSUPPORTED = 4, /* valid request the library does not implement */
   GCDF_EAGAIN = 5,       /* planning server: the queue is full, try again later */
   GCDF_PENDING = 6,      /* planning server: the request is not finished yet (poll only) */
   GCDF_ETIMEOUT = 7      /* a device wait gave up (see gcdf_device_status) */
