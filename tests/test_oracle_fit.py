@@ -50,3 +50,30 @@ def test_weight_and_configuration_vjp_match_central_differences():
             qm[b, d] -= h
             fd = (loss(w, qp) - loss(w, qm)) / (2 * h)
             assert abs(fd - dq[b, d]) <= 1e-6 * max(1.0, abs(dq[b, d]))
+
+
+def test_second_order_vjp_matches_central_differences_of_the_gradient_loss():
+    """L = g . f + sum_b G_b . grad_q f_b with grad_q f from the query oracle
+    (an independent reverse sweep): its weight gradient by central differences."""
+    n, H, L = 9, 24, 3
+    shape, w = small_net(n, hidden=H, n_layers=L)
+    w = np.asarray(w, dtype=np.float64)
+    q, p = _batch(n, 4, 5)
+    rng = np.random.default_rng(6)
+    g = rng.normal(size=4)
+    G = rng.normal(size=(4, n))
+    dw = fit.vjp2(n, H, L, w, q, p, g, G)
+
+    def loss(wv):
+        f, dq = mlp.eval_pairs(n, H, L, wv, q, p, np.arange(4), np.arange(4))
+        return float(g @ f + np.sum(G * dq))
+    h = 1e-4
+    picks = np.unique(np.concatenate([rng.integers(0, w.size, 80), [0, 5, 3 * H, w.size - 1, w.size - 2]]))
+    for k in picks:
+        wp, wm = w.copy(), w.copy()
+        wp[k] += h
+        wm[k] -= h
+        fd = (loss(wp) - loss(wm)) / (2 * h)
+        assert abs(fd - dw[k]) <= 1e-6 * max(1.0, abs(dw[k])), (k, fd, dw[k])
+    # with G = 0 it is the first-order weight gradient
+    assert np.allclose(fit.vjp2(n, H, L, w, q, p, g, 0 * G), fit.vjp(n, H, L, w, q, p, g)[0], rtol=1e-12, atol=1e-12)
