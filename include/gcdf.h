@@ -294,6 +294,22 @@ GCDF_API int gcdf_fit_forward(const gcdf_fit_desc *desc, const float *weights, c
 GCDF_API int gcdf_fit_vjp(const gcdf_fit_desc *desc, const float *weights, const float *q, const float *p,
                           int batch, const float *g_f, float *dweights, float *dq, gcdf_stream_t stream);
 
+/* f (batch,) and dq (batch, n) DEVICE out: f(q_b, p_b) and its gradient
+ * grad_q f(q_b, p_b) (the per-sample field and gradient that the regularisers
+ * of Table I — gradient direction, eikonal, tension — are built from). */
+GCDF_API int gcdf_fit_value_grad(const gcdf_fit_desc *desc, const float *weights, const float *q, const float *p,
+                                 int batch, float *f, float *dq, gcdf_stream_t stream);
+
+/* Second-order vector-Jacobian product for a loss of f and grad_q f: with
+ * g_f (batch,) = dL/df_b and G_q (batch, n) = dL/d(grad_q f_b), both DEVICE,
+ * dweights (gcdf_weight_count) DEVICE out = sum_b [g_b df_b/dweights +
+ * G_b . d(grad_q f_b)/dweights] (written, not accumulated).  The gradient of
+ * such a loss with respect to q itself is not provided.  Temporaries: about
+ * 5 L + 3 batch x hidden floats (activations, s', s'', the reverse sweep) and
+ * the partials array. */
+GCDF_API int gcdf_fit_vjp2(const gcdf_fit_desc *desc, const float *weights, const float *q, const float *p,
+                           int batch, const float *g_f, const float *G_q, float *dweights, gcdf_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Trajectory optimisation with the GCDF collision cost (Sec. IV-A).
  *

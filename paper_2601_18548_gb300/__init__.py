@@ -362,3 +362,55 @@ class FieldFunction(torch.autograd.Function):
 def field(weights: torch.Tensor, q: torch.Tensor, p: torch.Tensor, shape) -> torch.Tensor:
     """Differentiable per-sample field values (weights: flat FP32 CUDA tensor)."""
     return FieldFunction.apply(weights, q, p, tuple(shape))
+
+
+def fit_value_grad(shape, weights, q, p, stream=None):
+    """gcdf_fit_value_grad: (f (B,), grad_q f (B, n)) per sample."""
+    d = _lib.FitDesc(*[int(x) for x in shape])
+    f = torch.empty(q.shape[0], device=q.device, dtype=torch.float32)
+    dq = torch.empty_like(q)
+    _lib.check(_lib.load().gcdf_fit_value_grad(ctypes.byref(d), _ptr(weights, name="weights"), _ptr(q, name="q"),
+                                               _ptr(p, name="p"), int(q.shape[0]), _ptr(f, name="f"),
+                                               _ptr(dq, name="dq"), _stream(stream)))
+    return f, dq
+
+
+def fit_vjp2(shape, weights, q, p, g_f, G_q, stream=None):
+    """gcdf_fit_vjp2: dweights of sum_b g_b f_b + G_b . grad_q f_b."""
+    d = _lib.FitDesc(*[int(x) for x in shape])
+    dw = torch.empty_like(weights)
+    _lib.check(_lib.load().gcdf_fit_vjp2(ctypes.byref(d), _ptr(weights, name="weights"), _ptr(q, name="q"),
+                                         _ptr(p, name="p"), int(q.shape[0]), _ptr(g_f.contiguous(), name="g_f"),
+                                         _ptr(G_q.contiguous(), name="G_q"), _ptr(dw, name="dweights"),
+                                         _stream(stream)))
+    return dw
+
+
+class FieldGradFunction(torch.autograd.Function):
+    """(f, grad_q f)(q_b, p_b; weights) as an autograd.Function for losses on
+    the field and its gradient (the gradient, eikonal and tension terms of
+    Table I); the backward pass is gcdf_fit_vjp2 and gives the weight gradient
+    only."""
+
+    @staticmethod
+    def forward(ctx, weights, q, p, shape):
+        ctx.save_for_backward(weights, q, p)
+        ctx.shape = shape
+        return fit_value_grad(shape, weights.detach(), q.detach(), p)
+
+    @staticmethod
+    def backward(ctx, g_f, G_q):
+        if ctx.needs_input_grad[1] or ctx.needs_input_grad[2]:
+            raise RuntimeError("field_grad: gradients with respect to q or p are not provided")
+        weights, q, p = ctx.saved_tensors
+        if g_f is None:
+            g_f = torch.zeros(q.shape[0], device=q.device, dtype=torch.float32)
+        if G_q is None:
+            G_q = torch.zeros_like(q)
+        dw = fit_vjp2(ctx.shape, weights.detach(), q.detach(), p, g_f.detach().float(), G_q.detach().float())
+        return dw, None, None, None
+
+
+def field_grad(weights: torch.Tensor, q: torch.Tensor, p: torch.Tensor, shape):
+    """Differentiable (f, grad_q f) per sample, with respect to the weights."""
+    return FieldGradFunction.apply(weights, q, p, tuple(shape))

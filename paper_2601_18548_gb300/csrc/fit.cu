@@ -9,6 +9,18 @@
 //             dW_l = delta_l^T h_{l-1}; db_l = sum_b delta_l; dw_o = h_L^T g; db_o = sum_b g;
 //             dv = delta_1 W_1 -> dq (sin/cos chain rule)
 //
+// The regularisers of Table I (gradient direction, eikonal, tension) are
+// functions of grad_q f, so training on them needs the weight gradient of
+// sum_b G_b . grad_q f_b: a second-order product.  With a_l the factor of the
+// reverse sweep (a_L = w_o, delta_l = a_l * s'(z_l), a_{l-1} = delta_l W_l),
+// u = C^T G (C the sin/cos chain rule dv -> dq) and r_1 = u W_1^T,
+// r_{l+1} = (r_l * s'(z_l)) W_{l+1}^T:
+//   dW_1 += delta_1^T u;  dW_{l+1} += delta_{l+1}^T (r_l * s'(z_l));  dw_o += sum_b r_L * s'(z_L)
+// and the second-derivative terms e_l = r_l * a_l * s''(z_l) run back through
+// the network with the value term g:
+//   eps_L = e_L + g w_o * s'(z_L);  eps_{l-1} = e_{l-1} + (eps_l W_l) * s'(z_{l-1})
+//   dW_l += eps_l^T h_{l-1};  db_l = sum_b eps_l;  dw_o += h_L^T g;  db_o = sum_b g
+//
 // Every matrix product is one strided FP32 GEMM kernel (128 x 128 tiles, 8 x 8
 // outputs per thread); the vector products (the output f, the bias and
 // output-weight gradients) are a warp-per-row dot and a column reduction.
@@ -35,7 +47,7 @@ constexpr int kBM = 128, kBN = 128, kBK = 8, kGemmThreads = 256;
 __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const float* __restrict__ A, long long sam, long long sak,
                                                             const float* __restrict__ B, long long sbk,
                                                             long long sbn, float* __restrict__ C, int ldc, int M,
-                                                            int N, int K, int kc) {
+                                                            int N, int K, int kc, int accumulate) {
   __shared__ __align__(16) float As[kBK][kBM];
   __shared__ __align__(16) float Bs[kBK][kBN];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -88,21 +100,24 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const float* __restr
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
-      if (n < N) Cz[(long long)m * ldc + n] = acc[i][j];
+      if (n < N) {
+        float* c = Cz + (long long)m * ldc + n;
+        *c = accumulate ? *c + acc[i][j] : acc[i][j];
+      }
     }
   }
 }
 
 // C = sum over z of the partial tiles, in increasing z.
 __global__ void sum_partials_kernel(const float* __restrict__ P, int splits, int M, int N, int ldp,
-                                    float* __restrict__ C, int ldc) {
+                                    float* __restrict__ C, int ldc, int accumulate) {
   const long long total = (long long)M * N;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(e / N), n = (int)(e - (long long)m * N);
     float s = 0.f;
     for (int z = 0; z < splits; ++z) s += P[((long long)z * M + m) * ldp + n];
-    C[(long long)m * ldc + n] = s;
+    C[(long long)m * ldc + n] = accumulate ? C[(long long)m * ldc + n] + s : s;
   }
 }
 
@@ -152,9 +167,11 @@ __global__ void encode_kernel(const float* __restrict__ q, const float* __restri
   }
 }
 
-// z += b (per column); h = s(z) in place; s'(z) -> S.
+// z += b (per column); h = s(z) in place; s'(z) -> S; s''(z) -> S2 unless NULL.
+// With sg = 1 / (1 + e^-z): s = z sg, s' = sg (1 + z (1 - sg)),
+// s'' = sg (1 - sg) (2 + z (1 - 2 sg)).
 __global__ void bias_silu_kernel(float* __restrict__ Z, const float* __restrict__ bias, long long rows, int H,
-                                 float* __restrict__ S) {
+                                 float* __restrict__ S, float* __restrict__ S2) {
   const long long total = rows * H;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -162,16 +179,68 @@ __global__ void bias_silu_kernel(float* __restrict__ Z, const float* __restrict_
     const float sg = 1.f / (1.f + expf(-z));
     Z[e] = z * sg;
     S[e] = sg * (1.f + z * (1.f - sg));
+    if (S2) S2[e] = sg * (1.f - sg) * (2.f + z * (1.f - 2.f * sg));
   }
 }
 
-// delta_L = g w_o * S_L
+// delta_L = g w_o * S_L (g NULL: 1)
 __global__ void seed_kernel(const float* __restrict__ g, const float* __restrict__ wo, const float* __restrict__ S,
                             long long rows, int H, float* __restrict__ D) {
   const long long total = rows * H;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x)
-    D[e] = g[e / H] * wo[e % H] * S[e];
+    D[e] = (g ? g[e / H] : 1.f) * wo[e % H] * S[e];
+}
+
+// O = X * Y elementwise (O may alias X or Y)
+__global__ void mul2_kernel(float* O, const float* X, const float* Y, long long total) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    O[e] = X[e] * Y[e];
+}
+
+// E = r * a * S2 with a = A, or the broadcast row wo when A is NULL (E may alias A)
+__global__ void second_kernel(const float* __restrict__ R, const float* A, const float* __restrict__ wo,
+                              const float* __restrict__ S2, long long rows, int H, float* E) {
+  const long long total = rows * H;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    E[e] = R[e] * (A ? A[e] : wo[e % H]) * S2[e];
+}
+
+// X = Y + X * S  (eps_{l-1} = e_{l-1} + back * s'(z_{l-1}))
+__global__ void addmul_kernel(float* __restrict__ X, const float* __restrict__ S, const float* __restrict__ Y,
+                              long long total) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    X[e] = Y[e] + X[e] * S[e];
+}
+
+// E += g w_o * S  (the value term of eps_L)
+__global__ void seed_add_kernel(const float* __restrict__ g, const float* __restrict__ wo,
+                                const float* __restrict__ S, long long rows, int H, float* __restrict__ E) {
+  const long long total = rows * H;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    E[e] += g[e / H] * wo[e % H] * S[e];
+}
+
+// u = C^T G: the adjoint of the sin/cos chain rule (zeros at the point columns)
+__global__ void dq_adjoint_kernel(const float* __restrict__ q, const float* __restrict__ G, int B, int n, int d_in,
+                                  float* __restrict__ U) {
+  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x) {
+    const float* gb = G + b * n;
+    float* u = U + b * d_in;
+    u[0] = u[1] = u[2] = 0.f;
+    u[3] = gb[0];
+    u[4] = gb[1];
+    for (int a = 0; a < n - 2; ++a) {
+      float sn, cs;
+      sincosf(q[b * n + 2 + a], &sn, &cs);
+      u[5 + 2 * a] = cs * gb[2 + a];
+      u[6 + 2 * a] = -sn * gb[2 + a];
+    }
+  }
 }
 
 __global__ void mul_kernel(float* __restrict__ D, const float* __restrict__ S, long long total) {
@@ -217,10 +286,12 @@ struct Ws {
   }
 };
 
-// C (M x N, ldc) = A(m, k) B(k, n) summed over K; the batch-length reductions
-// (large K, few output tiles) go through `splits` chunks and the partials array.
+// C (M x N, ldc) = (or +=, with accumulate) A(m, k) B(k, n) summed over K; the
+// batch-length reductions (large K, few output tiles) go through `splits`
+// chunks and the partials array.
 cudaError_t gemm(const float* A, long long sam, long long sak, const float* B, long long sbk, long long sbn,
-                 float* C, int ldc, int M, int N, int K, float* partials, size_t partial_floats, cudaStream_t s) {
+                 float* C, int ldc, int M, int N, int K, float* partials, size_t partial_floats, cudaStream_t s,
+                 bool accumulate = false) {
   if (M == 0 || N == 0) return cudaSuccess;
   const int tm = (M + kBM - 1) / kBM, tn = (N + kBN - 1) / kBN;
   int splits = 1;
@@ -233,22 +304,23 @@ cudaError_t gemm(const float* A, long long sam, long long sak, const float* B, l
   if (splits < 1) splits = 1;
   dim3 grid(tn, tm, splits);
   if (splits == 1) {
-    gemm_kernel<<<grid, kGemmThreads, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, kc);
+    gemm_kernel<<<grid, kGemmThreads, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, kc, accumulate ? 1 : 0);
   } else {
-    gemm_kernel<<<grid, kGemmThreads, 0, s>>>(A, sam, sak, B, sbk, sbn, partials, N, M, N, K, kc);
-    sum_partials_kernel<<<grid1((long long)M * N), 256, 0, s>>>(partials, splits, M, N, N, C, ldc);
+    gemm_kernel<<<grid, kGemmThreads, 0, s>>>(A, sam, sak, B, sbk, sbn, partials, N, M, N, K, kc, 0);
+    sum_partials_kernel<<<grid1((long long)M * N), 256, 0, s>>>(partials, splits, M, N, N, C, ldc,
+                                                                accumulate ? 1 : 0);
   }
   return cudaGetLastError();
 }
 
 // out (C) = X^T w over the batch (w NULL: column sums), in a fixed order.
 cudaError_t colsum(const float* X, int rows, int C, const float* w, float* out, float* partials, size_t pfl,
-                   cudaStream_t s) {
+                   cudaStream_t s, bool accumulate = false) {
   int chunks = 64;
   while (chunks > 1 && (size_t)chunks * C > pfl) --chunks;
   dim3 grid((C + 255) / 256, chunks);
   colsum_kernel<<<grid, 256, 0, s>>>(X, rows, C, w, chunks, partials);
-  sum_partials_kernel<<<grid1(C), 256, 0, s>>>(partials, chunks, 1, C, C, out, C);
+  sum_partials_kernel<<<grid1(C), 256, 0, s>>>(partials, chunks, 1, C, C, out, C, accumulate ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -283,9 +355,10 @@ int check(const gcdf_fit_desc* d, const float* w, const float* q, const float* p
   return GCDF_OK;
 }
 
-// Forward pass storing h_l (Hs[l], l = 0 .. L, Hs[0] = v) and s'(z_l) (Ss[l - 1]).
+// Forward pass storing h_l (Hs[l], l = 0 .. L, Hs[0] = v), s'(z_l) (Ss[l - 1])
+// and, when S2s is given, s''(z_l) (S2s[l - 1]).
 int forward(const Shape& sh, const float* w, const float* q, const float* p, int B, float** Hs, float** Ss, float* f,
-            float* partials, size_t pfl, cudaStream_t s) {
+            cudaStream_t s, float** S2s = nullptr) {
   cudaError_t e;
   encode_kernel<<<grid1(B), 256, 0, s>>>(q, p, B, sh.n, sh.d_in, Hs[0]);
   for (int l = 1; l <= sh.L; ++l) {
@@ -294,7 +367,8 @@ int forward(const Shape& sh, const float* w, const float* q, const float* p, int
     // Z (B x H) = H_{l-1} (B x K) W^T
     if ((e = gemm(Hs[l - 1], K, 1, W, 1, K, Hs[l], sh.H, B, sh.H, K, nullptr, 0, s)))
       return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
-    bias_silu_kernel<<<grid1((long long)B * sh.H), 256, 0, s>>>(Hs[l], W + (size_t)sh.H * K, B, sh.H, Ss[l - 1]);
+    bias_silu_kernel<<<grid1((long long)B * sh.H), 256, 0, s>>>(Hs[l], W + (size_t)sh.H * K, B, sh.H, Ss[l - 1],
+                                                                S2s ? S2s[l - 1] : nullptr);
   }
   if (f) {
     // f (B) = H_L w_o + b_o
@@ -303,6 +377,23 @@ int forward(const Shape& sh, const float* w, const float* q, const float* p, int
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit forward launch: %s", cudaGetErrorString(e));
+  return GCDF_OK;
+}
+
+// Reverse sweep of the field's own gradient: delta_l = a_l * s'(z_l) into
+// D[l - 1], a_L = w_o, a_{l-1} = delta_l W_l into A[l - 2] (A[l - 2] may be
+// D[l - 2]: then only delta survives), for l = L .. 1.
+int reverse_sweep(const Shape& sh, const float* w, int B, float** Ss, float** D, float** A, cudaStream_t s) {
+  const int H = sh.H;
+  const long long n = (long long)B * H;
+  seed_kernel<<<grid1(n), 256, 0, s>>>(nullptr, w + sh.off_out, Ss[sh.L - 1], B, H, D[sh.L - 1]);
+  for (int l = sh.L; l >= 2; --l) {
+    cudaError_t e = gemm(D[l - 1], H, 1, w + sh.off(l), H, 1, A[l - 2], H, B, H, H, nullptr, 0, s);
+    if (e) return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+    mul2_kernel<<<grid1(n), 256, 0, s>>>(D[l - 2], A[l - 2], Ss[l - 2], n);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(GCDF_ECUDA, "reverse sweep launch: %s", cudaGetErrorString(e));
   return GCDF_OK;
 }
 
@@ -335,7 +426,7 @@ int gcdf_fit_forward(const gcdf_fit_desc* desc, const float* weights, const floa
     Hs[l] = (l & 1) ? h0 : h1;
     Ss[l - 1] = sc;
   }
-  rc = forward(sh, weights, q, p, batch, Hs, Ss, f, nullptr, 0, s);
+  rc = forward(sh, weights, q, p, batch, Hs, Ss, f, s);
   if (rc) return rc;
   clear_error();
   return GCDF_OK;
@@ -371,7 +462,7 @@ int gcdf_fit_vjp(const gcdf_fit_desc* desc, const float* weights, const float* q
 
       (e = ws.get(&partials, pfl)))
     return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
-  rc = forward(sh, weights, q, p, batch, Hs, Ss, nullptr, partials, pfl, s);
+  rc = forward(sh, weights, q, p, batch, Hs, Ss, nullptr, s);
   if (rc) return rc;
 
   const int H = sh.H;
@@ -406,6 +497,122 @@ int gcdf_fit_vjp(const gcdf_fit_desc* desc, const float* weights, const float* q
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit backward launch: %s", cudaGetErrorString(e));
+  clear_error();
+  return GCDF_OK;
+}
+
+int gcdf_fit_value_grad(const gcdf_fit_desc* desc, const float* weights, const float* q, const float* p, int batch,
+                        float* f, float* dq, gcdf_stream_t stream) {
+  Shape sh;
+  int rc = check(desc, weights, q, p, batch, sh);
+  if (rc) return rc;
+  if (batch == 0) { clear_error(); return GCDF_OK; }
+  if (!f || !al16(f) || !dq || !al16(dq)) return set_error(GCDF_EINVAL, "f or dq NULL or not 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  Ws ws(s);
+  float* Hs[18];
+  float* Ss[17];
+  float* D[17];
+  float *d0, *d1, *dv;
+  cudaError_t e;
+  if ((e = ws.get(&Hs[0], (size_t)batch * sh.d_in)) || (e = ws.get(&dv, (size_t)batch * sh.d_in)) ||
+      (e = ws.get(&d0, (size_t)batch * sh.H)) || (e = ws.get(&d1, (size_t)batch * sh.H)))
+    return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  for (int l = 1; l <= sh.L; ++l)
+    if ((e = ws.get(&Hs[l], (size_t)batch * sh.H)) || (e = ws.get(&Ss[l - 1], (size_t)batch * sh.H)))
+      return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  rc = forward(sh, weights, q, p, batch, Hs, Ss, f, s);
+  if (rc) return rc;
+  // delta ping-pongs between two buffers, a_{l-1} computed in place of delta_{l-1}
+  for (int l = 1; l <= sh.L; ++l) D[l - 1] = ((sh.L - l) & 1) ? d1 : d0;
+  if ((rc = reverse_sweep(sh, weights, batch, Ss, D, D, s))) return rc;
+  // dv (B x d_in) = delta_1 W_1
+  if ((e = gemm(D[0], sh.H, 1, weights, sh.d_in, 1, dv, sh.d_in, batch, sh.d_in, sh.H, nullptr, 0, s)))
+    return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+  dq_kernel<<<grid1(batch), 256, 0, s>>>(q, dv, batch, sh.n, sh.d_in, dq);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit value/grad launch: %s", cudaGetErrorString(e));
+  clear_error();
+  return GCDF_OK;
+}
+
+int gcdf_fit_vjp2(const gcdf_fit_desc* desc, const float* weights, const float* q, const float* p, int batch,
+                  const float* g_f, const float* G_q, float* dweights, gcdf_stream_t stream) {
+  Shape sh;
+  int rc = check(desc, weights, q, p, batch, sh);
+  if (rc) return rc;
+  if (!dweights || !al16(dweights)) return set_error(GCDF_EINVAL, "dweights NULL or not 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (batch == 0) {
+    if ((e = cudaMemsetAsync(dweights, 0, sh.total * sizeof(float), s)))
+      return set_error(GCDF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    clear_error();
+    return GCDF_OK;
+  }
+  if (!g_f || !al16(g_f) || !G_q || !al16(G_q))
+    return set_error(GCDF_EINVAL, "g_f or G_q NULL or not 16-byte aligned");
+  const int H = sh.H, L = sh.L;
+  const long long n = (long long)batch * H;
+  Ws ws(s);
+  float *Hs[18], *S1[17], *S2[17], *D[17], *AE[17];
+  float *U, *R0, *R1, *partials;
+  const size_t pfl = (size_t)64 * H * (H > sh.d_in ? H : sh.d_in);
+  if ((e = ws.get(&Hs[0], (size_t)batch * sh.d_in)) || (e = ws.get(&U, (size_t)batch * sh.d_in)) ||
+      (e = ws.get(&R0, (size_t)n)) || (e = ws.get(&R1, (size_t)n)) || (e = ws.get(&partials, pfl)))
+    return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  for (int l = 1; l <= L; ++l)
+    if ((e = ws.get(&Hs[l], (size_t)n)) || (e = ws.get(&S1[l - 1], (size_t)n)) || (e = ws.get(&S2[l - 1], (size_t)n)) ||
+        (e = ws.get(&D[l - 1], (size_t)n)) || (e = ws.get(&AE[l - 1], (size_t)n)))
+      return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  if ((rc = forward(sh, weights, q, p, batch, Hs, S1, nullptr, s, S2))) return rc;
+  // a_l (l < L) into AE[l - 1]; a_L = w_o is never stored
+  if ((rc = reverse_sweep(sh, weights, batch, S1, D, AE, s))) return rc;
+  const float* wo = weights + sh.off_out;
+  float* dwo = dweights + sh.off_out;
+  // first-derivative terms (written): u = C^T G; dW_1 = delta_1^T u; r_1 = u W_1^T
+  dq_adjoint_kernel<<<grid1(batch), 256, 0, s>>>(q, G_q, batch, sh.n, sh.d_in, U);
+  if ((e = gemm(D[0], 1, H, U, sh.d_in, 1, dweights, sh.d_in, H, sh.d_in, batch, partials, pfl, s)) ||
+      (e = gemm(U, sh.d_in, 1, weights, 1, sh.d_in, R0, H, batch, H, sh.d_in, nullptr, 0, s)))
+    return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+  float *r = R0, *rs = R1;
+  for (int l = 1; l <= L; ++l) {
+    // e_l = r_l * a_l * s''(z_l), in place of a_l
+    second_kernel<<<grid1(n), 256, 0, s>>>(r, l < L ? AE[l - 1] : nullptr, wo, S2[l - 1], batch, H, AE[l - 1]);
+    mul2_kernel<<<grid1(n), 256, 0, s>>>(rs, r, S1[l - 1], n);
+    if (l < L) {
+      // dW_{l+1} = delta_{l+1}^T rs;  r_{l+1} = rs W_{l+1}^T
+      const float* W = weights + sh.off(l + 1);
+      if ((e = gemm(D[l], 1, H, rs, H, 1, dweights + sh.off(l + 1), H, H, H, batch, partials, pfl, s)) ||
+          (e = gemm(rs, H, 1, W, 1, H, r, H, batch, H, H, nullptr, 0, s)))
+        return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+    } else if ((e = colsum(rs, batch, H, nullptr, dwo, partials, pfl, s))) {  // dw_o = sum_b r_L * s'(z_L)
+      return set_error(GCDF_ECUDA, "colsum: %s", cudaGetErrorString(e));
+    }
+  }
+  // value and second-derivative terms (accumulated; biases written)
+  if ((e = colsum(Hs[L], batch, H, g_f, dwo, partials, pfl, s, true)) ||
+      (e = colsum(g_f, batch, 1, nullptr, dwo + H, partials, pfl, s)))
+    return set_error(GCDF_ECUDA, "colsum: %s", cudaGetErrorString(e));
+  float* eps = AE[L - 1];
+  seed_add_kernel<<<grid1(n), 256, 0, s>>>(g_f, wo, S1[L - 1], batch, H, eps);
+  for (int l = L; l >= 1; --l) {
+    const int K = sh.fan_in(l);
+    float* dW = dweights + sh.off(l);
+    if ((e = gemm(eps, 1, H, Hs[l - 1], K, 1, dW, K, H, K, batch, partials, pfl, s, true)) ||
+        (e = colsum(eps, batch, H, nullptr, dW + (size_t)H * K, partials, pfl, s)))
+      return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+    if (l > 1) {
+      // eps_{l-1} = e_{l-1} + (eps_l W_l) * s'(z_{l-1})
+      float* back = (eps == R0) ? R1 : R0;
+      if ((e = gemm(eps, H, 1, weights + sh.off(l), H, 1, back, H, batch, H, H, nullptr, 0, s)))
+        return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+      addmul_kernel<<<grid1(n), 256, 0, s>>>(back, S1[l - 2], AE[l - 2], n);
+      eps = back;
+    }
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit vjp2 launch: %s", cudaGetErrorString(e));
   clear_error();
   return GCDF_OK;
 }

@@ -80,3 +80,86 @@ def test_fit_lowers_the_distance_loss():
         opt.step()
         losses.append(float(loss.detach()))
     assert losses[-1] < 0.5 * losses[0]
+
+
+@pytest.mark.parametrize("n,H,L,B", [(9, 256, 4, 1000), (10, 128, 2, 2048), (3, 96, 1, 333)])
+def test_value_grad_and_vjp2_match_the_oracle(n, H, L, B):
+    torch = need_gpu()
+    g = lib()
+    shape, w = small_net(n, hidden=H, n_layers=L)
+    q, p = _batch(n, B, n * 31 + B)
+    rng = np.random.default_rng(B + 5)
+    gf = rng.normal(size=B).astype(np.float32)
+    Gq = rng.normal(size=(B, n)).astype(np.float32)
+    wd = to_dev(torch, np.asarray(w, np.float32))
+    qd, pd = to_dev(torch, q), to_dev(torch, p)
+    q64, p64 = q.astype(np.float64), p.astype(np.float64)
+    f, dq = g.fit_value_grad((n, H, L), wd, qd, pd)
+    f_ref, _ = fit.forward(n, H, L, w, q64, p64)
+    _, dq_ref = fit.vjp(n, H, L, w, q64, p64, np.ones(B))
+    assert metrics.rel_err_scalar(f.cpu().numpy(), f_ref).max() <= 1e-5
+    assert metrics.rel_err_vector(dq.cpu().numpy(), dq_ref).max() <= 1e-5
+    dw = g.fit_vjp2((n, H, L), wd, qd, pd, to_dev(torch, gf), to_dev(torch, Gq)).cpu().numpy()
+    dw_ref = fit.vjp2(n, H, L, w, q64, p64, gf.astype(np.float64), Gq.astype(np.float64))
+    err = np.linalg.norm(dw - dw_ref) / np.linalg.norm(dw_ref)
+    assert err <= 1e-5, err
+    lay, _ = fit._layers(n, H, L, w)
+    for (off, o, i) in lay:
+        blk = slice(off, off + o * i + o)
+        e_blk = np.linalg.norm(dw[blk] - dw_ref[blk]) / np.linalg.norm(dw_ref[blk])
+        assert e_blk <= 1e-4, (off, e_blk)
+
+
+def test_vjp2_without_gradient_terms_is_the_first_order_vjp_and_autograd_agrees():
+    torch = need_gpu()
+    g = lib()
+    n, H, L, B = 9, 128, 3, 4096
+    _, w = small_net(n, hidden=H, n_layers=L)
+    q, p = _batch(n, B, 11)
+    wd = to_dev(torch, np.asarray(w, np.float32))
+    qd, pd = to_dev(torch, q), to_dev(torch, p)
+    rng = np.random.default_rng(3)
+    gf = to_dev(torch, rng.normal(size=B).astype(np.float32))
+    Gq = to_dev(torch, rng.normal(size=(B, n)).astype(np.float32))
+    # G = 0: every second-order term is an exact zero, the sums run in the same order
+    a = g.fit_vjp2((n, H, L), wd, qd, pd, gf, torch.zeros_like(qd))
+    b, _ = g.fit_vjp((n, H, L), wd, qd, pd, gf, want_dq=False)
+    assert torch.equal(a, b)
+    # value_grad agrees with the first-order products bit for bit
+    f, dq = g.fit_value_grad((n, H, L), wd, qd, pd)
+    assert torch.equal(f, g.fit_forward((n, H, L), wd, qd, pd))
+    # deterministic, and the autograd Function routes to the same call
+    c = g.fit_vjp2((n, H, L), wd, qd, pd, gf, Gq)
+    assert torch.equal(c, g.fit_vjp2((n, H, L), wd, qd, pd, gf, Gq))
+    wr = wd.clone().requires_grad_(True)
+    f2, dq2 = g.field_grad(wr, qd, pd, (n, H, L))
+    ((f2 * gf).sum() + (dq2 * Gq).sum()).backward()
+    assert torch.equal(wr.grad, c)
+    with pytest.raises(RuntimeError):
+        f3, dq3 = g.field_grad(wd, qd.clone().requires_grad_(True), pd, (n, H, L))
+        dq3.sum().backward()
+
+
+def test_fit_with_the_gradient_term_lowers_both_losses():
+    """Teacher-student fit on the distance loss plus a gradient-matching term
+    (the gradient loss of Table I): 40 Adam steps through field_grad."""
+    torch = need_gpu()
+    g = lib()
+    n, H, L, B = 9, 128, 3, 8192
+    _, w_teacher = small_net(n, hidden=H, n_layers=L, seed=1)
+    _, w0 = small_net(n, hidden=H, n_layers=L, seed=2)
+    q, p = _batch(n, B, 13)
+    qd, pd = to_dev(torch, q), to_dev(torch, p)
+    f_t, dq_t = g.fit_value_grad((n, H, L), to_dev(torch, np.asarray(w_teacher, np.float32)), qd, pd)
+    wd = to_dev(torch, np.asarray(w0, np.float32)).requires_grad_(True)
+    opt = torch.optim.Adam([wd], lr=2e-3)
+    hist = []
+    for _ in range(40):
+        opt.zero_grad()
+        f, dq = g.field_grad(wd, qd, pd, (n, H, L))
+        l_d = ((f - f_t) ** 2).mean()
+        l_g = ((dq - dq_t) ** 2).sum(dim=1).mean()
+        (l_d + l_g).backward()
+        opt.step()
+        hist.append((float(l_d.detach()), float(l_g.detach())))
+    assert hist[-1][0] < 0.7 * hist[0][0] and hist[-1][1] < 0.7 * hist[0][1], (hist[0], hist[-1])
