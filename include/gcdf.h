@@ -271,20 +271,32 @@ GCDF_API int gcdf_jacobian_scatter(const float *grad, int n_waypoints, int n_dof
  * given by its flat weights in DEVICE memory (layout of gcdf_weight_count,
  * e.g. FP32 master weights being trained), evaluated per SAMPLE (q_b, p_b)
  * rather than over a waypoint x point grid, with the vector-Jacobian products
- * a training step needs.  Every product is a hand-written FP32 GEMM; the
- * reductions over the batch (weight and bias gradients) are summed in a fixed
- * order, so results are deterministic.  Temporaries: the activations and
- * s'(z) of every layer (2 L batch x hidden floats) and a 64-chunk partials
- * array, from cudaMallocAsync on the stream.
+ * a training step needs.  Every product is a hand-written GEMM (FP32 on CUDA
+ * cores, or BF16 operands with FP32 accumulation on tcgen05 tensor cores, by
+ * gcdf_fit_desc.precision); the reductions over the batch (weight and bias
+ * gradients) are summed in a fixed order, so results are deterministic.
+ * Temporaries: the activations and s'(z) of every layer (2 L batch x hidden
+ * floats), a 64-chunk partials array and, for BF16, two operand images of
+ * about batch x max(hidden, input width) BF16 values, from cudaMallocAsync on
+ * the stream.  A tensor-core wait that gives up (about a second) sets the
+ * status that gcdf_fit_device_status reads; the call itself cannot see it.
  * ------------------------------------------------------------------------- */
 
 typedef struct gcdf_fit_desc {
   int n_dof;            /* n, 3 .. 12 */
   int hidden;           /* H, 1 .. 4096 */
   int n_hidden_layers;  /* L, 1 .. 16 */
+  int precision;        /* GCDF_FP32 (SIMT FP32 GEMMs) or GCDF_BF16 (the matrix products on
+                           tcgen05 tensor cores with BF16 operands and FP32 accumulation; the
+                           weights, activations and element-wise steps stay FP32) */
 } gcdf_fit_desc;
 
 /* f (batch,) DEVICE out: f(q_b, p_b) for q (batch, n) and p (batch, 3) DEVICE. */
+/* Synchronises the current device, then *status = the fit kernels' device
+ * status word since the last call (0: every tensor-core wait completed; bit 1:
+ * one gave up and its product is incomplete) and clears it.  Errors: ECUDA. */
+GCDF_API int gcdf_fit_device_status(int *status);
+
 GCDF_API int gcdf_fit_forward(const gcdf_fit_desc *desc, const float *weights, const float *q, const float *p,
                               int batch, float *f, gcdf_stream_t stream);
 

@@ -317,21 +317,30 @@ class Server:
 
 
 # ---------------------------------------------------------------------------
-# Differentiable fit (gcdf_fit_forward / gcdf_fit_vjp)
+# Differentiable fit (gcdf_fit_forward / gcdf_fit_vjp / gcdf_fit_value_grad /
+# gcdf_fit_vjp2); precision "fp32" (SIMT GEMMs) or "bf16" (tensor-core GEMMs,
+# BF16 operands, FP32 accumulation and master weights)
 # ---------------------------------------------------------------------------
 
-def fit_forward(shape, weights: torch.Tensor, q: torch.Tensor, p: torch.Tensor, stream=None) -> torch.Tensor:
+def _fit_desc(shape, precision):
+    if precision not in ("fp32", "bf16"):
+        raise ValueError(f"fit precision {precision!r}: 'fp32' or 'bf16'")
+    return _lib.FitDesc(*[int(x) for x in shape], _PREC[precision])
+
+
+def fit_forward(shape, weights: torch.Tensor, q: torch.Tensor, p: torch.Tensor, stream=None,
+                precision="fp32") -> torch.Tensor:
     """gcdf_fit_forward: f (B,) per sample; shape = (n_dof, hidden, n_layers)."""
-    d = _lib.FitDesc(*[int(x) for x in shape])
+    d = _fit_desc(shape, precision)
     f = torch.empty(q.shape[0], device=q.device, dtype=torch.float32)
     _lib.check(_lib.load().gcdf_fit_forward(ctypes.byref(d), _ptr(weights, name="weights"), _ptr(q, name="q"),
                                             _ptr(p, name="p"), int(q.shape[0]), _ptr(f, name="f"), _stream(stream)))
     return f
 
 
-def fit_vjp(shape, weights, q, p, g_f, want_dq=True, stream=None):
+def fit_vjp(shape, weights, q, p, g_f, want_dq=True, stream=None, precision="fp32"):
     """gcdf_fit_vjp: (dweights, dq or None) for the upstream gradient g_f (B,)."""
-    d = _lib.FitDesc(*[int(x) for x in shape])
+    d = _fit_desc(shape, precision)
     dw = torch.empty_like(weights)
     dq = torch.empty_like(q) if want_dq else None
     _lib.check(_lib.load().gcdf_fit_vjp(ctypes.byref(d), _ptr(weights, name="weights"), _ptr(q, name="q"),
@@ -341,32 +350,9 @@ def fit_vjp(shape, weights, q, p, g_f, want_dq=True, stream=None):
     return dw, dq
 
 
-class FieldFunction(torch.autograd.Function):
-    """f(q_b, p_b; weights) as an autograd.Function: the forward and both
-    vector-Jacobian products (weights and q) run in libgcdf's kernels."""
-
-    @staticmethod
-    def forward(ctx, weights, q, p, shape):
-        ctx.save_for_backward(weights, q, p)
-        ctx.shape = shape
-        return fit_forward(shape, weights.detach(), q.detach(), p)
-
-    @staticmethod
-    def backward(ctx, g_f):
-        weights, q, p = ctx.saved_tensors
-        dw, dq = fit_vjp(ctx.shape, weights.detach(), q.detach(), p, g_f.detach().float(),
-                         want_dq=ctx.needs_input_grad[1])
-        return dw, dq, None, None
-
-
-def field(weights: torch.Tensor, q: torch.Tensor, p: torch.Tensor, shape) -> torch.Tensor:
-    """Differentiable per-sample field values (weights: flat FP32 CUDA tensor)."""
-    return FieldFunction.apply(weights, q, p, tuple(shape))
-
-
-def fit_value_grad(shape, weights, q, p, stream=None):
+def fit_value_grad(shape, weights, q, p, stream=None, precision="fp32"):
     """gcdf_fit_value_grad: (f (B,), grad_q f (B, n)) per sample."""
-    d = _lib.FitDesc(*[int(x) for x in shape])
+    d = _fit_desc(shape, precision)
     f = torch.empty(q.shape[0], device=q.device, dtype=torch.float32)
     dq = torch.empty_like(q)
     _lib.check(_lib.load().gcdf_fit_value_grad(ctypes.byref(d), _ptr(weights, name="weights"), _ptr(q, name="q"),
@@ -375,15 +361,46 @@ def fit_value_grad(shape, weights, q, p, stream=None):
     return f, dq
 
 
-def fit_vjp2(shape, weights, q, p, g_f, G_q, stream=None):
+def fit_vjp2(shape, weights, q, p, g_f, G_q, stream=None, precision="fp32"):
     """gcdf_fit_vjp2: dweights of sum_b g_b f_b + G_b . grad_q f_b."""
-    d = _lib.FitDesc(*[int(x) for x in shape])
+    d = _fit_desc(shape, precision)
     dw = torch.empty_like(weights)
     _lib.check(_lib.load().gcdf_fit_vjp2(ctypes.byref(d), _ptr(weights, name="weights"), _ptr(q, name="q"),
                                          _ptr(p, name="p"), int(q.shape[0]), _ptr(g_f.contiguous(), name="g_f"),
                                          _ptr(G_q.contiguous(), name="G_q"), _ptr(dw, name="dweights"),
                                          _stream(stream)))
     return dw
+
+
+def fit_device_status() -> int:
+    """gcdf_fit_device_status: synchronise; the fit kernels' status word since
+    the last call (0 = every tensor-core wait completed), then clear it."""
+    v = ctypes.c_int(0)
+    _lib.check(_lib.load().gcdf_fit_device_status(ctypes.byref(v)))
+    return int(v.value)
+
+
+class FieldFunction(torch.autograd.Function):
+    """f(q_b, p_b; weights) as an autograd.Function: the forward and both
+    vector-Jacobian products (weights and q) run in libgcdf's kernels."""
+
+    @staticmethod
+    def forward(ctx, weights, q, p, shape, precision):
+        ctx.save_for_backward(weights, q, p)
+        ctx.shape, ctx.precision = shape, precision
+        return fit_forward(shape, weights.detach(), q.detach(), p, precision=precision)
+
+    @staticmethod
+    def backward(ctx, g_f):
+        weights, q, p = ctx.saved_tensors
+        dw, dq = fit_vjp(ctx.shape, weights.detach(), q.detach(), p, g_f.detach().float(),
+                         want_dq=ctx.needs_input_grad[1], precision=ctx.precision)
+        return dw, dq, None, None, None
+
+
+def field(weights: torch.Tensor, q: torch.Tensor, p: torch.Tensor, shape, precision="fp32") -> torch.Tensor:
+    """Differentiable per-sample field values (weights: flat FP32 CUDA tensor)."""
+    return FieldFunction.apply(weights, q, p, tuple(shape), precision)
 
 
 class FieldGradFunction(torch.autograd.Function):
@@ -393,10 +410,10 @@ class FieldGradFunction(torch.autograd.Function):
     only."""
 
     @staticmethod
-    def forward(ctx, weights, q, p, shape):
+    def forward(ctx, weights, q, p, shape, precision):
         ctx.save_for_backward(weights, q, p)
-        ctx.shape = shape
-        return fit_value_grad(shape, weights.detach(), q.detach(), p)
+        ctx.shape, ctx.precision = shape, precision
+        return fit_value_grad(shape, weights.detach(), q.detach(), p, precision=precision)
 
     @staticmethod
     def backward(ctx, g_f, G_q):
@@ -407,10 +424,11 @@ class FieldGradFunction(torch.autograd.Function):
             g_f = torch.zeros(q.shape[0], device=q.device, dtype=torch.float32)
         if G_q is None:
             G_q = torch.zeros_like(q)
-        dw = fit_vjp2(ctx.shape, weights.detach(), q.detach(), p, g_f.detach().float(), G_q.detach().float())
-        return dw, None, None, None
+        dw = fit_vjp2(ctx.shape, weights.detach(), q.detach(), p, g_f.detach().float(), G_q.detach().float(),
+                      precision=ctx.precision)
+        return dw, None, None, None, None
 
 
-def field_grad(weights: torch.Tensor, q: torch.Tensor, p: torch.Tensor, shape):
+def field_grad(weights: torch.Tensor, q: torch.Tensor, p: torch.Tensor, shape, precision="fp32"):
     """Differentiable (f, grad_q f) per sample, with respect to the weights."""
-    return FieldGradFunction.apply(weights, q, p, tuple(shape))
+    return FieldGradFunction.apply(weights, q, p, tuple(shape), precision)

@@ -27,7 +27,7 @@ class NetDesc(ctypes.Structure):
 
 
 class FitDesc(ctypes.Structure):
-    _fields_ = [("n_dof", _i), ("hidden", _i), ("n_hidden_layers", _i)]
+    _fields_ = [("n_dof", _i), ("hidden", _i), ("n_hidden_layers", _i), ("precision", _i)]
 
 
 class PlanParams(ctypes.Structure):
@@ -69,6 +69,7 @@ SIGNATURES = {
     "gcdf_partition_offsets": (_i, [_vp, _i, _vp, _i, _f, _vp, _vp]),
     "gcdf_partition_indices": (_i, [_vp, _i, _vp, _i, _f, _vp, _vp, _vp]),
     "gcdf_jacobian_scatter": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp, _vp, _vp]),
+    "gcdf_fit_device_status": (_i, [ctypes.POINTER(_i)]),
     "gcdf_fit_forward": (_i, [ctypes.POINTER(FitDesc), _vp, _vp, _vp, _i, _vp, _vp]),
     "gcdf_fit_vjp": (_i, [ctypes.POINTER(FitDesc), _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp]),
     "gcdf_fit_value_grad": (_i, [ctypes.POINTER(FitDesc), _vp, _vp, _vp, _i, _vp, _vp, _vp]),

@@ -22,14 +22,19 @@
 //   dW_l += eps_l^T h_{l-1};  db_l = sum_b eps_l;  dw_o += h_L^T g;  db_o = sum_b g
 //
 // Every matrix product is one strided FP32 GEMM kernel (128 x 128 tiles, 8 x 8
-// outputs per thread); the vector products (the output f, the bias and
+// outputs per thread) or, with BF16 precision, the tcgen05 GEMM of fit_tc.cu on
+// BF16 images of its operands (FP32 accumulation; the activations, s'(z) and
+// every element-wise step stay FP32); the vector products (the output f, the bias and
 // output-weight gradients) are a warp-per-row dot and a column reduction.
 // Whatever reduces over the batch (weight and bias gradients) splits it into
 // chunks whose partials are summed in a fixed order: deterministic gradients.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cstring>
 #include <vector>
 
+#include "fit_tc.cuh"
 #include "gcdf_internal.cuh"
 
 namespace gcdf {
@@ -324,6 +329,109 @@ cudaError_t colsum(const float* X, int rows, int C, const float* w, float* out, 
   return cudaGetLastError();
 }
 
+// Y (rows x cols, row stride ldy) = BF16 rounding of X (rows x cols, row stride ldx)
+__global__ void cast_bf16_kernel(const float* __restrict__ X, long long rows, int cols, long long ldx,
+                                 __nv_bfloat16* __restrict__ Y, long long ldy) {
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x)
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) Y[r * ldy + c] = __float2bfloat16_rn(X[r * ldx + c]);
+}
+
+// Y[c, r] = BF16 rounding of X[r, c] for X rows x cols (row stride ldx), Y cols x
+// rows (row stride ldy): 32 x 32 tiles through shared memory, block 32 x 8
+// (blockIdx.x: row tile, blockIdx.y: column tile).
+__global__ void transpose_bf16_kernel(const float* __restrict__ X, long long rows, int cols, long long ldx,
+                                      __nv_bfloat16* __restrict__ Y, long long ldy) {
+  __shared__ float t[32][33];
+  const long long r0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const long long r = r0 + i;
+    const int c = c0 + threadIdx.x;
+    t[i][threadIdx.x] = (r < rows && c < cols) ? X[r * ldx + c] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i;
+    const long long r = r0 + threadIdx.x;
+    if (c < cols && r < rows) Y[(long long)c * ldy + r] = __float2bfloat16_rn(t[threadIdx.x][i]);
+  }
+}
+
+long long pad8(long long x) { return (x + 7) / 8 * 8; }
+
+// The products of one call: FP32 SIMT GEMMs, or the BF16 tensor-core GEMM on
+// K-major BF16 images of both operands (a strided operand whose K index is the
+// contiguous one is rounded in place order, the other one transposed).
+struct Ctx {
+  cudaStream_t s;
+  float* partials = nullptr;
+  size_t pfl = 0;
+  bool bf16 = false;
+  __nv_bfloat16 *sa = nullptr, *sb = nullptr;
+  size_t cap = 0;  // elements of sa and of sb
+  int* err = nullptr;
+
+  // the operand images for products among batch B and widths up to maxK
+  cudaError_t reserve(Ws& ws, long long B, long long maxK) {
+    if (!bf16) return cudaSuccess;
+    cap = (size_t)std::max({maxK * pad8(B), B * pad8(maxK), maxK * pad8(maxK)});
+    cudaError_t e;
+    if ((e = ws.get(&sa, cap)) || (e = ws.get(&sb, cap))) return e;
+    err = fit_status_word();
+    return err ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
+
+  // K-major BF16 image (rows x K, row stride ld) of X(r, k) = X[r srow + k sk]
+  cudaError_t image(const float* X, long long srow, long long sk, int rows, int K, __nv_bfloat16* Y, long long ld) {
+    if (sk == 1) {
+      cast_bf16_kernel<<<(int)std::min<long long>(rows, 152 * 16), 128, 0, s>>>(X, rows, K, srow, Y, ld);
+    } else if (srow == 1) {  // X is K x rows with row stride sk
+      dim3 grid((unsigned)((K + 31) / 32), (unsigned)((rows + 31) / 32));
+      transpose_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(X, K, rows, sk, Y, ld);
+    } else {
+      return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+
+  // C (M x N, ldc) = (or +=) A(m, k) B(k, n) summed over K; `split`: the
+  // product may split K over the partials array
+  cudaError_t mm(const float* A, long long sam, long long sak, const float* B, long long sbk, long long sbn, float* C,
+                 int ldc, int M, int N, int K, bool split, bool accumulate = false) {
+    if (!bf16) return gemm(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, split ? partials : nullptr, split ? pfl : 0, s,
+                           accumulate);
+    if (M == 0 || N == 0) return cudaSuccess;
+    const long long ld = pad8(K);
+    if ((size_t)M * ld > cap || (size_t)N * ld > cap) return cudaErrorInvalidValue;
+    cudaError_t e;
+    // A(m, k) = A[m sam + k sak]; B as an N x K operand: B(k, n) = B[n sbn + k sbk]
+    if ((e = image(A, sam, sak, M, K, sa, ld)) || (e = image(B, sbn, sbk, N, K, sb, ld))) return e;
+    const int kb = tc_gemm_kblock();
+    const long long kblocks = (K + kb - 1) / kb;
+    const long long tiles = (long long)((M + tc_gemm_tile_m() - 1) / tc_gemm_tile_m()) *
+                            ((N + tc_gemm_tile_n() - 1) / tc_gemm_tile_n());
+    long long splits = 1;
+    if (split && partials && tiles < 152 && kblocks >= 16) {
+      splits = std::min<long long>((152 + tiles - 1) / tiles, kblocks / 8);
+      while (splits > 1 && (size_t)splits * M * N > pfl) --splits;
+    }
+    const long long per = (kblocks + splits - 1) / splits;
+    splits = (kblocks + per - 1) / per;
+    bool enc_fail = false;
+    if (splits == 1) {
+      e = tc_gemm_bf16(sa, ld, sb, ld, M, N, K, C, ldc, 0, 1, (int)per, accumulate, err, s, &enc_fail);
+    } else {
+      e = tc_gemm_bf16(sa, ld, sb, ld, M, N, K, partials, N, (long long)M * N, (int)splits, (int)per, false, err, s,
+                       &enc_fail);
+      if (e == cudaSuccess && !enc_fail)
+        sum_partials_kernel<<<grid1((long long)M * N), 256, 0, s>>>(partials, (int)splits, M, N, N, C, ldc,
+                                                                    accumulate ? 1 : 0);
+    }
+    if (enc_fail) return cudaErrorInvalidValue;
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
+};
+
 bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 struct Shape {
@@ -335,6 +443,7 @@ struct Shape {
     return (size_t)H * d_in + H + (size_t)(l - 2) * ((size_t)H * H + H);
   }
   int fan_in(int l) const { return l == 1 ? d_in : H; }
+  bool bf16;
 };
 
 int check(const gcdf_fit_desc* d, const float* w, const float* q, const float* p, int B, Shape& sh) {
@@ -343,6 +452,8 @@ int check(const gcdf_fit_desc* d, const float* w, const float* q, const float* p
       d->n_hidden_layers > 16)
     return set_error(GCDF_EINVAL, "bad shape (n_dof %d, hidden %d, layers %d)", d->n_dof, d->hidden,
                      d->n_hidden_layers);
+  if (d->precision != GCDF_FP32 && d->precision != GCDF_BF16)
+    return set_error(GCDF_EINVAL, "fit precision %d is neither GCDF_FP32 nor GCDF_BF16", d->precision);
   if (B < 0) return set_error(GCDF_EINVAL, "batch %d < 0", B);
   if (B > 0 && (!w || !q || !p || !al16(w) || !al16(q) || !al16(p)))
     return set_error(GCDF_EINVAL, "weights, q or p NULL or not 16-byte aligned");
@@ -352,20 +463,22 @@ int check(const gcdf_fit_desc* d, const float* w, const float* q, const float* p
   sh.d_in = 3 + 2 + 2 * (sh.n - 2);
   sh.off_out = sh.off(sh.L + 1);
   sh.total = sh.off_out + sh.H + 1;
+  sh.bf16 = d->precision == GCDF_BF16;
   return GCDF_OK;
 }
 
 // Forward pass storing h_l (Hs[l], l = 0 .. L, Hs[0] = v), s'(z_l) (Ss[l - 1])
 // and, when S2s is given, s''(z_l) (S2s[l - 1]).
 int forward(const Shape& sh, const float* w, const float* q, const float* p, int B, float** Hs, float** Ss, float* f,
-            cudaStream_t s, float** S2s = nullptr) {
+            Ctx& cx, float** S2s = nullptr) {
+  const cudaStream_t s = cx.s;
   cudaError_t e;
   encode_kernel<<<grid1(B), 256, 0, s>>>(q, p, B, sh.n, sh.d_in, Hs[0]);
   for (int l = 1; l <= sh.L; ++l) {
     const int K = sh.fan_in(l);
     const float* W = w + sh.off(l);
     // Z (B x H) = H_{l-1} (B x K) W^T
-    if ((e = gemm(Hs[l - 1], K, 1, W, 1, K, Hs[l], sh.H, B, sh.H, K, nullptr, 0, s)))
+    if ((e = cx.mm(Hs[l - 1], K, 1, W, 1, K, Hs[l], sh.H, B, sh.H, K, false)))
       return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
     bias_silu_kernel<<<grid1((long long)B * sh.H), 256, 0, s>>>(Hs[l], W + (size_t)sh.H * K, B, sh.H, Ss[l - 1],
                                                                 S2s ? S2s[l - 1] : nullptr);
@@ -383,17 +496,28 @@ int forward(const Shape& sh, const float* w, const float* q, const float* p, int
 // Reverse sweep of the field's own gradient: delta_l = a_l * s'(z_l) into
 // D[l - 1], a_L = w_o, a_{l-1} = delta_l W_l into A[l - 2] (A[l - 2] may be
 // D[l - 2]: then only delta survives), for l = L .. 1.
-int reverse_sweep(const Shape& sh, const float* w, int B, float** Ss, float** D, float** A, cudaStream_t s) {
+int reverse_sweep(const Shape& sh, const float* w, int B, float** Ss, float** D, float** A, Ctx& cx) {
+  const cudaStream_t s = cx.s;
   const int H = sh.H;
   const long long n = (long long)B * H;
   seed_kernel<<<grid1(n), 256, 0, s>>>(nullptr, w + sh.off_out, Ss[sh.L - 1], B, H, D[sh.L - 1]);
   for (int l = sh.L; l >= 2; --l) {
-    cudaError_t e = gemm(D[l - 1], H, 1, w + sh.off(l), H, 1, A[l - 2], H, B, H, H, nullptr, 0, s);
+    cudaError_t e = cx.mm(D[l - 1], H, 1, w + sh.off(l), H, 1, A[l - 2], H, B, H, H, false);
     if (e) return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
     mul2_kernel<<<grid1(n), 256, 0, s>>>(D[l - 2], A[l - 2], Ss[l - 2], n);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(GCDF_ECUDA, "reverse sweep launch: %s", cudaGetErrorString(e));
+  return GCDF_OK;
+}
+
+int make_ctx(Ctx& cx, Ws& ws, const Shape& sh, int B, cudaStream_t s, float* partials, size_t pfl) {
+  cx.s = s;
+  cx.partials = partials;
+  cx.pfl = pfl;
+  cx.bf16 = sh.bf16;
+  cudaError_t e = cx.reserve(ws, B, std::max(sh.H, sh.d_in));
+  if (e != cudaSuccess) return set_error(GCDF_ENOMEM, "fit operand images: %s", cudaGetErrorString(e));
   return GCDF_OK;
 }
 
@@ -403,6 +527,20 @@ int reverse_sweep(const Shape& sh, const float* w, int B, float** Ss, float** D,
 using namespace gcdf;
 
 extern "C" {
+
+int gcdf_fit_device_status(int* status) {
+  if (!status) return set_error(GCDF_EINVAL, "status is NULL");
+  int* w = fit_status_word();
+  if (!w) return set_error(GCDF_ECUDA, "fit status word unavailable");
+  cudaError_t e;
+  int v = 0;
+  if ((e = cudaDeviceSynchronize()) || (e = cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemset(w, 0, sizeof(int))))
+    return set_error(GCDF_ECUDA, "fit status: %s", cudaGetErrorString(e));
+  *status = v;
+  clear_error();
+  return GCDF_OK;
+}
 
 int gcdf_fit_forward(const gcdf_fit_desc* desc, const float* weights, const float* q, const float* p, int batch,
                      float* f, gcdf_stream_t stream) {
@@ -426,7 +564,9 @@ int gcdf_fit_forward(const gcdf_fit_desc* desc, const float* weights, const floa
     Hs[l] = (l & 1) ? h0 : h1;
     Ss[l - 1] = sc;
   }
-  rc = forward(sh, weights, q, p, batch, Hs, Ss, f, s);
+  Ctx cx;
+  if ((rc = make_ctx(cx, ws, sh, batch, s, nullptr, 0))) return rc;
+  rc = forward(sh, weights, q, p, batch, Hs, Ss, f, cx);
   if (rc) return rc;
   clear_error();
   return GCDF_OK;
@@ -462,7 +602,9 @@ int gcdf_fit_vjp(const gcdf_fit_desc* desc, const float* weights, const float* q
 
       (e = ws.get(&partials, pfl)))
     return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
-  rc = forward(sh, weights, q, p, batch, Hs, Ss, nullptr, s);
+  Ctx cx;
+  if ((rc = make_ctx(cx, ws, sh, batch, s, partials, pfl))) return rc;
+  rc = forward(sh, weights, q, p, batch, Hs, Ss, nullptr, cx);
   if (rc) return rc;
 
   const int H = sh.H;
@@ -479,13 +621,13 @@ int gcdf_fit_vjp(const gcdf_fit_desc* desc, const float* weights, const float* q
     const float* W = weights + sh.off(l);
     float* dW = dweights + sh.off(l);
     // dW_l (H x K) = delta^T (H x B) H_{l-1} (B x K);  db_l = delta^T 1
-    if ((e = gemm(D, 1, H, Hs[l - 1], K, 1, dW, K, H, K, batch, partials, pfl, s)) ||
+    if ((e = cx.mm(D, 1, H, Hs[l - 1], K, 1, dW, K, H, K, batch, true)) ||
         (e = colsum(D, batch, H, nullptr, dW + (size_t)H * K, partials, pfl, s)))
       return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
     if (l > 1 || dq) {
       // back (B x K) = delta (B x H) W_l (H x K)
       float* back = (D == D1) ? D0 : D1;  // never the buffer it reads
-      if ((e = gemm(D, H, 1, W, K, 1, back, K, batch, K, H, nullptr, 0, s)))
+      if ((e = cx.mm(D, H, 1, W, K, 1, back, K, batch, K, H, false)))
         return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
       if (l > 1) {
         mul_kernel<<<grid1((long long)batch * K), 256, 0, s>>>(back, Ss[l - 2], (long long)batch * K);
@@ -521,13 +663,15 @@ int gcdf_fit_value_grad(const gcdf_fit_desc* desc, const float* weights, const f
   for (int l = 1; l <= sh.L; ++l)
     if ((e = ws.get(&Hs[l], (size_t)batch * sh.H)) || (e = ws.get(&Ss[l - 1], (size_t)batch * sh.H)))
       return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
-  rc = forward(sh, weights, q, p, batch, Hs, Ss, f, s);
+  Ctx cx;
+  if ((rc = make_ctx(cx, ws, sh, batch, s, nullptr, 0))) return rc;
+  rc = forward(sh, weights, q, p, batch, Hs, Ss, f, cx);
   if (rc) return rc;
   // delta ping-pongs between two buffers, a_{l-1} computed in place of delta_{l-1}
   for (int l = 1; l <= sh.L; ++l) D[l - 1] = ((sh.L - l) & 1) ? d1 : d0;
-  if ((rc = reverse_sweep(sh, weights, batch, Ss, D, D, s))) return rc;
+  if ((rc = reverse_sweep(sh, weights, batch, Ss, D, D, cx))) return rc;
   // dv (B x d_in) = delta_1 W_1
-  if ((e = gemm(D[0], sh.H, 1, weights, sh.d_in, 1, dv, sh.d_in, batch, sh.d_in, sh.H, nullptr, 0, s)))
+  if ((e = cx.mm(D[0], sh.H, 1, weights, sh.d_in, 1, dv, sh.d_in, batch, sh.d_in, sh.H, false)))
     return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
   dq_kernel<<<grid1(batch), 256, 0, s>>>(q, dv, batch, sh.n, sh.d_in, dq);
   e = cudaGetLastError();
@@ -565,15 +709,17 @@ int gcdf_fit_vjp2(const gcdf_fit_desc* desc, const float* weights, const float* 
     if ((e = ws.get(&Hs[l], (size_t)n)) || (e = ws.get(&S1[l - 1], (size_t)n)) || (e = ws.get(&S2[l - 1], (size_t)n)) ||
         (e = ws.get(&D[l - 1], (size_t)n)) || (e = ws.get(&AE[l - 1], (size_t)n)))
       return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
-  if ((rc = forward(sh, weights, q, p, batch, Hs, S1, nullptr, s, S2))) return rc;
+  Ctx cx;
+  if ((rc = make_ctx(cx, ws, sh, batch, s, partials, pfl))) return rc;
+  if ((rc = forward(sh, weights, q, p, batch, Hs, S1, nullptr, cx, S2))) return rc;
   // a_l (l < L) into AE[l - 1]; a_L = w_o is never stored
-  if ((rc = reverse_sweep(sh, weights, batch, S1, D, AE, s))) return rc;
+  if ((rc = reverse_sweep(sh, weights, batch, S1, D, AE, cx))) return rc;
   const float* wo = weights + sh.off_out;
   float* dwo = dweights + sh.off_out;
   // first-derivative terms (written): u = C^T G; dW_1 = delta_1^T u; r_1 = u W_1^T
   dq_adjoint_kernel<<<grid1(batch), 256, 0, s>>>(q, G_q, batch, sh.n, sh.d_in, U);
-  if ((e = gemm(D[0], 1, H, U, sh.d_in, 1, dweights, sh.d_in, H, sh.d_in, batch, partials, pfl, s)) ||
-      (e = gemm(U, sh.d_in, 1, weights, 1, sh.d_in, R0, H, batch, H, sh.d_in, nullptr, 0, s)))
+  if ((e = cx.mm(D[0], 1, H, U, sh.d_in, 1, dweights, sh.d_in, H, sh.d_in, batch, true)) ||
+      (e = cx.mm(U, sh.d_in, 1, weights, 1, sh.d_in, R0, H, batch, H, sh.d_in, false)))
     return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
   float *r = R0, *rs = R1;
   for (int l = 1; l <= L; ++l) {
@@ -583,8 +729,8 @@ int gcdf_fit_vjp2(const gcdf_fit_desc* desc, const float* weights, const float* 
     if (l < L) {
       // dW_{l+1} = delta_{l+1}^T rs;  r_{l+1} = rs W_{l+1}^T
       const float* W = weights + sh.off(l + 1);
-      if ((e = gemm(D[l], 1, H, rs, H, 1, dweights + sh.off(l + 1), H, H, H, batch, partials, pfl, s)) ||
-          (e = gemm(rs, H, 1, W, 1, H, r, H, batch, H, H, nullptr, 0, s)))
+      if ((e = cx.mm(D[l], 1, H, rs, H, 1, dweights + sh.off(l + 1), H, H, H, batch, true)) ||
+          (e = cx.mm(rs, H, 1, W, 1, H, r, H, batch, H, H, false)))
         return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
     } else if ((e = colsum(rs, batch, H, nullptr, dwo, partials, pfl, s))) {  // dw_o = sum_b r_L * s'(z_L)
       return set_error(GCDF_ECUDA, "colsum: %s", cudaGetErrorString(e));
@@ -599,13 +745,13 @@ int gcdf_fit_vjp2(const gcdf_fit_desc* desc, const float* weights, const float* 
   for (int l = L; l >= 1; --l) {
     const int K = sh.fan_in(l);
     float* dW = dweights + sh.off(l);
-    if ((e = gemm(eps, 1, H, Hs[l - 1], K, 1, dW, K, H, K, batch, partials, pfl, s, true)) ||
+    if ((e = cx.mm(eps, 1, H, Hs[l - 1], K, 1, dW, K, H, K, batch, true, true)) ||
         (e = colsum(eps, batch, H, nullptr, dW + (size_t)H * K, partials, pfl, s)))
       return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
     if (l > 1) {
       // eps_{l-1} = e_{l-1} + (eps_l W_l) * s'(z_{l-1})
       float* back = (eps == R0) ? R1 : R0;
-      if ((e = gemm(eps, H, 1, weights + sh.off(l), H, 1, back, H, batch, H, H, nullptr, 0, s)))
+      if ((e = cx.mm(eps, H, 1, weights + sh.off(l), H, 1, back, H, batch, H, H, false)))
         return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
       addmul_kernel<<<grid1(n), 256, 0, s>>>(back, S1[l - 2], AE[l - 2], n);
       eps = back;

@@ -173,3 +173,109 @@ def lowp_eval_fp8(n_dof, H, L, weights, q_rows, p_rows):
     dq[:, :2] = denc[:, :2]
     dq[:, 2:] = np.cos(ang) * denc[:, 2::2] - np.sin(ang) * denc[:, 3::2]
     return f, dq
+
+
+# ---------------------------------------------------------------------------
+# Differentiable fit with BF16 GEMM operands (gcdf_fit_* with precision BF16):
+# every matrix product rounds both operands to BF16 and accumulates exactly;
+# the encoding, SiLU, s', s'', the element-wise products, the vector products
+# (f, the bias and output-weight gradients) stay at high precision.  With
+# rnd = identity this is the plain first- and second-order backpropagation.
+# ---------------------------------------------------------------------------
+
+def _fit_input(q, p):
+    q = np.asarray(q, np.float64)
+    p = np.asarray(p, np.float64)
+    a = q[:, 2:]
+    sc = np.empty((q.shape[0], 2 * a.shape[1]))
+    sc[:, 0::2] = np.sin(a)
+    sc[:, 1::2] = np.cos(a)
+    return np.concatenate([p, q[:, :2], sc], axis=1).astype(np.float32).astype(np.float64)
+
+
+def _fit_silu(z):
+    sg = 1.0 / (1.0 + np.exp(-z))
+    return z * sg, sg * (1.0 + z * (1.0 - sg)), sg * (1.0 - sg) * (2.0 + z * (1.0 - 2.0 * sg))
+
+
+def _mm(a, b, rnd):
+    return rnd(a) @ rnd(b)
+
+
+def fit_model(n_dof, H, L, weights, q, p, g_f, G_q=None, rnd=round_bf16):
+    """(f, dweights, dq) of the first-order products for g_f, or, with G_q,
+    (f, grad_q f, dweights of sum g f + G . grad_q f)."""
+    lay = _layers(n_dof, H, L, weights)
+    Ws = [W for W, _ in lay[:-1]]
+    bs = [b for _, b in lay[:-1]]
+    wo, bo = lay[-1][0][0], lay[-1][1][0]
+    q = np.asarray(q, np.float64)
+    B = q.shape[0]
+    g = np.asarray(g_f, np.float64)
+    hs, s1, s2 = [_fit_input(q, p)], [], []
+    for W, b in zip(Ws, bs):
+        h, d1, d2 = _fit_silu(_mm(hs[-1], W.T, rnd) + b)
+        hs.append(h)
+        s1.append(d1)
+        s2.append(d2)
+    f = hs[-1] @ wo + bo
+    grads = []  # flat blocks in the layout's order
+    sizes = [(W.shape[0] * W.shape[1] + W.shape[0]) for W in Ws] + [H + 1]
+    dw = np.zeros(sum(sizes))
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(int)
+
+    def chain(dv):
+        dq = np.empty((B, n_dof))
+        dq[:, 0], dq[:, 1] = dv[:, 3], dv[:, 4]
+        a = q[:, 2:].astype(np.float32).astype(np.float64)
+        dq[:, 2:] = np.cos(a) * dv[:, 5::2] - np.sin(a) * dv[:, 6::2]
+        return dq
+
+    if G_q is None:
+        dw[offs[L]: offs[L] + H] = g @ hs[L]
+        dw[offs[L] + H] = g.sum()
+        d = g[:, None] * wo[None, :] * s1[L - 1]
+        for l in range(L - 1, -1, -1):
+            o, i = Ws[l].shape
+            dw[offs[l]: offs[l] + o * i] = _mm(d.T, hs[l], rnd).reshape(-1)
+            dw[offs[l] + o * i: offs[l] + o * i + o] = d.sum(axis=0)
+            back = _mm(d, Ws[l], rnd)
+            if l > 0:
+                d = back * s1[l - 1]
+        return f, dw, chain(back)
+    G = np.asarray(G_q, np.float64)
+    # the field's own reverse sweep: a_l, delta_l
+    A = [None] * L
+    D = [None] * L
+    D[L - 1] = wo[None, :] * s1[L - 1]
+    for l in range(L - 1, 0, -1):
+        A[l - 1] = _mm(D[l], Ws[l], rnd)
+        D[l - 1] = A[l - 1] * s1[l - 1]
+    dq = chain(_mm(D[0], Ws[0], rnd))
+    u = np.zeros_like(hs[0])
+    a = q[:, 2:].astype(np.float32).astype(np.float64)
+    u[:, 3], u[:, 4] = G[:, 0], G[:, 1]
+    u[:, 5::2] = np.cos(a) * G[:, 2:]
+    u[:, 6::2] = -np.sin(a) * G[:, 2:]
+    o0, i0 = Ws[0].shape
+    dw[offs[0]: offs[0] + o0 * i0] = _mm(D[0].T, u, rnd).reshape(-1)
+    r = _mm(u, Ws[0].T, rnd)
+    E = [None] * L
+    for l in range(L):
+        E[l] = r * (A[l] if l < L - 1 else wo[None, :]) * s2[l]
+        rs = r * s1[l]
+        if l + 1 < L:
+            dw[offs[l + 1]: offs[l + 1] + H * H] = _mm(D[l + 1].T, rs, rnd).reshape(-1)
+            r = _mm(rs, Ws[l + 1].T, rnd)
+        else:
+            dw[offs[L]: offs[L] + H] = rs.sum(axis=0)
+    dw[offs[L]: offs[L] + H] += g @ hs[L]
+    dw[offs[L] + H] = g.sum()
+    eps = E[L - 1] + g[:, None] * wo[None, :] * s1[L - 1]
+    for l in range(L - 1, -1, -1):
+        o, i = Ws[l].shape
+        dw[offs[l]: offs[l] + o * i] += _mm(eps.T, hs[l], rnd).reshape(-1)
+        dw[offs[l] + o * i: offs[l] + o * i + o] = eps.sum(axis=0)
+        if l > 0:
+            eps = E[l - 1] + _mm(eps, Ws[l], rnd) * s1[l - 1]
+    return f, dq, dw

@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -46,3 +48,21 @@ def test_weight_count_and_argument_errors_without_gpu():
     assert "n_dof" in g.last_error()
     rc = lib.gcdf_query(None, None, 1, None, 1, None, None, 0, None, None, None, None)
     assert rc == g._lib.GCDF_EINVAL
+
+
+def test_fit_argument_errors_without_gpu():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2601_18548_gb300 as g
+    lib = g._lib.load()
+    # precision other than FP32 / BF16, bad shapes and a negative batch are
+    # rejected before any CUDA call
+    for desc in ((9, 256, 4, g._lib.GCDF_FP8), (9, 256, 4, 7), (2, 256, 4, 0), (9, 0, 4, 1), (9, 256, 17, 1)):
+        d = g._lib.FitDesc(*desc)
+        assert lib.gcdf_fit_forward(ctypes.byref(d), None, None, None, 0, None, None) == g._lib.GCDF_EINVAL
+        assert lib.gcdf_fit_vjp2(ctypes.byref(d), None, None, None, 0, None, None, None, None) == g._lib.GCDF_EINVAL
+    d = g._lib.FitDesc(9, 256, 4, g._lib.GCDF_BF16)
+    assert lib.gcdf_fit_value_grad(ctypes.byref(d), None, None, None, -1, None, None, None) == g._lib.GCDF_EINVAL
+    assert lib.gcdf_fit_device_status(None) == g._lib.GCDF_EINVAL
+    with pytest.raises(ValueError):
+        g._fit_desc((9, 256, 4), "fp16")

@@ -163,3 +163,139 @@ def test_fit_with_the_gradient_term_lowers_both_losses():
         opt.step()
         hist.append((float(l_d.detach()), float(l_g.detach())))
     assert hist[-1][0] < 0.7 * hist[0][0] and hist[-1][1] < 0.7 * hist[0][1], (hist[0], hist[-1])
+
+
+# ---- BF16 operands on the tensor cores ---------------------------------------
+# Bars: max(2e-2, 1.5 x E), E the error against the oracle of the rounding model
+# of tests/_lowp_model.py (both operands of every product rounded to BF16,
+# exact accumulation, everything else at high precision): the 2e-2 target
+# wherever BF16 rounding alone allows it.
+
+def _bar(e_model):
+    return max(2e-2, 1.5 * e_model)
+
+
+def _nrel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n,H,L,B", [(10, 512, 5, 2048), (9, 256, 4, 1000), (3, 96, 2, 333), (12, 64, 1, 5000)])
+def test_bf16_forward_and_vjp_match_the_oracle(n, H, L, B):
+    from _lowp_model import fit_model
+    torch = need_gpu()
+    g = lib()
+    _, w = small_net(n, hidden=H, n_layers=L)
+    q, p = _batch(n, B, n * 100 + B)
+    gf = np.random.default_rng(B).normal(size=B).astype(np.float32)
+    wd, qd, pd = to_dev(torch, np.asarray(w, np.float32)), to_dev(torch, q), to_dev(torch, p)
+    q64, p64 = q.astype(np.float64), p.astype(np.float64)
+    f = g.fit_forward((n, H, L), wd, qd, pd, precision="bf16").cpu().numpy()
+    dw, dq = g.fit_vjp((n, H, L), wd, qd, pd, to_dev(torch, gf), precision="bf16")
+    dw, dq = dw.cpu().numpy(), dq.cpu().numpy()
+    assert g.fit_device_status() == 0
+    f_ref, _ = fit.forward(n, H, L, w, q64, p64)
+    dw_ref, dq_ref = fit.vjp(n, H, L, w, q64, p64, gf.astype(np.float64))
+    fm, dwm, dqm = fit_model(n, H, L, w, q64, p64, gf.astype(np.float64))
+    for (a, m, r, err) in ((f, fm, f_ref, metrics.rel_err_scalar), (dq, dqm, dq_ref, metrics.rel_err_vector)):
+        ek, em = err(a, r), err(m, r)
+        print("bf16 kernel", ek.max(), np.percentile(ek, 99), "model", em.max(), np.percentile(em, 99))
+        assert ek.max() <= _bar(em.max()) and np.percentile(ek, 99) <= _bar(np.percentile(em, 99))
+    ek, em = _nrel(dw, dw_ref), _nrel(dwm, dw_ref)
+    print("bf16 dweights kernel", ek, "model", em)
+    assert ek <= _bar(em)
+
+
+@pytest.mark.parametrize("n,H,L,B", [(9, 256, 4, 1000), (10, 128, 2, 2048)])
+def test_bf16_value_grad_and_vjp2_match_the_oracle(n, H, L, B):
+    from _lowp_model import fit_model
+    torch = need_gpu()
+    g = lib()
+    _, w = small_net(n, hidden=H, n_layers=L)
+    q, p = _batch(n, B, n * 31 + B)
+    rng = np.random.default_rng(B + 5)
+    gf = rng.normal(size=B).astype(np.float32)
+    Gq = rng.normal(size=(B, n)).astype(np.float32)
+    wd, qd, pd = to_dev(torch, np.asarray(w, np.float32)), to_dev(torch, q), to_dev(torch, p)
+    q64, p64 = q.astype(np.float64), p.astype(np.float64)
+    f, dq = g.fit_value_grad((n, H, L), wd, qd, pd, precision="bf16")
+    dw = g.fit_vjp2((n, H, L), wd, qd, pd, to_dev(torch, gf), to_dev(torch, Gq), precision="bf16").cpu().numpy()
+    assert g.fit_device_status() == 0
+    _, dq_ref = fit.vjp(n, H, L, w, q64, p64, np.ones(B))
+    dw_ref = fit.vjp2(n, H, L, w, q64, p64, gf.astype(np.float64), Gq.astype(np.float64))
+    _, dqm, dwm = fit_model(n, H, L, w, q64, p64, gf.astype(np.float64), Gq.astype(np.float64))
+    ek, em = metrics.rel_err_vector(dq.cpu().numpy(), dq_ref), metrics.rel_err_vector(dqm, dq_ref)
+    assert ek.max() <= _bar(em.max()) and np.percentile(ek, 99) <= _bar(np.percentile(em, 99))
+    ek, em = _nrel(dw, dw_ref), _nrel(dwm, dw_ref)
+    print("bf16 vjp2 kernel", ek, "model", em)
+    assert ek <= _bar(em)
+
+
+def test_bf16_is_deterministic_and_reduces_to_the_first_order_vjp():
+    torch = need_gpu()
+    g = lib()
+    n, H, L, B = 10, 512, 5, 8192
+    _, w = small_net(n, hidden=H, n_layers=L)
+    q, p = _batch(n, B, 17)
+    wd, qd, pd = to_dev(torch, np.asarray(w, np.float32)), to_dev(torch, q), to_dev(torch, p)
+    gf = to_dev(torch, np.random.default_rng(4).normal(size=B).astype(np.float32))
+    a = g.fit_vjp((n, H, L), wd, qd, pd, gf, precision="bf16")
+    b = g.fit_vjp((n, H, L), wd, qd, pd, gf, precision="bf16")
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    c = g.fit_vjp2((n, H, L), wd, qd, pd, gf, torch.zeros_like(qd), precision="bf16")
+    assert torch.equal(c, a[0])
+    f, _ = g.fit_value_grad((n, H, L), wd, qd, pd, precision="bf16")
+    assert torch.equal(f, g.fit_forward((n, H, L), wd, qd, pd, precision="bf16"))
+    assert g.fit_device_status() == 0
+
+
+def test_bf16_full_batch_samples_match_the_oracle():
+    """The training-step size (10-DOF 5 x 512, batch 65,536): f and grad_q f of
+    sampled rows against the oracle, the weight gradient against the FP32 path."""
+    from _lowp_model import fit_model
+    torch = need_gpu()
+    g = lib()
+    n, H, L, B = 10, 512, 5, 65536
+    _, w = small_net(n, hidden=H, n_layers=L)
+    r = synth.SplitMix64(91)
+    q = np.stack([synth.random_config(r, n, -3.0, 3.0) for _ in range(B)]).astype(np.float32)
+    p = synth.uniform_points(r, B, [-3, -3, 0], [3, 3, 2]).astype(np.float32)
+    wd, qd, pd = to_dev(torch, np.asarray(w, np.float32)), to_dev(torch, q), to_dev(torch, p)
+    f, dq = g.fit_value_grad((n, H, L), wd, qd, pd, precision="bf16")
+    rows = np.random.default_rng(0).choice(B, 512, replace=False)
+    q64, p64 = q[rows].astype(np.float64), p[rows].astype(np.float64)
+    f_ref, _ = fit.forward(n, H, L, w, q64, p64)
+    _, dq_ref = fit.vjp(n, H, L, w, q64, p64, np.ones(len(rows)))
+    fm, dqm, _ = fit_model(n, H, L, w, q64, p64, np.zeros(len(rows)), np.zeros((len(rows), n)))
+    ek, em = metrics.rel_err_scalar(f.cpu().numpy()[rows], f_ref), metrics.rel_err_scalar(fm, f_ref)
+    assert ek.max() <= _bar(em.max())
+    ek, em = metrics.rel_err_vector(dq.cpu().numpy()[rows], dq_ref), metrics.rel_err_vector(dqm, dq_ref)
+    assert ek.max() <= _bar(em.max())
+    gf = (2.0 / B) * f
+    dw16, _ = g.fit_vjp((n, H, L), wd, qd, pd, gf, want_dq=False, precision="bf16")
+    dw32, _ = g.fit_vjp((n, H, L), wd, qd, pd, gf, want_dq=False)
+    e = float(torch.linalg.norm(dw16 - dw32) / torch.linalg.norm(dw32))
+    print("full batch bf16 vs fp32 dweights", e)
+    assert e <= 2e-2
+    assert g.fit_device_status() == 0
+
+
+def test_bf16_fit_lowers_the_distance_loss():
+    torch = need_gpu()
+    g = lib()
+    n, H, L, B = 9, 128, 3, 8192
+    _, w_teacher = small_net(n, hidden=H, n_layers=L, seed=1)
+    _, w0 = small_net(n, hidden=H, n_layers=L, seed=2)
+    q, p = _batch(n, B, 9)
+    qd, pd = to_dev(torch, q), to_dev(torch, p)
+    target = g.fit_forward((n, H, L), to_dev(torch, np.asarray(w_teacher, np.float32)), qd, pd)
+    wd = to_dev(torch, np.asarray(w0, np.float32)).requires_grad_(True)
+    opt = torch.optim.Adam([wd], lr=2e-3)
+    losses = []
+    for _ in range(40):
+        opt.zero_grad()
+        loss = ((g.field(wd, qd, pd, (n, H, L), precision="bf16") - target) ** 2).mean()
+        loss.backward()
+        opt.step()
+        losses.append(float(loss.detach()))
+    assert losses[-1] < 0.5 * losses[0]
+    assert g.fit_device_status() == 0
