@@ -21,6 +21,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "fit_tc.cuh"
 #include "tc_ptx.cuh"
 
@@ -248,10 +250,15 @@ int tc_gemm_tile_m() { return 2 * kRowsA; }
 int tc_gemm_tile_n() { return kTileN; }
 int tc_gemm_kblock() { return kKBlock; }
 
+namespace {
+std::mutex g_fit_mutex;  // guards the per-device status words and attribute flags
+}  // namespace
+
 int* fit_status_word() {
   static int* words[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_fit_mutex);
   if (!words[dev]) {
     int* w = nullptr;
     if (cudaMalloc(&w, sizeof(int)) != cudaSuccess) return nullptr;
@@ -266,11 +273,19 @@ cudaError_t tc_gemm_bf16(const void* A, long long lda, const void* B, long long 
                          cudaStream_t s, bool* encode_failed) {
   *encode_failed = false;
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  {
+    // opt in, once per device, to the kernel's dynamic shared memory
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_fit_mutex);
+    if (!attr_set[dev]) {
+      e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+      if (e != cudaSuccess) return e;
+      attr_set[dev] = true;
+    }
   }
   CUtensorMap ma, mb;
   if (!encode(&ma, A, M, K, lda, kRowsA) || !encode(&mb, B, N, K, ldb, kRowsB)) {
