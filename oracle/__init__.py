@@ -24,8 +24,10 @@ Contents
            base), the dense->sparse GCDF Jacobian of Eq. (17)/(18) and the
            single-step projection of Theorem 1.
   fit      per-sample field values and their vector-Jacobian products with
-           respect to the weights and q, for fitting with the distance loss
-           of Table I.
+           respect to the weights and q (first order: the distance loss of
+           Table I; second order: losses on grad_q f).
+  labels   labelled (q, p, f) samples of a capsule robot's sampled GCDF
+           (the data generation of Sec. III-C), for fitting on exact labels.
   metrics  the relative-error measures used by every parity test.
 
 Every function states the passage it follows.  Parity pins live in
