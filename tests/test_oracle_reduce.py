@@ -95,3 +95,19 @@ def test_csr_partition_equals_dense_subset():
         ci, gi, ai = red.reduce_waypoint(red.SOFTMIN, 0.1, f, dq, jj)
         assert (c[i] == ci) or (np.isinf(c[i]) and np.isinf(ci))
         np.testing.assert_array_equal(g[i], gi)
+
+
+def test_nan_propagates_to_the_waypoint_cost():
+    """The header's contract: a NaN pair value makes that waypoint's cost NaN in
+    every reduction (MIN ranks NaN first and reports its point), never a
+    silently finite number."""
+    from oracle import reduce as red
+    f = np.array([0.3, np.nan, 0.1, np.nan])
+    dq = np.arange(8, dtype=np.float64).reshape(4, 2)
+    pidx = np.array([10, 11, 12, 13])
+    c, g, a = red.reduce_waypoint(red.MIN, 0.0, f, dq, pidx)
+    assert np.isnan(c) and a == 11 and np.array_equal(g, dq[1])
+    c, g, a = red.reduce_waypoint(red.SOFTMIN, 0.02, f, dq, pidx)
+    assert np.isnan(c)
+    c, g, a = red.reduce_waypoint(red.HINGE, 0.05, f, dq, pidx)
+    assert np.isnan(c)
