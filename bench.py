@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -162,6 +163,21 @@ def make_workload():
 # CPU oracle leg (the only place this script runs oracle/)
 # ---------------------------------------------------------------------------
 
+def host_cpu() -> dict:
+    """The host's logical CPU count and model (for the CPU baseline's record)."""
+    model = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part"):
+                    model = f"{platform.machine()} {line.split(':', 1)[1].strip()}"
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
 def cpu_oracle_leg(wl, budget_s: float = 12.0, gpu_result=None):
     """Time the FP64 oracle on a bounded sample of the workload: whole waypoints
     (all 16,384 points each, evenly spread over the trajectory) until about
@@ -189,7 +205,7 @@ def cpu_oracle_leg(wl, budget_s: float = 12.0, gpu_result=None):
         cores = os.cpu_count()
     out = {"value": pairs / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
            "sample": f"{len(done)} of {N} waypoints x {M} points ({pairs} pairs), FP64 NumPy, {dt:.1f} s",
-           "pairs": pairs, "seconds": dt}
+           "pairs": pairs, "seconds": dt, "host": host_cpu()}
     if gpu_result is not None:
         c_gpu, g_gpu = gpu_result
         out["sample_err_cost_max"] = float(metrics.rel_err_scalar(c_gpu[done], np.array(costs)).max())
@@ -218,7 +234,7 @@ def run_reference(args):
                    "n_points": wl.p.shape[0], "net": "9-DOF 4x256 SiLU",
                    "sample": "whole waypoints, bounded time per step"},
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": rs[-1]["cores"], "kind": "oracle",
-                         "sample": rs[-1]["sample"]},
+                         "sample": rs[-1]["sample"], "host": rs[-1]["host"]},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
