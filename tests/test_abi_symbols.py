@@ -66,3 +66,45 @@ def test_fit_argument_errors_without_gpu():
     assert lib.gcdf_fit_device_status(None) == g._lib.GCDF_EINVAL
     with pytest.raises(ValueError):
         g._fit_desc((9, 256, 4), "fp16")
+
+
+def test_host_side_argument_checks_without_gpu():
+    """Every entry point rejects bad arguments before any CUDA call (the fake
+    pointers below are non-NULL and aligned but never dereferenced)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2601_18548_gb300 as g
+    L = g._lib
+    lib = L.load()
+    fake = ctypes.c_void_p(1 << 20)
+    # partition: negative or NaN radius, negative sizes, NULL / misaligned pointers
+    for r in (-1.0, float("nan")):
+        assert lib.gcdf_partition_offsets(fake, 4, fake, 4, r, fake, None) == L.GCDF_EINVAL
+    assert lib.gcdf_partition_offsets(fake, -1, fake, 4, 1.0, fake, None) == L.GCDF_EINVAL
+    assert lib.gcdf_partition_offsets(None, 4, fake, 4, 1.0, fake, None) == L.GCDF_EINVAL
+    assert lib.gcdf_partition_indices(fake, 4, ctypes.c_void_p((1 << 20) + 4), 4, 1.0, fake, fake,
+                                      None) == L.GCDF_EINVAL
+    # Jacobian scatter: n_dof outside 1..12, negative sizes, 2 N n past 2^31 - 1
+    for (N, n, P) in ((4, 0, 4), (4, 13, 4), (-1, 9, 4), (4, 9, -1), (1 << 30, 9, 1)):
+        assert lib.gcdf_jacobian_scatter(fake, N, n, None, 4, P, fake, fake, fake, None) == L.GCDF_EINVAL
+    # planner and server
+    prm = L.PlanParams(0.1, 1.0, 0.5, 100.0, 1.0, 0.05, 1.0, 1e-6, 1e8, 50, 0.0)
+    assert lib.gcdf_plan_solve(None, None, 0, ctypes.byref(prm), fake, None, None, None) == L.GCDF_EINVAL
+    out = ctypes.c_void_p()
+    assert lib.gcdf_server_create(None, ctypes.byref(out)) == L.GCDF_EINVAL
+    for bad in (dict(dt=0.0), dict(iterations=-1), dict(partition_radius=-1.0), dict(lambda_max=1e-9),
+                dict(delta=float("nan"))):
+        p2 = L.PlanParams(0.1, 1.0, 0.5, 100.0, 1.0, 0.05, 1.0, 1e-6, 1e8, 50, 0.0)
+        for k, v in bad.items():
+            setattr(p2, k, v)
+        d = L.ServerDesc(1 << 30, 4, 16, p2)
+        assert lib.gcdf_server_create(ctypes.byref(d), ctypes.byref(out)) == L.GCDF_EINVAL, bad
+    for (budget, act, queued) in ((0, 4, 16), (1 << 30, 0, 16), (1 << 30, 4, -1)):
+        d = L.ServerDesc(budget, act, queued, prm)
+        assert lib.gcdf_server_create(ctypes.byref(d), ctypes.byref(out)) == L.GCDF_EINVAL
+    t = ctypes.c_uint64()
+    assert lib.gcdf_plan_submit(None, None, ctypes.byref(t)) == L.GCDF_EINVAL
+    assert lib.gcdf_plan_poll(None, 1, None) == L.GCDF_EINVAL
+    assert lib.gcdf_plan_request_bytes(None, 10, 10) == 0
+    assert lib.gcdf_server_destroy(None) == L.GCDF_OK
+    assert lib.gcdf_project(None, fake, 1, fake, 1, None, None, 0, None, None, fake, None) == L.GCDF_EINVAL
