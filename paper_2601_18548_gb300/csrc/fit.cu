@@ -360,8 +360,8 @@ __global__ void transpose_bf16_kernel(const float* __restrict__ X, long long row
 long long pad8(long long x) { return (x + 7) / 8 * 8; }
 
 // The products of one call: FP32 SIMT GEMMs, or the BF16 tensor-core GEMM on
-// K-major BF16 images of both operands (a strided operand whose K index is the
-// contiguous one is rounded in place order, the other one transposed).
+// K-major BF16 images of both operands (an operand whose K index is already the
+// contiguous one is rounded row by row, the other one is transposed).
 struct Ctx {
   cudaStream_t s;
   float* partials = nullptr;
@@ -386,6 +386,7 @@ struct Ctx {
     if (sk == 1) {
       cast_bf16_kernel<<<(int)std::min<long long>(rows, 152 * 16), 128, 0, s>>>(X, rows, K, srow, Y, ld);
     } else if (srow == 1) {  // X is K x rows with row stride sk
+      if ((rows + 31) / 32 > 65535) return cudaErrorInvalidValue;  // grid y limit (rows are feature widths)
       dim3 grid((unsigned)((K + 31) / 32), (unsigned)((rows + 31) / 32));
       transpose_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(X, K, rows, sk, Y, ld);
     } else {
