@@ -57,3 +57,26 @@ def test_reference_arm_other_ranks_do_nothing(monkeypatch):
     class A:
         steps, warmup, gpus, ref_budget = 1, 3, 2, 1.0
     assert bench.run_reference(A()) == 0
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    """`bench.py --impl reference` (the oracle on the host cores) prints one
+    JSON line with every key of the benchmark contract."""
+    import json
+
+    import bench
+    monkeypatch.setenv("RANK", "0")
+
+    class A:
+        steps, warmup, gpus, ref_budget = 1, 3, 1, 0.2
+    assert bench.run_reference(A()) in (0, None)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["steps"] == 1 and line["warmup"] == 3 and "workload" in line["config"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
