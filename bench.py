@@ -173,7 +173,7 @@ def host_cpu() -> dict:
                 if key in ("model name", "cpu part"):
                     model = f"{platform.machine()} {line.split(':', 1)[1].strip()}"
                     break
-    except OSError:
+    except Exception:  # a record field only: never fail the benchmark over it
         pass
     return {"nproc": os.cpu_count(), "model": model}
 
