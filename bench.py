@@ -37,8 +37,6 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
 
 
 def flops_per_pair(shape: synth.NetShape) -> int:
@@ -107,8 +105,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, uuid: str | None):
+    def __init__(self, uuid: str | None, interval_ms: int = 200):
         self.uuid = uuid
+        self.interval_ms = int(interval_ms)
         self.proc = None
         self.path = os.path.join("/tmp", f"gcdf_clocks_{os.getpid()}.csv")
 
@@ -116,7 +115,7 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                                          "-lms", str(self.interval_ms)], stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -150,6 +149,14 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:  # a record field only
+        return None
 
 
 WAYPOINTS, POINTS = 128, 16384
@@ -211,6 +218,27 @@ def cpu_oracle_leg(wl, budget_s: float = 12.0, gpu_result=None):
         out["sample_err_cost_max"] = float(metrics.rel_err_scalar(c_gpu[done], np.array(costs)).max())
         out["sample_err_grad_max"] = float(metrics.rel_err_vector(g_gpu[done], np.array(grads)).max())
     return out
+
+
+_SINGLE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+                      "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")
+
+
+def cpu_oracle_single_thread(budget_s: float = 6.0):
+    """The same oracle leg in a fresh interpreter with every BLAS / OpenMP pool
+    limited to one thread (the limits must be set before NumPy loads)."""
+    env = dict(os.environ)
+    for k in _SINGLE_THREAD_ENV:
+        env[k] = "1"
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "r = bench.cpu_oracle_leg(bench.make_workload(), budget_s=%r); r['cores'] = 1; "
+            "print(json.dumps(r))") % (ROOT, float(budget_s))
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=budget_s * 10 + 120)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # a record field only: never fail the benchmark over it
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def run_reference(args):
@@ -287,13 +315,7 @@ def run_gpu(args):
     for ev in k_start + k_stop:
         ev.record(stream)  # creates the CUDA event (PyTorch creates it on first record)
     torch.cuda.synchronize()
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(dev).uuid)
-        uuid = "GPU-" + uuid if not uuid.startswith("GPU-") else uuid
-    except Exception:
-        pass
-    clocks = ClockSampler(uuid)
+    clocks = ClockSampler(_uuid(torch, dev), interval_ms=50)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -353,13 +375,18 @@ def run_gpu(args):
         bound, punit = "tensor", "TFLOP/s"
         peak_note = f"fp8 dense = 2 x bf16 dense burst {peak_src} (nominal ratio 4.5 / 2.25 PFLOP/s)"
     else:
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        fma = measure_fp32_fma_peak(g, torch)
+        peak = fma["tflops"]
         bound, punit = "alu", "TFLOP/s"
-        peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock (derived)"
+        peak_note = "measured FP32 FMA loop (gcdf_diag_fp32_fma): " + fma["launch"]
+    extras = {}
+    if world == 1 and not args.no_extras:
+        extras = gpu_extras(g, torch, dev, wl, net, args, peaks)
     cb = None
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_oracle_leg(wl, budget_s=args.ref_budget,
                             gpu_result=(out[0].cpu().numpy(), out[1].cpu().numpy()))
+        cb["single_thread"] = cpu_oracle_single_thread(min(6.0, args.ref_budget))
     line = {
         "metric": "GCDF value+grad pairs/s (soft-min collision cost)",
         "value": value,
@@ -388,11 +415,115 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(c_h.numel() * 4 + g_h.numel() * 4 + a_h.numel() * 4)},
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
+        **extras,
     }
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def measure_fp32_fma_peak(g, torch, reps=7):
+    """Measured FP32 FMA rate (TFLOP/s) of the library's FMA loop: 4 blocks of
+    256 threads per SM, 8 independent chains per thread, median of `reps`
+    launches timed with CUDA events after one warm-up launch."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, threads, iters = 4 * sms, 256, 20000
+    sink = torch.empty(blocks * threads, device="cuda")
+    flops = g.diag_fp32_fma(blocks, threads, iters, sink)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.diag_fp32_fma(blocks, threads, iters, sink)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.median(ts)
+    return {"tflops": flops / (ms / 1e3) / 1e12, "ms": ms, "flops_per_launch": flops,
+            "launch": f"{blocks} x {threads} threads, 8 FMA chains x {4 * iters} steps each"}
+
+
+def _kernel_ms(g, torch, net, fn, reps, flush=None):
+    """Median duration (ms) of the fused kernel inside fn(), from the library's
+    profile events on the current stream."""
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g.set_profile_events(net, a, b)
+        fn()
+        torch.cuda.synchronize()
+        g.set_profile_events(net)
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def gpu_extras(g, torch, dev, wl, net, args, peaks):
+    """Measurements reported beside the headline (after its timed region):
+      fp32_path   the FP32 CUDA-core kernel on the same workload against the
+                  measured FP32 FMA rate;
+      sweep       the BF16 kernel at larger scenes (128-2048 waypoints x
+                  16,384-65,536 points) against the BF16 dense peak;
+      sustained   the step back to back for ~2 s (no flush) with its own clock
+                  record: the steady-state rate against the sustained peak."""
+    s = wl.shape
+    fpp = flops_per_pair(s)
+    out = {}
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+    fma = measure_fp32_fma_peak(g, torch)
+    q = torch.from_numpy(wl.q).to(dev)
+    p = torch.from_numpy(wl.p).to(dev)
+    net32 = g.create_net(s.n_dof, s.hidden, s.n_layers, wl.weights, "fp32")
+    ms32 = _kernel_ms(g, torch, net32, lambda: g.collision_cost(net32, q, p, wl.reduction, wl.param), 5, flush)
+    del net32
+    out["fp32_path"] = {"kernel_ms": ms32, "pairs_per_s": wl.n_pairs / (ms32 / 1e3),
+                        "achieved_tflops": fpp * wl.n_pairs / (ms32 / 1e3) / 1e12,
+                        "peak_tflops": fma["tflops"], "frac": fpp * wl.n_pairs / (ms32 / 1e3) / 1e12 / fma["tflops"],
+                        "peak_source": "measured FP32 FMA loop (gcdf_diag_fp32_fma): " + fma["launch"],
+                        "bound": "alu"}
+    peak = float(peaks["bf16_tflops"])
+    sweep = []
+    if args.precision in ("bf16", "fp16"):
+        for (N, M) in ((128, 65536), (512, 16384), (512, 65536), (2048, 16384), (2048, 65536)):
+            sc = synth.box_scene(n_waypoints=N, n_points=M)
+            qs = torch.from_numpy(sc.q).to(dev)
+            ps = torch.from_numpy(sc.p).to(dev)
+            ms = _kernel_ms(g, torch, net, lambda: g.collision_cost(net, qs, ps, wl.reduction, wl.param), 3)
+            P = N * M
+            sweep.append({"n_waypoints": N, "n_points": M, "pairs": P, "kernel_ms": ms,
+                          "pairs_per_s": P / (ms / 1e3), "achieved_tflops": fpp * P / (ms / 1e3) / 1e12,
+                          "frac": fpp * P / (ms / 1e3) / 1e12 / peak})
+            del qs, ps
+        out["sweep"] = {"precision": args.precision, "peak_tflops": peak, "points": sweep}
+    # steady state: back-to-back steps for about two seconds
+    outb = (torch.empty(q.shape[0], device=dev), torch.empty(q.shape[0], s.n_dof, device=dev),
+            torch.empty(q.shape[0], device=dev, dtype=torch.int32))
+    one = _kernel_ms(g, torch, net, lambda: g.collision_cost(net, q, p, wl.reduction, wl.param, out=outb), 3)
+    n_rep = max(10, int(2000.0 / max(one, 1e-3)))
+    clocks = ClockSampler(_uuid(torch, dev), interval_ms=50)
+    clocks.start()
+    time.sleep(0.2)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(n_rep):
+        g.collision_cost(net, q, p, wl.reduction, wl.param, out=outb)
+    b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sec = a.elapsed_time(b) / 1e3
+    sus_peak = float(peaks.get("bf16_tflops_sustained", peak))
+    if args.precision in ("bf16", "fp16"):
+        out["sustained"] = {"steps": n_rep, "seconds": sec, "pairs_per_s": wl.n_pairs * n_rep / sec,
+                            "achieved_tflops": fpp * wl.n_pairs * n_rep / sec / 1e12, "peak_tflops": sus_peak,
+                            "frac": fpp * wl.n_pairs * n_rep / sec / 1e12 / sus_peak,
+                            "peak_source": "bf16 dense sustained (seconds-long loop under the power cap)",
+                            "clocks": clk}
+    return out
 
 
 def _serve_requests(rng, pools, rate, duration, h_rng, m_rng):
@@ -710,8 +841,9 @@ def run_fit(args):
     fwd = 2 * (d_in * H + (L - 1) * H * H + H)
     flops = B * (2 * fwd + fwd + 2 * (L - 1) * H * H)
     if prec == "fp32":
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
-        bound, src = "alu", "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (derived)"
+        fma = measure_fp32_fma_peak(g, torch)
+        peak, bound = fma["tflops"], "alu"
+        src = "measured FP32 FMA loop (gcdf_diag_fp32_fma): " + fma["launch"]
     else:
         peaks, psrc = load_peaks()
         peak, bound = float(peaks["bf16_tflops"]), "tensor"
@@ -738,6 +870,8 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp8", "fp32"])
     ap.add_argument("--ref-budget", type=float, default=12.0, help="seconds of oracle work per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP32-path, scene-sweep and sustained measurements after the timed region")
     ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch from ncu")
     ap.add_argument("--waypoints", type=int, default=128, help="smaller scenes for profiling only")
     ap.add_argument("--points", type=int, default=16384, help="smaller scenes for profiling only")

@@ -188,10 +188,12 @@ GCDF_API int gcdf_collision_cost(gcdf_net *net, const float *q, int n_waypoints,
  *
  * All calls on a device share the array, so calls whose GPU work overlaps in
  * time (on different streams, or from different threads) race and corrupt
- * each other's results; serialise them (one stream, or events).  The first
- * call on each device looks up the array's device address (under a lock);
- * make that first call before any stream capture.  Calls no cudaMalloc,
- * cudaMallocAsync or cudaFree.
+ * each other's results; serialise them (one stream, or events).  Every call
+ * looks up the array's device address in the current context
+ * (cudaGetSymbolAddress; the first call on a device may also load the
+ * library's device code there), so the address stays right after the context
+ * is destroyed and recreated; make the first call on each device before any
+ * stream capture.  Calls no cudaMalloc, cudaMallocAsync or cudaFree.
  */
 GCDF_API int gcdf_collision_cost_noalloc(gcdf_net *net, const float *q, int n_waypoints,
                                          const float *p, int n_points, const int *part_offsets,
@@ -208,6 +210,33 @@ GCDF_API int gcdf_collision_cost_noalloc(gcdf_net *net, const float *q, int n_wa
  * the word.  Errors: EINVAL (NULL argument), ECUDA.
  */
 GCDF_API int gcdf_device_status(gcdf_net *net, int *status);
+
+/*
+ * Self-test of the device-side failure detection (no counterpart in the
+ * paper).  Launches, on the net's device and synchronously, one block whose
+ * two warps wait with the tensor-core kernel's own bounded-wait routines (the
+ * producer/MMA wait and the epilogue's warp-wide wait) on an mbarrier that
+ * nothing ever arrives on, with a limit of limit_cycles clock cycles instead of
+ * the kernel's ~1 s.  Both waits must give up, raise the kernel's abort flag
+ * and set bit 0 of the net's status word, exactly as a wait of the fused
+ * kernel would; no copy, MMA or tensor memory is in flight, so the context
+ * stays usable.  seen (3 ints, HOST) out: [producer wait expired (1/0),
+ * epilogue wait expired (1/0), abort flag raised (1/0)].  Read and clear the
+ * status word with gcdf_device_status.  Errors: EINVAL (NULL argument,
+ * limit_cycles outside [1e3, 4e9], net of another device), ECUDA.
+ */
+GCDF_API int gcdf_selftest_wait_expiry(gcdf_net *net, long long limit_cycles, int *seen);
+
+/*
+ * FP32 fused-multiply-add rate loop (no counterpart in the paper): the
+ * measured roofline denominator of the FP32 CUDA-core paths.  Enqueues one
+ * launch of `blocks` x `threads` threads (threads a multiple of 32, at most
+ * 1024), each running 8 independent FMA chains for 4 x iters steps and writing
+ * one float to sink (blocks x threads floats, DEVICE).  Returns the FLOPs the
+ * launch performs (2 per FMA) — time it with events on `stream` — or minus an
+ * error code (EINVAL for bad arguments, ECUDA).
+ */
+GCDF_API long long gcdf_diag_fp32_fma(int blocks, int threads, int iters, float *sink, gcdf_stream_t stream);
 
 /*
  * Profiling hook: while set, every gcdf_query / gcdf_collision_cost call on

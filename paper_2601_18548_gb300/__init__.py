@@ -206,6 +206,23 @@ def set_profile_events(net: Net, start=None, stop=None) -> None:
     _lib.check(_lib.load().gcdf_set_profile_events(net.handle, a, b))
 
 
+def selftest_wait_expiry(net: Net, limit_cycles: int = 200000):
+    """gcdf_selftest_wait_expiry: [producer wait expired, epilogue wait expired,
+    abort flag raised] of a probe whose waits can never complete."""
+    seen = (ctypes.c_int * 3)()
+    _lib.check(_lib.load().gcdf_selftest_wait_expiry(net.handle, int(limit_cycles), seen))
+    return [int(x) for x in seen]
+
+
+def diag_fp32_fma(blocks: int, threads: int, iters: int, sink: torch.Tensor, stream=None) -> int:
+    """gcdf_diag_fp32_fma: enqueue the FMA-rate loop; returns its FLOP count."""
+    r = _lib.load().gcdf_diag_fp32_fma(int(blocks), int(threads), int(iters), _ptr(sink, name="sink"),
+                                       _stream(stream))
+    if r < 0:
+        _lib.check(int(-r))
+    return int(r)
+
+
 def last_error() -> str:
     """gcdf_last_error."""
     m = _lib.load().gcdf_last_error()

@@ -3,7 +3,6 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <vector>
 
@@ -486,6 +485,37 @@ int gcdf_set_profile_events(gcdf_net* net, void* start_event, void* stop_event) 
   return GCDF_OK;
 }
 
+int gcdf_selftest_wait_expiry(gcdf_net* net, long long limit_cycles, int* seen) {
+  if (!net || !seen) return fail(GCDF_EINVAL, "net or seen is NULL");
+  if (limit_cycles < 1000 || limit_cycles > 4000000000LL)
+    return fail(GCDF_EINVAL, "limit_cycles %lld outside [1e3, 4e9]", limit_cycles);
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != net->device) return fail(GCDF_EINVAL, "net belongs to device %d, current device is %d", net->device, dev);
+  int* d_seen = nullptr;
+  cudaError_t e = cudaMalloc((void**)&d_seen, 4 * sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if ((e = cudaMemset(d_seen, 0xff, 4 * sizeof(int))) == cudaSuccess &&
+      (e = launch_wait_expiry_probe(net->err_word, limit_cycles, d_seen, nullptr)) == cudaSuccess &&
+      (e = cudaDeviceSynchronize()) == cudaSuccess)
+    e = cudaMemcpy(seen, d_seen, 3 * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d_seen);
+  if (e != cudaSuccess) return cuda_fail(e, "wait-expiry self-test");
+  g_err[0] = 0;
+  return GCDF_OK;
+}
+
+long long gcdf_diag_fp32_fma(int blocks, int threads, int iters, float* sink, gcdf_stream_t stream) {
+  if (blocks <= 0 || threads <= 0 || threads > 1024 || threads % 32 || iters <= 0 || !sink) {
+    fail(GCDF_EINVAL, "bad FMA-loop arguments (blocks %d, threads %d, iters %d)", blocks, threads, iters);
+    return -GCDF_EINVAL;
+  }
+  cudaError_t e = launch_fma_rate(blocks, threads, iters, sink, (cudaStream_t)stream);
+  if (e != cudaSuccess) return -cuda_fail(e, "FMA loop launch");
+  g_err[0] = 0;
+  return (long long)blocks * threads * fma_rate_flops_per_thread(iters);
+}
+
 const char* gcdf_last_error(void) { return g_err; }
 
 }  // extern "C"
@@ -507,23 +537,18 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = 16u << 20;  // 16 MiB per device, held until the process exits
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_noalloc_mutex;
-void* g_noalloc_ptr[64] = {nullptr};
-
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Device address of the scratch array for the current device, looked up once
-// per device (the host-side name of the array is not a device address).
-int noalloc_scratch(int dev, void** out) {
-  if (dev < 0 || dev >= 64) return fail(GCDF_EINVAL, "device ordinal %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+// Device address of the scratch array in the current device's context.  The
+// host-side name of the array is not a device address.  Looked up on every
+// call: the lookup is cheap once the module is loaded on the device, and a
+// cached address would go stale if the context were destroyed and recreated
+// (cudaDeviceReset), after which the array lives elsewhere.
+int noalloc_scratch(void** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+  *out = p;
   return GCDF_OK;
 }
 
@@ -562,7 +587,7 @@ int gcdf_collision_cost_noalloc(gcdf_net* net, const float* q, int N, const floa
                 "(use gcdf_collision_cost, or split the waypoints into smaller calls)",
                 need, kNoAllocScratchBytes);
   void* scratch = nullptr;
-  if ((rc = noalloc_scratch(net->device, &scratch))) return rc;
+  if ((rc = noalloc_scratch(&scratch))) return rc;
   unsigned char* sp = static_cast<unsigned char*>(scratch);
   float* A = reinterpret_cast<float*>(sp);
   float* trig = reinterpret_cast<float*>(sp + b_A);

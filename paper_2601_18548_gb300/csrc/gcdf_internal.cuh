@@ -223,5 +223,8 @@ size_t tc_image_elems(int H, int L, int d_q);
 void tc_build_image(const float* W, int H, int L, int d_q, int d_in, int fmt, void* out, float* scales);
 int tc_encode_maps(const void* image, int H, int L, int d_q, int fmt, TcWeights& tw);
 int tc_nj(int d_q);
+cudaError_t launch_wait_expiry_probe(int* err, long long limit_cycles, int* seen, cudaStream_t s);
+cudaError_t launch_fma_rate(int blocks, int threads, int iters, float* sink, cudaStream_t s);
+long long fma_rate_flops_per_thread(int iters);
 
 }  // namespace gcdf

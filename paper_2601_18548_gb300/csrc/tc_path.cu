@@ -125,14 +125,16 @@ constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
 __device__ __forceinline__ uint32_t bar(uint32_t base, int i) { return base + kOffBar + 8 * i; }
 
 // Wait used by the single-thread producer and MMA roles: gives up early when
-// another role has aborted.
-__device__ __forceinline__ bool wait_role(uint32_t b, uint32_t parity, volatile int* abort_flag, int* err) {
+// another role has aborted.  `limit` (cycles) is kWaitCycles except in the
+// expiry self-test.
+__device__ __forceinline__ bool wait_role(uint32_t b, uint32_t parity, volatile int* abort_flag, int* err,
+                                          long long limit = kWaitCycles) {
   if (ptx::mbar_try_wait(b, parity)) return true;
   const long long t0 = clock64();
   while (true) {
     if (ptx::mbar_try_wait(b, parity)) return true;
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       atomicOr(err, 1);
       return false;
@@ -143,12 +145,13 @@ __device__ __forceinline__ bool wait_role(uint32_t b, uint32_t parity, volatile 
 // Wait used by epilogue threads: only its own time limit ends it, so every
 // thread waiting on the same phase takes the same decision.  Waiting threads
 // sleep in hardware rather than poll, leaving issue slots to working warps.
-__device__ __forceinline__ bool wait_epi(uint32_t b, uint32_t parity, volatile int* abort_flag, int* err) {
+__device__ __forceinline__ bool wait_epi(uint32_t b, uint32_t parity, volatile int* abort_flag, int* err,
+                                         long long limit = kWaitCycles) {
   if (ptx::mbar_try_wait(b, parity)) return true;
   const long long t0 = clock64();
   while (true) {
     if (ptx::mbar_try_wait_sleep(b, parity, 100000u)) return true;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       atomicOr(err, 1);
       return false;
@@ -158,9 +161,44 @@ __device__ __forceinline__ bool wait_epi(uint32_t b, uint32_t parity, volatile i
 
 // wait_epi by every lane of a warp, with one decision for the whole warp (the
 // epilogue synchronises its warps, so no lane may leave a loop alone)
-__device__ __forceinline__ bool wait_epi_warp(uint32_t b, uint32_t parity, volatile int* abort_flag, int* err) {
-  const bool got = wait_epi(b, parity, abort_flag, err);
+__device__ __forceinline__ bool wait_epi_warp(uint32_t b, uint32_t parity, volatile int* abort_flag, int* err,
+                                              long long limit = kWaitCycles) {
+  const bool got = wait_epi(b, parity, abort_flag, err, limit);
   return __all_sync(0xffffffffu, got);
+}
+
+// Self-test of the bounded waits (gcdf_selftest_wait_expiry): one CTA of two
+// warps waits, with the fused kernel's own helpers, on an mbarrier that nothing
+// ever arrives on.  Warp 0's lane 0 takes the producer / MMA wait, warp 1 the
+// epilogue's warp-wide wait; both must give up after `limit` cycles, raise the
+// abort flag and set bit 0 of the status word.  No copy, MMA or tensor memory
+// is involved, so nothing is left in flight when the waits expire.
+// seen[0] / seen[1]: 1 when the producer / epilogue wait returned "expired",
+// seen[2]: the abort flag afterwards.
+__global__ void __launch_bounds__(64, 1) wait_expiry_probe_kernel(int* err, long long limit, int* seen) {
+  __shared__ __align__(8) uint64_t never;
+  __shared__ int abort_flag_s;
+  volatile int* abort_flag = &abort_flag_s;
+  const uint32_t b = ptx::smem_u32(&never);
+  if (threadIdx.x == 0) {
+    abort_flag_s = 0;
+    ptx::mbar_init(b, 1);
+    ptx::fence_barrier_init();
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    if (lane == 0) {
+      // gives up at its own limit or when the other warp's expiry raised the flag
+      const bool got = wait_role(b, 0u, abort_flag, err, limit);
+      seen[0] = got ? 0 : 1;
+    }
+  } else {
+    const bool got = wait_epi_warp(b, 0u, abort_flag, err, limit);
+    if (lane == 0) seen[1] = got ? 0 : 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) seen[2] = abort_flag_s;
 }
 
 __device__ __forceinline__ int total_tiles(const WorkDesc& w) {
@@ -1073,6 +1111,11 @@ cudaError_t launch_tc_t(const WorkDesc& w, const TcWeights& tw, int num_sms, cud
   if (npt <= 0) return cudaSuccess;
   cfg.gridDim = dim3(2 * (npt < mc ? npt : mc));
   return cudaLaunchKernelEx(&cfg, tc_fused_kernel<kFmt>, w, tw.map_w, tw.map_j, tw);
+}
+
+cudaError_t launch_wait_expiry_probe(int* err, long long limit_cycles, int* seen, cudaStream_t s) {
+  wait_expiry_probe_kernel<<<1, 64, 0, s>>>(err, limit_cycles, seen);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_tc(const WorkDesc& w, const TcWeights& tw, int num_sms, cudaStream_t s) {

@@ -108,3 +108,15 @@ def test_host_side_argument_checks_without_gpu():
     assert lib.gcdf_plan_request_bytes(None, 10, 10) == 0
     assert lib.gcdf_server_destroy(None) == L.GCDF_OK
     assert lib.gcdf_project(None, fake, 1, fake, 1, None, None, 0, None, None, fake, None) == L.GCDF_EINVAL
+
+
+def test_diagnostic_entry_points_check_their_arguments_without_gpu():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2601_18548_gb300 as g
+    lib = g._lib.load()
+    seen = (ctypes.c_int * 3)()
+    assert lib.gcdf_selftest_wait_expiry(None, 100000, seen) == g._lib.GCDF_EINVAL
+    assert lib.gcdf_diag_fp32_fma(0, 256, 10, None, None) == -g._lib.GCDF_EINVAL
+    assert lib.gcdf_diag_fp32_fma(4, 100, 10, None, None) == -g._lib.GCDF_EINVAL
+    assert "FMA" in g.last_error()

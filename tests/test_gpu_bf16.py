@@ -2,16 +2,20 @@
 
 Bars (err_f, err_g of oracle.metrics, max and p99 over pairs):
   FP16  max <= 2e-2 against the FP64 oracle.
-  BF16  max and p99 <= max(2e-2, 1.5 x E), where E is the error, against the
-        oracle, of tests/_lowp_model.py: the same network rounded to BF16 at
-        exactly the kernel's rounding points, with an exact tanh.  Rounding to
-        BF16 alone already gives a max of 2.8e-2 on the box scene (the format
-        has 8 significant bits), so a fixed 2e-2 max is not attainable by any
-        BF16 kernel there; the bar is 2e-2 wherever the format allows it.  The
-        factor 1.5 covers the hardware tanh approximation, whose error is of
-        the order of the FP16 intermediate rounding the model already applies
-        (measured kernel errors stay within 1.3 x E); the kernel must also stay
-        within 1.5 x E of the model itself.
+  BF16  max and p99 <= max(2e-2, K_BF16 x E_ref), K_BF16 = 1.25 fixed.  E_ref is
+        the error, against the FP64 oracle, of oracle/lowp.py: the same
+        network with every operand of a hidden-layer product (weights W_2..W_L,
+        W_1q, the activations and the reverse vectors) rounded to BF16 and
+        everything else exact.  E_ref depends on the BF16 format and the
+        weights only, never on a kernel, so no kernel change can move the bar.
+        On the box scene E_ref alone is max 2.9e-2 / p99 1.5e-2 for f (the
+        format has 8 significant bits and activation rounding carries most of
+        it), so the benchmark spec's 2e-2 holds for the p99 there but not for the
+        max; the factor 1.25 covers what a kernel adds on top of the format:
+        its FP16 epilogue roundings (each 8x finer than one BF16 rounding), the
+        hardware tanh and the FP32 accumulation order.
+The kernel is also checked against tests/_lowp_model.py, a model of its own
+rounding points, to show where the remaining difference comes from.
 The SOFTMIN cost gradient mixes per-pair gradients with weights exp(-f / T); a
 value error e shifts a weight by exp(e / T), so its bound is derived per case
 as TOL + 2 * max|f| * max_err_f / T and the measured number is printed.
@@ -27,6 +31,7 @@ from _lowp_model import lowp_eval
 
 pytestmark = pytest.mark.gpu
 TOL = 2e-2
+K_BF16 = 1.25
 
 
 def _net(g, shape, w, prec="bf16"):
@@ -47,13 +52,13 @@ def _bar(prec, shape, w, q, p, f_ref, g_ref, offsets=None, idx=None, shift=None,
     """(max, p99) bars for err_f and err_g of this case."""
     if prec == "fp16":
         return (TOL, TOL), (TOL, TOL)
+    from oracle import lowp
     ii, jj = _pairs(q, p, offsets, idx) if pairs is None else pairs
-    fm, gm = lowp_eval(shape.n_dof, shape.hidden, shape.n_layers, w, q[ii], p[jj],
-                       None if shift is None else shift[ii], "bf16")
+    fm, gm = lowp.eval_pairs(shape.n_dof, shape.hidden, shape.n_layers, w, q, p, ii, jj, shift, "bf16")
     ef, eg = errs(fm, gm, f_ref, g_ref)
-    print("  bf16 rounding model vs oracle: err_f", ef, "err_g", eg)
-    return ((max(TOL, 1.5 * ef["max"]), max(TOL, 1.5 * ef["p99"])),
-            (max(TOL, 1.5 * eg["max"]), max(TOL, 1.5 * eg["p99"])))
+    print("  BF16-operand reference vs oracle: err_f", ef, "err_g", eg)
+    return ((max(TOL, K_BF16 * ef["max"]), max(TOL, K_BF16 * ef["p99"])),
+            (max(TOL, K_BF16 * eg["max"]), max(TOL, K_BF16 * eg["p99"])))
 
 
 def _ok(ef, eg, bars):

@@ -166,13 +166,15 @@ def test_fit_with_the_gradient_term_lowers_both_losses():
 
 
 # ---- BF16 operands on the tensor cores ---------------------------------------
-# Bars: max(2e-2, 1.5 x E), E the error against the oracle of the rounding model
-# of tests/_lowp_model.py (both operands of every product rounded to BF16,
-# exact accumulation, everything else at high precision): the 2e-2 target
-# wherever BF16 rounding alone allows it.
+# Bars: max(2e-2, 1.25 x E), E the error against the oracle of fit_model in
+# tests/_lowp_model.py: both operands of every matrix product rounded to BF16,
+# exact accumulation, everything else exact.  That is what BF16 GEMM operands
+# cost by definition, whatever a kernel does around its products, so the bar
+# does not follow the kernel; the 2e-2 target holds wherever BF16 rounding
+# alone allows it.  The factor is the one of the field's BF16 bar.
 
 def _bar(e_model):
-    return max(2e-2, 1.5 * e_model)
+    return max(2e-2, 1.25 * e_model)
 
 
 def _nrel(a, b):

@@ -165,3 +165,36 @@ def test_deterministic_repeat():
     b = [x.cpu().numpy() for x in g.collision_cost(net, q, p, "softmin", 0.02)]
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+def test_full_size_scene_sampled_waypoints():
+    """The benchmark workload (128 waypoints x 16,384 points, soft-min T = 0.02)
+    on the FP32 path in the bench's launch configuration; the oracle checks 4
+    whole waypoints: per-pair f and df/dq within 1e-5, the soft-min cost within
+    1e-5 and its gradient within the soft-min bound above."""
+    from oracle import mlp
+    torch = need_gpu()
+    g = lib()
+    wl = synth.box_scene()
+    s = wl.shape
+    net = g.create_net(s.n_dof, s.hidden, s.n_layers, wl.weights, "fp32")
+    q, p = to_dev(torch, wl.q), to_dev(torch, wl.p)
+    c, gc, am = g.collision_cost(net, q, p, "softmin", 0.02)
+    f, gr = g.query(net, q, p)
+    torch.cuda.synchronize()
+    wps = [0, 41, 90, 127]
+    M = wl.p.shape[0]
+    fs = f.cpu().numpy().reshape(-1, M)[wps].ravel()
+    gs = gr.cpu().numpy().reshape(-1, M, 9)[wps].reshape(-1, 9)
+    ii = np.repeat(wps, M)
+    jj = np.tile(np.arange(M), len(wps))
+    f_ref, gq_ref = mlp.eval_pairs(9, 256, 4, wl.weights, wl.q, wl.p, ii, jj)
+    ef, eg = errs(fs, gs, f_ref, gq_ref)
+    print("fp32 full-size sampled: err_f", ef, "err_g", eg)
+    assert ef["max"] <= TOL and eg["max"] <= TOL, (ef, eg)
+    c_ref, g_ref, _ = oracle_cost(s, wl.weights, wl.q, wl.p, "softmin", 0.02, waypoints=wps)
+    ec = metrics.rel_err_scalar(c.cpu().numpy()[wps], c_ref).max()
+    egc = metrics.rel_err_vector(gc.cpu().numpy()[wps], g_ref).max()
+    print(f"fp32 full-size soft-min cost err {ec:.3e} grad err {egc:.3e}")
+    assert ec <= TOL
+    assert egc <= TOL + 4 * np.abs(f_ref).max() * 1e-6 / 0.02

@@ -93,3 +93,26 @@ def test_noalloc_rejects_requests_beyond_its_array():
                                          None)
     assert rc == g._lib.GCDF_EINVAL
     assert "scratch" in g.last_error()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_noalloc_after_a_larger_call_with_other_values(prec):
+    """The shared array keeps what the previous call left in it.  A larger call
+    with other inputs and another reduction fills more of the array with other
+    values first; the checked call must still match gcdf_collision_cost, which
+    shows that it writes every word it reads."""
+    torch = need_gpu()
+    g = lib()
+    wl = synth.box_scene(n_waypoints=40, n_points=3000)
+    s = wl.shape
+    net = g.create_net(s.n_dof, s.hidden, s.n_layers, wl.weights, prec)
+    q, p = to_dev(torch, wl.q), to_dev(torch, wl.p)
+    big_q = to_dev(torch, random_traj(300, 9, 77, -5, 5))
+    big_p = to_dev(torch, synth.uniform_points(synth.SplitMix64(78), 5000, [-5, -5, 0], [5, 5, 2]))
+    ref = [x.cpu().numpy() for x in g.collision_cost(net, q, p, "softmin", 0.02)]
+    _noalloc(g, torch, net, big_q, big_p, "hinge", 0.3)
+    torch.cuda.synchronize()
+    got = [x.cpu().numpy() for x in _noalloc(g, torch, net, q, p, "softmin", 0.02)]
+    assert metrics.rel_err_scalar(got[0], ref[0]).max() <= TOL
+    assert metrics.rel_err_vector(got[1], ref[1]).max() <= TOL
+    assert np.array_equal(got[2], ref[2])
