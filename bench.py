@@ -455,6 +455,8 @@ def _kernel_ms(g, torch, net, fn, reps, flush=None):
         if flush is not None:
             flush.fill_(1.0)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()  # PyTorch creates the CUDA event on its first record
+        b.record()
         g.set_profile_events(net, a, b)
         fn()
         torch.cuda.synchronize()

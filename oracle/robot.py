@@ -103,6 +103,37 @@ class MobileArm:
         return np.array(A), np.array(B), np.array(R)
 
 
+    def capsules_batch(self, Q: np.ndarray):
+        """capsules() for K configurations at once: A, B (K, C, 3) and R (C,).
+        The same forward kinematics, with the rotations as (K, 3, 3) stacks."""
+        Q = np.asarray(Q, dtype=np.float64).reshape(-1, self.n_dof)
+        K = Q.shape[0]
+        tb = np.stack([Q[:, 0], Q[:, 1], np.zeros(K)], axis=1)
+        rot = _rot_batch("z", Q[:, 2])
+        A = [tb + np.array([0.0, 0.0, self.base_z[0]])]
+        B = [tb + np.array([0.0, 0.0, self.base_z[1]])]
+        pos = tb + rot @ np.asarray(self.mount, dtype=np.float64)
+        for k, ax in enumerate(self.axes):
+            rot = rot @ _rot_batch(ax, Q[:, 3 + k])
+            nxt = pos + self.offsets[k] * rot[:, :, 2]
+            A.append(pos)
+            B.append(nxt)
+            pos = nxt
+        R = np.array([self.base_radius] + list(self.radii))
+        return np.stack(A, axis=1), np.stack(B, axis=1), R
+
+
+def _rot_batch(axis: str, a: np.ndarray) -> np.ndarray:
+    """rot_z / rot_y for an array of angles: (K, 3, 3)."""
+    c, s = np.cos(a), np.sin(a)
+    o, z = np.ones_like(a), np.zeros_like(a)
+    if axis == "z":
+        rows = [[c, -s, z], [s, c, z], [z, z, o]]
+    else:
+        rows = [[c, z, s], [z, o, z], [-s, z, c]]
+    return np.stack([np.stack(r, axis=-1) for r in rows], axis=-2)
+
+
 def mobile_arm_7() -> MobileArm:
     """10-DOF variant: a seventh (y) joint before the last link."""
     return MobileArm(axes=("z", "y", "y", "z", "y", "y", "z"),
@@ -147,6 +178,15 @@ def sdf(robot, p: np.ndarray, q: np.ndarray) -> float:
     A, B, R = robot.capsules(q)
     d = segment_distance(np.asarray(p, dtype=np.float64)[None, :], A, B) - R
     return float(np.min(d))
+
+
+def sdf_batch(robot, p: np.ndarray, Q: np.ndarray) -> np.ndarray:
+    """sdf() of one point p for K configurations Q (K, n) at once (robots
+    with capsules_batch); equal to sdf() up to the rounding of the stacked
+    rotation products."""
+    A, B, R = robot.capsules_batch(Q)
+    d = segment_distance(np.asarray(p, dtype=np.float64)[None, None, :], A, B) - R[None, :]
+    return np.min(d, axis=1)
 
 
 # ---------------------------------------------------------------------------
@@ -198,6 +238,80 @@ def sample_zero_level_set(robot, p, starts: np.ndarray, dirs: np.ndarray,
         if z is not None:
             out.append(z)
     return np.array(out).reshape(-1, robot.n_dof)
+
+
+def sample_zero_level_set_batch(robot, p, starts: np.ndarray, dirs: np.ndarray,
+                                t_max: float = 2.0, n_steps: int = 64, tol: float = 1e-12,
+                                max_iter: int = 200) -> np.ndarray:
+    """sample_zero_level_set with every line marched and bisected at once
+    (robots with capsules_batch): the same march of n_steps points per line,
+    the first sign change (or an exact zero) of f_s, bisection on the sign
+    until |f_s| < tol, and the opposite direction for lines that never
+    change sign.  Returns (K', n) in the order of the starts."""
+    starts = np.asarray(starts, dtype=np.float64)
+    dirs = np.asarray(dirs, dtype=np.float64)
+    K, n = starts.shape
+    found = np.zeros((K, n))
+    ok = np.zeros(K, dtype=bool)
+    for sgn in (1.0, -1.0):
+        todo = np.nonzero(~ok)[0]
+        if todo.size == 0:
+            break
+        q0, u = starts[todo], sgn * dirs[todo]
+        ts = t_max * np.arange(n_steps + 1) / n_steps          # t = 0 (start), then the march
+        pts = q0[:, None, :] + ts[None, :, None] * u[:, None, :]
+        S = sdf_batch(robot, p, pts.reshape(-1, n)).reshape(todo.size, n_steps + 1)
+        pos = S > 0
+        change = np.zeros_like(S, dtype=bool)
+        change[:, 1:] = (pos[:, 1:] != pos[:, :-1]) | (S[:, 1:] == 0.0)
+        change[:, 0] = S[:, 0] == 0.0
+        hit = change.any(axis=1)
+        k = np.argmax(change, axis=1)
+        exact = hit & (S[np.arange(todo.size), k] == 0.0)
+        t_hit = np.where(exact, ts[k], 0.0)
+        # bisection on [t_{k-1}, t_k] for the lines whose sign changed
+        bis = hit & ~exact
+        t_lo = np.where(bis, ts[np.maximum(k - 1, 0)], 0.0)
+        t_hi = np.where(bis, ts[k], 0.0)
+        s_lo = np.where(bis, S[np.arange(todo.size), np.maximum(k - 1, 0)], 1.0)
+        tm = 0.5 * (t_lo + t_hi)
+        active = bis.copy()
+        for _ in range(max_iter):
+            if not active.any():
+                break
+            ia = np.nonzero(active)[0]
+            tm[ia] = 0.5 * (t_lo[ia] + t_hi[ia])
+            sm = sdf_batch(robot, p, q0[ia] + tm[ia, None] * u[ia])
+            done = (np.abs(sm) < tol) | ((t_hi[ia] - t_lo[ia]) < 1e-15)
+            same = (sm > 0) == (s_lo[ia] > 0)
+            upd_lo = ~done & same
+            upd_hi = ~done & ~same
+            t_lo[ia[upd_lo]] = tm[ia[upd_lo]]
+            s_lo[ia[upd_lo]] = sm[upd_lo]
+            t_hi[ia[upd_hi]] = tm[ia[upd_hi]]
+            active[ia[done]] = False
+        tm[active] = 0.5 * (t_lo[active] + t_hi[active])
+        t_fin = np.where(exact, t_hit, tm)
+        found[todo[hit]] = q0[hit] + t_fin[hit, None] * u[hit]
+        ok[todo[hit]] = True
+    return found[ok].reshape(-1, n)
+
+
+def gcdf_label_batch(robot, p, Qs: np.ndarray, Z: np.ndarray, m_diag=None):
+    """gcdf_label for configurations Qs (S, n) at once: f (S,), grad (S, n) and
+    the two smallest distances (S, 2)."""
+    Qs = np.asarray(Qs, dtype=np.float64)
+    m = np.ones(Qs.shape[1]) if m_diag is None else np.asarray(m_diag, dtype=np.float64)
+    diff = Qs[:, None, :] - Z[None, :, :]
+    d = np.sqrt(np.sum(diff * diff * m[None, None, :], axis=2))
+    k = np.argmin(d, axis=1)
+    sgn = np.where(sdf_batch(robot, p, Qs) >= 0, 1.0, -1.0)
+    f = sgn * d[np.arange(Qs.shape[0]), k]
+    dk = diff[np.arange(Qs.shape[0]), k]
+    safe = np.where(f != 0, f, 1.0)
+    grad = np.where((f != 0)[:, None], m[None, :] * dk / safe[:, None], 0.0)
+    two = np.sort(d, axis=1)[:, :2] if d.shape[1] >= 2 else np.repeat(d, 2, axis=1)
+    return f, grad, two
 
 
 def gcdf_label(robot, p, q, Z: np.ndarray, m_diag=None):
