@@ -579,9 +579,20 @@ def _run_server(g, nets, params, reqs, budget, max_active, max_queued):
                     first = r["submit_s"] if first is None else min(first, r["submit_s"])
                     last = max(last, r["done_s"])
             time.sleep(0.0005)
+        st = srv.stats()
     finally:
         srv.close()
-    return _lat(lat, last - (first or 0.0), len(lat), rejected)
+    out = _lat(lat, last - (first or 0.0), len(lat), rejected)
+    if st["steps"]:
+        k = st["steps"]
+        out["worker_loop"] = {
+            "steps": k, "mean_batch": st["active_sum"] / k,
+            "step_device_ms": 1e3 * st["step_device_s"] / k,
+            "step_host_ms": 1e3 * st["step_host_s"] / k,
+            "pass_ms": 1e3 * st["pass_s"] / k,
+            "host_overhead_ms_per_step": 1e3 * (st["pass_s"] - st["step_device_s"]) / k,
+            "host_overhead_frac": (st["pass_s"] - st["step_device_s"]) / st["pass_s"] if st["pass_s"] > 0 else None}
+    return out
 
 
 def _run_sequential(g, torch, nets, params, reqs):
@@ -649,6 +660,12 @@ def run_serve(args):
     line = {
         "metric": "served plan p50/p99 latency and throughput", "unit": "s / requests per s",
         "n_gpus": 1, "data": "synthetic",
+        "summary": {"mix": "A", "served_p50_s": served["p50_s"], "served_p99_s": served["p99_s"],
+                    "served_rps": served["throughput_rps"], "fp32_per_request_p50_s": fp32_seq["p50_s"],
+                    "fp32_per_request_p99_s": fp32_seq["p99_s"],
+                    "fp32_per_request_rps": fp32_seq["throughput_rps"],
+                    "served_beats_fp32_per_request": bool(served["throughput_rps"] >= fp32_seq["throughput_rps"]
+                                                          and served["p99_s"] <= fp32_seq["p99_s"])},
         "config": {"arrivals": "Poisson", "steps_per_request": 50, "robots": "9- and 10-DOF, 4 x 256 SiLU",
                    "budget_bytes": budget,
                    "mix_A": {"rate_rps": args.serve_rate, "seconds": args.serve_seconds, "requests": len(reqs_a),
@@ -880,7 +897,7 @@ def main():
     ap.add_argument("--serve", action="store_true", help="served-planning latency benchmark instead")
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
-    ap.add_argument("--overload-seconds", type=float, default=1.0)
+    ap.add_argument("--overload-seconds", type=float, default=10.0)
     ap.add_argument("--plan", action="store_true", help="batched trajectory-optimisation benchmark instead")
     ap.add_argument("--plan-problems", type=int, default=64)
     ap.add_argument("--aux", action="store_true", help="partition / Jacobian / projection kernels instead")

@@ -478,6 +478,29 @@ GCDF_API int gcdf_plan_poll(gcdf_server *server, uint64_t ticket, gcdf_plan_resu
 /* Server clock in seconds (the clock of gcdf_plan_result). */
 GCDF_API double gcdf_server_clock(gcdf_server *server);
 
+/* Counters of a server's worker loop since creation (no counterpart in the
+ * paper: they show what the host-driven loop costs).  A step is one
+ * optimiser step of every admitted request.
+ *   steps          steps run
+ *   step_device_s  device time of the steps' launches (CUDA events around them)
+ *   step_host_s    host time from a step's first launch to the return of the
+ *                  synchronisation that ends it (includes step_device_s)
+ *   pass_s         host time of the loop passes that ran a step, including
+ *                  admission, rebuilding the step arrays and reading back
+ *                  finished requests (includes step_host_s)
+ *   active_sum     sum over steps of the admitted requests (mean batch =
+ *                  active_sum / steps) */
+typedef struct gcdf_server_stats {
+  uint64_t steps;
+  double step_device_s;
+  double step_host_s;
+  double pass_s;
+  uint64_t active_sum;
+} gcdf_server_stats;
+
+/* Copy the counters above.  Errors: EINVAL (NULL argument). */
+GCDF_API int gcdf_server_stats_get(gcdf_server *server, gcdf_server_stats *out);
+
 /* Stop the server thread (after the step in progress) and free its memory.
  * Unfinished requests are dropped.  NULL is a no-op. */
 GCDF_API int gcdf_server_destroy(gcdf_server *server);

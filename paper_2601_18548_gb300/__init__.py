@@ -324,6 +324,13 @@ class Server:
     def clock(self) -> float:
         return float(self._lib.gcdf_server_clock(self.handle))
 
+    def stats(self) -> dict:
+        """gcdf_server_stats_get: the worker loop's step counters."""
+        st = _lib.ServerStats()
+        _lib.check(self._lib.gcdf_server_stats_get(self.handle, ctypes.byref(st)))
+        return {"steps": int(st.steps), "step_device_s": st.step_device_s, "step_host_s": st.step_host_s,
+                "pass_s": st.pass_s, "active_sum": int(st.active_sum)}
+
     def close(self):
         if getattr(self, "handle", None) and self.handle.value:
             self._lib.gcdf_server_destroy(self.handle)

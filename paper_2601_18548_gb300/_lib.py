@@ -56,6 +56,11 @@ class PlanResult(ctypes.Structure):
                 ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint64), ("step_device_s", ctypes.c_double), ("step_host_s", ctypes.c_double),
+                ("pass_s", ctypes.c_double), ("active_sum", ctypes.c_uint64)]
+
+
 SIGNATURES = {
     "gcdf_weight_count": (ctypes.c_size_t, [ctypes.POINTER(NetDesc)]),
     "gcdf_create_net": (_i, [ctypes.POINTER(NetDesc), _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
@@ -81,6 +86,7 @@ SIGNATURES = {
     "gcdf_plan_submit": (_i, [_vp, ctypes.POINTER(PlanRequest), ctypes.POINTER(ctypes.c_uint64)]),
     "gcdf_plan_poll": (_i, [_vp, ctypes.c_uint64, ctypes.POINTER(PlanResult)]),
     "gcdf_server_clock": (ctypes.c_double, [_vp]),
+    "gcdf_server_stats_get": (_i, [_vp, ctypes.POINTER(ServerStats)]),
     "gcdf_plan_request_bytes": (ctypes.c_size_t, [_vp, _i, _i]),
     "gcdf_server_destroy": (_i, [_vp]),
     "gcdf_last_error": (ctypes.c_char_p, []),

@@ -97,6 +97,8 @@ struct gcdf_server {
   std::map<uint64_t, std::unique_ptr<Req>> done;
   std::vector<Group> groups;                // worker thread only
   bool dirty = false;                       // worker thread only
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;  // around each step's launches (worker thread only)
+  gcdf_server_stats stats{};                // under mu
 
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -268,7 +270,18 @@ void worker_loop(gcdf_server* s) {
   const gcdf_plan_params prm = s->desc.params;
   const int evals = prm.iterations + 1;
   std::vector<Req*> fresh;
+  auto pass_start = std::chrono::steady_clock::now();
+  bool stepped = false;
   for (;;) {
+    {
+      const auto now = std::chrono::steady_clock::now();
+      if (stepped) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stats.pass_s += std::chrono::duration<double>(now - pass_start).count();
+      }
+      pass_start = now;
+      stepped = false;
+    }
     fresh.clear();
     {
       std::unique_lock<std::mutex> lk(s->mu);
@@ -336,13 +349,29 @@ void worker_loop(gcdf_server* s) {
         if (build_group(s, g, prm)) return;
       s->dirty = false;
     }
-    // 3. one step per group
+    // 3. one step per group; host time from the first launch to the return of
+    // the synchronisation against the device time between two events
+    const auto h0 = std::chrono::steady_clock::now();
+    cudaError_t e = cudaEventRecord(s->ev_a, s->stream);
+    if (e != cudaSuccess) { fail_server(s, GCDF_ECUDA, "cudaEventRecord", e); return; }
     for (Group& g : s->groups) {
       const int rc = plan_step(g.net, g.ps, g.a, s->consts, prm.delta, s->stream);
       if (rc) { fail_server(s, rc, "plan step", cudaGetLastError()); return; }
     }
-    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if ((e = cudaEventRecord(s->ev_b, s->stream)) != cudaSuccess) { fail_server(s, GCDF_ECUDA, "cudaEventRecord", e); return; }
+    e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) { fail_server(s, GCDF_ECUDA, "step", e); return; }
+    {
+      const double host_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - h0).count();
+      float dev_ms = 0.f;
+      cudaEventElapsedTime(&dev_ms, s->ev_a, s->ev_b);
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->stats.steps += 1;
+      s->stats.step_host_s += host_s;
+      s->stats.step_device_s += 1e-3 * dev_ms;
+      s->stats.active_sum += (uint64_t)s->active.size();
+    }
+    stepped = true;
     // 4. finished requests
     std::vector<Req*> fin;
     for (auto& up : s->active)
@@ -397,7 +426,11 @@ int gcdf_server_create(const gcdf_server_desc* desc, gcdf_server** out) {
   s->t0 = std::chrono::steady_clock::now();
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&s->ev_a);
+  if (e == cudaSuccess) e = cudaEventCreate(&s->ev_b);
   if (e != cudaSuccess) {
+    if (s->ev_a) cudaEventDestroy(s->ev_a);
+    if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return set_error(GCDF_ECUDA, "server stream: %s", cudaGetErrorString(e));
   }
@@ -471,6 +504,14 @@ int gcdf_plan_poll(gcdf_server* s, uint64_t ticket, gcdf_plan_result* res) {
 
 double gcdf_server_clock(gcdf_server* s) { return s ? s->now() : 0.0; }
 
+int gcdf_server_stats_get(gcdf_server* s, gcdf_server_stats* out) {
+  if (!s || !out) return set_error(GCDF_EINVAL, "server or out is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->stats;
+  clear_error();
+  return GCDF_OK;
+}
+
 size_t gcdf_plan_request_bytes(gcdf_net* net, int n_waypoints, int n_points) {
   if (!net || n_waypoints < 0 || n_points < 0) return 0;
   return request_bytes(net, n_waypoints, n_points, net_n_dof(net));
@@ -489,6 +530,8 @@ int gcdf_server_destroy(gcdf_server* s) {
   for (auto& r : s->active)
     if (r->dmem) cudaFreeAsync(r->dmem, s->stream);
   cudaStreamSynchronize(s->stream);
+  cudaEventDestroy(s->ev_a);
+  cudaEventDestroy(s->ev_b);
   cudaStreamDestroy(s->stream);
   delete s;
   return GCDF_OK;

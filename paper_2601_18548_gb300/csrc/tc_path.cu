@@ -287,8 +287,11 @@ __device__ __forceinline__ void warp_partial_part(int mode, float param, bool va
     if (valid && f != f) v0 = f;
   }
   float v[4];
+  // HINGE selects the active rows' gradients (an inactive row adds nothing,
+  // not 0 x its gradient: a NaN or infinite gradient of an inactive row must
+  // not reach the sum)
 #pragma unroll
-  for (int m = 0; m < 3; ++m) v[m] = (d0 + 4 * m < n) ? wgt * dqm[m] : 0.f;
+  for (int m = 0; m < 3; ++m) v[m] = (d0 + 4 * m < n && (mode == kSoftmin || wgt != 0.f)) ? wgt * dqm[m] : 0.f;
   v[3] = (mode == kSoftmin) ? wgt : v0;
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1)

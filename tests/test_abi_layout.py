@@ -15,7 +15,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 STRUCTS = {"NetDesc": "gcdf_net_desc", "FitDesc": "gcdf_fit_desc", "PlanParams": "gcdf_plan_params",
            "PlanProblem": "gcdf_plan_problem", "ServerDesc": "gcdf_server_desc",
-           "PlanRequest": "gcdf_plan_request", "PlanResult": "gcdf_plan_result"}
+           "PlanRequest": "gcdf_plan_request", "PlanResult": "gcdf_plan_result",
+           "ServerStats": "gcdf_server_stats"}
 
 
 def _c_layout():
