@@ -134,7 +134,8 @@ GCDF_API int gcdf_destroy_net(gcdf_net *net);
  *   shift  (n_waypoints, 2) or NULL: per-waypoint base shift b_i.
  *   f      (n_pairs,)        out: f for pair k in stacked order
  *                            (dense: k = i * n_points + j)
- *   grad   (n_pairs, n) or NULL  out: df/dq for pair k
+ *   grad   (n_pairs, n) or NULL  out: df/dq for pair k; NULL runs the forward
+ *          layers alone (no reverse sweep: about half the work)
  * n_waypoints == 0 or n_pairs == 0 enqueues nothing and returns GCDF_OK.
  */
 GCDF_API int gcdf_query(gcdf_net *net, const float *q, int n_waypoints,
@@ -200,6 +201,22 @@ GCDF_API int gcdf_collision_cost_noalloc(gcdf_net *net, const float *q, int n_wa
                                          const int *part_idx, int n_pairs, const float *shift,
                                          int reduction, float param, float *cost, float *grad,
                                          int *argmin, gcdf_stream_t stream);
+
+/*
+ * HINGE and MIN need df/dq only where the reduction uses it: HINGE on the pairs
+ * with f < delta (the active set of the l1 penalty, Eq. 12), MIN at each
+ * waypoint's first minimising entry.  With the active set on (the default for
+ * every net), gcdf_collision_cost and gcdf_plan_solve / the planning server
+ * evaluate HINGE and MIN in two passes: every pair's value without the reverse
+ * sweep, then value and gradient of the active pairs alone (NaN values count
+ * as active, so they still reach the cost).  The cost, gradient and argmin are
+ * those of the one-pass reduction; the HINGE sums are added in another order.
+ * Temporaries grow by 8 bytes per pair (the values and the active lists).
+ * gcdf_collision_cost_noalloc always runs in one pass.  enable 0 selects the
+ * one-pass evaluation.  Not thread-safe against calls in flight on the same
+ * net.  Errors: EINVAL (net NULL).
+ */
+GCDF_API int gcdf_set_active_set(gcdf_net *net, int enable);
 
 /*
  * Device-side status of a net's kernels since the last call: 0 when every

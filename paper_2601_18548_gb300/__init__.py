@@ -206,6 +206,12 @@ def set_profile_events(net: Net, start=None, stop=None) -> None:
     _lib.check(_lib.load().gcdf_set_profile_events(net.handle, a, b))
 
 
+def set_active_set(net: Net, enable: bool) -> None:
+    """gcdf_set_active_set: HINGE / MIN in two passes (values, then the active
+    pairs' gradients) when enabled (the default), in one pass otherwise."""
+    _lib.check(_lib.load().gcdf_set_active_set(net.handle, 1 if enable else 0))
+
+
 def selftest_wait_expiry(net: Net, limit_cycles: int = 200000):
     """gcdf_selftest_wait_expiry: [producer wait expired, epilogue wait expired,
     abort flag raised] of a probe whose waits can never complete."""

@@ -70,6 +70,7 @@ SIGNATURES = {
     "gcdf_collision_cost_noalloc": (_i, [_vp, _vp, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _f, _vp, _vp, _vp, _vp]),
     "gcdf_device_status": (_i, [_vp, ctypes.POINTER(_i)]),
     "gcdf_set_profile_events": (_i, [_vp, _vp, _vp]),
+    "gcdf_set_active_set": (_i, [_vp, _i]),
     "gcdf_selftest_wait_expiry": (_i, [_vp, ctypes.c_longlong, ctypes.POINTER(_i)]),
     "gcdf_diag_fp32_fma": (ctypes.c_longlong, [_i, _i, _i, _vp, _vp]),
     "gcdf_project": (_i, [_vp, _vp, _i, _vp, _i, _vp, _vp, _i, _vp, _vp, _vp, _vp]),

@@ -185,21 +185,37 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
     ok = __all_sync(0xffffffffu, ok);
     if (ok) {
       ptx::tc_fence_after();
-      const int row = tm * 2 * kRowsA + (int)rank * kRowsA + q * 32 + lane;
-      float* crow = a.C + (long long)blockIdx.y * a.zstride + (long long)row * a.ldc;
+      // Each 32 x 32 block (lane = row after tcgen05.ld) is transposed through
+      // shared memory, so that each store instruction writes 32 consecutive
+      // floats of one row of C (one 128-byte line) instead of one float in 32
+      // rows.  The operand ring is idle once the accumulator is complete (every
+      // MMA, and so every TMA load, has finished): warp q uses 33 x 32 floats
+      // of it (row stride 33: conflict-free in both directions).
+      float* tile = reinterpret_cast<float*>(gbase) + q * (32 * 33);
+      const int row0 = tm * 2 * kRowsA + (int)rank * kRowsA + q * 32;
+      float* cz = a.C + (long long)blockIdx.y * a.zstride;
       const int n0 = tn * kTileN;
 #pragma unroll 1
       for (int c0 = 0; c0 < kTileN; c0 += 32) {
         uint32_t v[32];
         ptx::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
         ptx::tmem_wait_ld();
-        if (row < a.M) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = n0 + c0 + j;
-            if (n < a.N) crow[n] = a.accumulate ? crow[n] + __uint_as_float(v[j]) : __uint_as_float(v[j]);
+        for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(v[j]);
+        __syncwarp();
+        const int n = n0 + c0 + lane;
+        if (n < a.N) {
+#pragma unroll 4
+          for (int r = 0; r < 32; ++r) {
+            const int row = row0 + r;
+            if (row < a.M) {
+              float* c = cz + (long long)row * a.ldc + n;
+              const float x = tile[r * 33 + lane];
+              *c = a.accumulate ? *c + x : x;
+            }
           }
         }
+        __syncwarp();
       }
     }
   }

@@ -11,6 +11,8 @@
 //   g_L = w_o * s'(z_L),  g_{l-1} = (W_l^T g_l) * s'(z_{l-1}),
 //   df/denc = W_1q^T g_1,  then the sin/cos chain rule.
 //
+// A query without a gradient output runs the forward layers only.
+//
 // Layout.  A tile is TP = 8192 / H pairs of one waypoint.  256 threads; thread
 // (pg, fg) owns pairs 4pg..4pg+3 and features fg + G f (f = 0..7, G = H / 8);
 // a warp spans 4 pair groups and 8 feature groups.
@@ -109,7 +111,10 @@ fp32_fused_kernel(const WorkDesc w, const Fp32Weights fw) {
   const int pg = (warp / (C::G / 8)) * 4 + (lane >> 3);
   const int fg = (warp % (C::G / 8)) * 8 + (lane & 7);
   const int L = fw.L;
-  const int nseq = 2 * (L - 1) * C::NCH;  // chunks per tile
+  // value-only query (no gradient output): the forward layers alone
+  const bool fwd_only = (w.mode == kQuery && w.g_out == nullptr);
+  const int n_phases = fwd_only ? (L - 1) : 2 * (L - 1);
+  const int nseq = n_phases * C::NCH;  // chunks per tile
   const int n = w.n_dof;
   const int d_q = fw.d_q;
 
@@ -169,7 +174,7 @@ fp32_fused_kernel(const WorkDesc w, const Fp32Weights fw) {
 
     // ---- forward layers 2..L and reverse sweep L..2 ---------------------------
     float fsum[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int ph = 0; ph < 2 * (L - 1); ++ph) {
+    for (int ph = 0; ph < n_phases; ++ph) {
       float acc[4][8];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
@@ -267,7 +272,7 @@ fp32_fused_kernel(const WorkDesc w, const Fp32Weights fw) {
     __syncthreads();  // act holds g_1 [c][pair]; fpart complete
 
     // ---- df/denc = W_1q^T g_1 ------------------------------------------------
-    for (int o = tid; o < C::TP * d_q; o += 256) {
+    for (int o = tid; o < (fwd_only ? 0 : C::TP * d_q); o += 256) {
       const int pair = o % C::TP;
       const int d = o / C::TP;
       const float* wcol = fw.W1 + 3 + d;
@@ -294,9 +299,11 @@ fp32_fused_kernel(const WorkDesc w, const Fp32Weights fw) {
         fval = s;
         const float* de = denc + pair * 24;
         const float* tr = w.trig + (size_t)wp * 2 * w.n_ang;
-        dq[0] = de[0];
-        dq[1] = de[1];
-        for (int a = 0; a < w.n_ang; ++a) dq[2 + a] = tr[2 * a + 1] * de[2 + 2 * a] - tr[2 * a] * de[3 + 2 * a];
+        if (!fwd_only) {
+          dq[0] = de[0];
+          dq[1] = de[1];
+          for (int a = 0; a < w.n_ang; ++a) dq[2 + a] = tr[2 * a + 1] * de[2 + 2 * a] - tr[2 * a] * de[3 + 2 * a];
+        }
         if (valid) pair_at(w, wp, start + pair, j, k);
       }
       if (w.mode == kQuery) {

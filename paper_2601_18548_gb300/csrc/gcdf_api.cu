@@ -37,6 +37,7 @@ struct gcdf_net {
   float* tc_w1p;
   TcWeights tcw;     // tensor maps and pointers for the tensor-core kernel
   int* err_word;     // device status word written by bounded waits
+  int active_set;    // HINGE / MIN: value-only pass, then gradients of the active pairs only
   float bout;
   size_t off_W1, off_b1, off_wout;
   cudaEvent_t prof_start, prof_stop;  // optional events around the fused kernel
@@ -257,9 +258,54 @@ int run(gcdf_net* net, WorkDesc& w, const float* shift, Temps& tmp, cudaStream_t
   return GCDF_OK;
 }
 
+// HINGE / MIN in two passes: f of every pair (value-only, no reverse sweep),
+// the per-waypoint active lists (support.cu), then the fused value + gradient
+// pass over those lists alone.  The merge of the second pass gives the cost,
+// gradient and argmin of the full reduction (the pairs left out add exactly
+// zero); only the order of the HINGE sums differs from the one-pass result.
+int reduce_active(gcdf_net* net, WorkDesc& w, const float* shift, float* cost, float* grad, int* argmin,
+                  cudaStream_t s) {
+  Temps tmp(s);
+  cudaError_t e;
+  float* fv = nullptr;
+  int *cnt = nullptr, *nact = nullptr, *amin = nullptr, *off2 = nullptr, *idx2 = nullptr;
+  const size_t cap = w.mode == kHinge ? (size_t)w.n_pairs : (size_t)w.N;
+  if ((e = tmp.get((void**)&fv, (size_t)w.n_pairs * sizeof(float))) ||
+      (e = tmp.get((void**)&cnt, (size_t)w.N * sizeof(int))) || (e = tmp.get((void**)&nact, (size_t)w.N * sizeof(int))) ||
+      (e = tmp.get((void**)&amin, (size_t)w.N * sizeof(int))) ||
+      (e = tmp.get((void**)&off2, (size_t)(w.N + 1) * sizeof(int))) || (e = tmp.get((void**)&idx2, cap * sizeof(int))))
+    return cuda_fail(e, "cudaMallocAsync");
+  // pass 1: every pair's value
+  WorkDesc w1 = w;
+  w1.mode = kQuery;
+  w1.f_out = fv;
+  w1.g_out = nullptr;
+  int rc = run(net, w1, shift, tmp, s);
+  if (rc) return rc;
+  if ((e = launch_active_lists(w, fv, cnt, nact, amin, off2, idx2, s))) return cuda_fail(e, "active-list launch");
+  // pass 2: value + gradient over the active lists (an upper bound of their
+  // length sizes the tiles and records; the kernels read the exact count)
+  WorkDesc w2 = w;
+  w2.offsets = off2;
+  w2.idx = idx2;
+  w2.point_base = nullptr;
+  w2.tile_start = nullptr;
+  w2.tiles_per_wp = 0;
+  w2.n_pairs = (int)cap;
+  w2.n_tiles = (int)(((long long)cap + w2.tile - 1) / w2.tile + w.N);
+  Partial* parts = nullptr;
+  if ((e = tmp.get((void**)&parts, (size_t)w2.n_tiles * sizeof(Partial)))) return cuda_fail(e, "cudaMallocAsync");
+  w2.partials = parts;
+  if ((rc = run(net, w2, shift, tmp, s))) return rc;
+  if ((e = launch_merge(w2, w2.N, cost, grad, argmin, s))) return cuda_fail(e, "merge launch");
+  return GCDF_OK;
+}
+
 // Fused pass plus per-waypoint merge for a validated WorkDesc (mode, param set).
 int reduce_call(gcdf_net* net, WorkDesc& w, const float* shift, float* cost, float* grad, int* argmin,
                 cudaStream_t s) {
+  if (net->active_set && w.n_pairs > 0 && (w.mode == kHinge || w.mode == kMin))
+    return reduce_active(net, w, shift, cost, grad, argmin, s);
   Temps tmp(s);
   cudaError_t e;
   Partial* parts = nullptr;
@@ -305,7 +351,10 @@ int net_device(const gcdf_net* net) { return net->device; }
 size_t net_step_bytes_per_row(const gcdf_net* net, int M) {
   const int tile = net->precision == GCDF_FP32 ? fp32_tile_pairs(net->H) : tc_tile_pairs();
   const size_t tiles = (size_t)(M + tile - 1) / tile + 1;
-  return (size_t)net->H * 4 + (size_t)2 * (net->n_dof - 2) * 4 + 4 + tiles * sizeof(Partial);
+  // + with active sets: every pair's value, its list entry, the per-row
+  // counters and a second set of tile records
+  const size_t act = net->active_set ? (size_t)M * 8 + 20 + tiles * sizeof(Partial) : 0;
+  return (size_t)net->H * 4 + (size_t)2 * (net->n_dof - 2) * 4 + 4 + tiles * sizeof(Partial) + act;
 }
 
 // Collision cost over range lists: waypoint i uses points point_base[i] ..
@@ -376,6 +425,7 @@ int gcdf_create_net(const gcdf_net_desc* desc, const float* weights_host, size_t
   n->off_b1 = (size_t)n->H * n->d_in;
   n->off_wout = need - 1 - n->H;
   n->bout = weights_host[need - 1];
+  n->active_set = 1;
   if ((rc = dev_alloc_copy(&n->w_dev, weights_host, need))) { free_net(n); return rc; }
   {
     const int zero = 0;
@@ -471,6 +521,13 @@ int gcdf_device_status(gcdf_net* net, int* status) {
   const int zero = 0;
   if ((e = cudaMemcpy(net->err_word, &zero, sizeof(int), cudaMemcpyHostToDevice))) return cuda_fail(e, "cudaMemcpy");
   *status = v;
+  g_err[0] = 0;
+  return GCDF_OK;
+}
+
+int gcdf_set_active_set(gcdf_net* net, int enable) {
+  if (!net) return fail(GCDF_EINVAL, "net is NULL");
+  net->active_set = enable ? 1 : 0;
   g_err[0] = 0;
   return GCDF_OK;
 }

@@ -192,6 +192,11 @@ cudaError_t launch_prep(const WorkDesc& w, const float* W1, const float* b1, int
 cudaError_t launch_tile_map(const int* offsets, int N, int tile, int* tile_start, cudaStream_t s);
 cudaError_t launch_merge(const WorkDesc& w, int n_waypoints, float* cost, float* grad, int* argmin,
                          cudaStream_t s);
+// Active lists of a HINGE / MIN reduction (w.mode, w.param) from the values f
+// of every list position of w: out_off (N + 1) and point indices out_idx (at
+// most w.n_pairs, or N for MIN); cnt, nact, amin (N) are temporaries.
+cudaError_t launch_active_lists(const WorkDesc& w, const float* f, int* cnt, int* nact, int* amin, int* out_off,
+                                int* out_idx, cudaStream_t s);
 
 struct Fp32Weights {
   const float* BF;   // (L-1) x [H][H]: forward operand, row = input feature, columns permuted

@@ -391,7 +391,17 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
   const int warp = tid >> 5;
   const int lane = tid & 31;
   const int L = tw.L;
-  const int n_steps = 2 * (L - 1);  // weight steps per tile (forward then reverse)
+  // A query without a gradient output (value-only) runs the forward steps
+  // alone: no stash, no reverse steps, no input-Jacobian chain.
+  const bool fwd = (w.mode == kQuery && w.g_out == nullptr);
+  const int n_steps = fwd ? (L - 1) : 2 * (L - 1);  // weight steps per tile (forward, then reverse)
+  // A-buffer parity: step s of tile `it` reads buffer (tile_par(it) + s) & 1
+  // and its epilogue writes the other one; a tile's first layer goes to
+  // buffer tile_par(it) & 1.  With the full sweep (n_steps even, plus the
+  // input-Jacobian chain on the same buffer as the last reverse step) that is
+  // (it + s) & 1; forward-only tiles continue the alternation across tiles, so
+  // the next tile's first layer never lands in the buffer its last step reads.
+  auto tile_par = [&](int it) -> int { return fwd ? it * (L - 1) : it; };
   const int nj = tw.nj;
   const int ntiles = total_tiles(w);
   // CTA pairs (clusters of 2) take pair tiles round robin; CTA `rank` of the pair
@@ -488,7 +498,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
             for (int pr = 0; pr < 2 && ok; ++pr)
               ok = load_stage(&map_w, pr * 128, row0 + hh * kHalf + (int)rank * kRowsCta, kSlabBytes);
         }
-        for (int pr = 0; pr < 2 && ok; ++pr)  // W_1q^T: nj rows, nj / 2 per CTA
+        for (int pr = 0; pr < 2 && ok && !fwd; ++pr)  // W_1q^T: nj rows, nj / 2 per CTA
           ok = load_stage(&map_j, pr * 128, (int)rank * (nj / 2), (uint32_t)(nj / 2) * 128u);
       }
       // drain (even CTA): the last kStages stages are the only ones that can be
@@ -539,8 +549,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         if (++cst == kStages) { cst = 0; cph ^= 1u; }
       };
       for (int it = 0; it < my_tiles && ok; ++it) {
-        for (int s = 0; s <= n_steps && ok; ++s) {
-          const uint64_t dAbuf = ((it + s) & 1) ? dA1 : dA0;
+        for (int s = 0; s <= (fwd ? n_steps - 1 : n_steps) && ok; ++s) {
+          const uint64_t dAbuf = ((tile_par(it) + s) & 1) ? dA1 : dA0;
           // the input Jacobian df/denc = W_1q^T g_1 goes to TMEM columns [384, 384 + nj):
           // the stash is free by then, so the next tile's first chain need not wait for it
           const bool jstep = (s == n_steps);
@@ -673,7 +683,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     };
     // h_1 = s(A_i + W_1p p) for this row and the warp's 64 columns -> A buffer (tile parity)
     auto first_layer = [&](int it) {
-      const uint32_t abuf = base + ((it & 1) ? kOffA1 : kOffA0);
+      const uint32_t abuf = base + ((tile_par(it) & 1) ? kOffA1 : kOffA0);
       const int c0 = cw;
 #pragma unroll 1
       for (int cc = 0; cc < 64; cc += 16) {
@@ -693,7 +703,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     // then); the tile tail copies it into the A buffer (TMEM -> shared memory, no
     // arithmetic).  Measured: 1.4 % faster with FP16 operands, 1.7 % slower with
     // BF16 ones, where the tile tail computes the first layer itself.
-    const bool early_h1 = kF16 && L == 4;
+    const bool early_h1 = kF16 && L == 4 && !fwd;
     const uint32_t t_h1 = t_lane + 256 + (cw >> 1);
     auto first_layer_tmem = [&]() {
 #pragma unroll 1
@@ -710,7 +720,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       ptx::tmem_wait_st();
     };
     auto first_layer_copy = [&](int it) {
-      const uint32_t abuf = base + ((it & 1) ? kOffA1 : kOffA0);
+      const uint32_t abuf = base + ((tile_par(it) & 1) ? kOffA1 : kOffA0);
       uint32_t v[32];
       ptx::tmem_ld16(t_h1, v);
       ptx::tmem_ld16(t_h1 + 16, v + 16);
@@ -729,7 +739,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       const int cur_wp = wp, cur_start = start, cur_len = len;
       const bool h1_early = early_h1 && it + 1 < my_tiles;
       for (int s = 0; s < n_steps && ok; ++s) {
-        const uint32_t obuf = base + (((it + s + 1) & 1) ? kOffA1 : kOffA0);
+        const uint32_t obuf = base + (((tile_par(it) + s + 1) & 1) ? kOffA1 : kOffA0);
         {
           const int h = hg;
           if (!wait_epi_warp(bar(base, B_ACC0 + h), acc_n & 1u, abort_flag, tw.err)) { ok = false; break; }
@@ -765,10 +775,10 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
                 o[i] = to_operand<kFmt>(hh);
               }
               store8c(obuf, c0 + cc, o);
-              ptx::tmem_st8(t_st + cc / 2, st2);
+              if (!fwd) ptx::tmem_st8(t_st + cc / 2, st2);
             }
             }
-            ptx::tmem_wait_st();
+            if (!fwd) ptx::tmem_wait_st();
           } else if (s == L - 2) {
             // last forward layer: f partial (FP32 sum), g_L = w_o s'(z_L) -> A
             fpart = 0.f;
@@ -795,7 +805,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
                 fpart = fmaf(wo.x, ptx::f16lo(hh), fmaf(wo.y, ptx::f16hi(hh), fpart));
                 o[i] = to_operand<kFmt>(ptx::hmul2(wh[i], s2));
               }
-              store8c(obuf, c0 + cc, o);
+              if (!fwd) store8c(obuf, c0 + cc, o);
             }
             s_f[kq * kTile + row] = fpart;
             ptx::mbar_arrive(bar(base, B_FD));
@@ -837,7 +847,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               store8c(obuf, c0 + cc, o);
             }
           }
-          epi_done(h);
+          // (forward-only: the last step produces no operand, so no MMA waits for it)
+          if (!(fwd && s == n_steps - 1)) epi_done(h);
           if (s == L - 1 && L >= 3) {
             // the first reverse step has read this warp's stash columns of z_{L-1}:
             // recompute 2 s'(z_1) = 2 s'(A_i + W_1p p) into them while the tensor
@@ -863,6 +874,32 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         }
       }
       if (!ok) break;
+
+      if (fwd) {
+        // ---- forward-only tile tail: f of this tile, then the next tile's first
+        // layer.  The output comes first so that every warp has read this tile's
+        // f partials before it releases the next tile's first step (which
+        // rewrites them when L = 2).
+        if (!wait_epi_warp(bar(base, B_FD), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }
+        if (kq == 0 && row < cur_len) {
+          int j;
+          long long k;
+          pair_at(w, cur_wp, cur_start + row, j, k);
+          w.f_out[k] = s_f[row] + s_f[kTile + row] + s_f[2 * kTile + row] + s_f[3 * kTile + row] + tw.bout;
+        }
+        if (it + 1 < my_tiles) {
+          load_tile(it + 1);
+          // the next first layer's buffer was last read by an earlier step, whose
+          // MMAs completed before this step's accumulator; the half-1 wait keeps
+          // both halves' warps one step apart, as in the full sweep
+          if (hg == 0) {
+            if (!wait_epi_warp(bar(base, B_ACC0 + 1), (acc_n - 1u) & 1u, abort_flag, tw.err)) { ok = false; break; }
+            ptx::tc_fence_after();
+          }
+          first_layer(it + 1);
+        }
+        continue;
+      }
 
       // ---- tile tail ------------------------------------------------------------
       if (it + 1 < my_tiles) {
