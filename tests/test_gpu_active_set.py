@@ -119,8 +119,9 @@ def test_hinge_and_min_csr_lists_with_empty_lists_shift_and_nan(prec):
         for kind, param in (("hinge", 0.4), ("min", 0.0)):
             a, b = _both(g, torch, net, q, pts, kind, param, off, idx, shift)
             assert np.array_equal(np.isnan(a[0]), np.isnan(b[0]))
+            assert np.array_equal(np.isinf(a[0]), np.isinf(b[0]))  # MIN over an empty list: +inf
             assert np.array_equal(a[2], b[2])
-            fin = ~np.isnan(a[0])
+            fin = np.isfinite(a[0])
             assert np.all(np.abs(a[0][fin] - b[0][fin]) <= 1e-4 * np.maximum(1.0, np.abs(b[0][fin])))
             empty = np.diff(off) == 0
             assert np.all(a[2][empty] == -1) and np.all(a[1][empty] == 0)
