@@ -407,6 +407,15 @@ struct Ctx {
     cudaError_t e;
     // A(m, k) = A[m sam + k sak]; B as an N x K operand: B(k, n) = B[n sbn + k sbk]
     if ((e = image(A, sam, sak, M, K, sa, ld)) || (e = image(B, sbn, sbk, N, K, sb, ld))) return e;
+    return mm_images(sa, ld, sb, ld, M, N, K, C, ldc, split, accumulate, nullptr);
+  }
+
+  // C (M x N, ldc) = (or +=) A B^T on BF16 images A (M x K, row stride lda) and
+  // B (N x K, ldb), with an optional fused epilogue (not with `split`)
+  cudaError_t mm_images(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B, long long ldb, int M, int N,
+                        int K, float* C, long long ldc, bool split, bool accumulate, const GemmEpilogue* ep) {
+    if (M == 0 || N == 0) return cudaSuccess;
+    cudaError_t e;
     const int kb = tc_gemm_kblock();
     const long long kblocks = (K + kb - 1) / kb;
     const long long tiles = (long long)((M + tc_gemm_tile_m() - 1) / tc_gemm_tile_m()) *
@@ -416,13 +425,14 @@ struct Ctx {
       splits = std::min<long long>((152 + tiles - 1) / tiles, kblocks / 8);
       while (splits > 1 && (size_t)splits * M * N > pfl) --splits;
     }
+    if (ep) splits = 1;
     const long long per = (kblocks + splits - 1) / splits;
     splits = (kblocks + per - 1) / per;
     bool enc_fail = false;
     if (splits == 1) {
-      e = tc_gemm_bf16(sa, ld, sb, ld, M, N, K, C, ldc, 0, 1, (int)per, accumulate, err, s, &enc_fail);
+      e = tc_gemm_bf16(A, lda, B, ldb, M, N, K, C, ldc, 0, 1, (int)per, accumulate, err, s, &enc_fail, ep);
     } else {
-      e = tc_gemm_bf16(sa, ld, sb, ld, M, N, K, partials, N, (long long)M * N, (int)splits, (int)per, false, err, s,
+      e = tc_gemm_bf16(A, lda, B, ldb, M, N, K, partials, N, (long long)M * N, (int)splits, (int)per, false, err, s,
                        &enc_fail);
       if (e == cudaSuccess && !enc_fail)
         sum_partials_kernel<<<grid1((long long)M * N), 256, 0, s>>>(partials, (int)splits, M, N, N, C, ldc,
@@ -512,6 +522,17 @@ int reverse_sweep(const Shape& sh, const float* w, int B, float** Ss, float** D,
   return GCDF_OK;
 }
 
+// Context of the BF16 image path: no staging images (the producers write them).
+int make_ctx_images(Ctx& cx, cudaStream_t s, float* partials, size_t pfl) {
+  cx.s = s;
+  cx.partials = partials;
+  cx.pfl = pfl;
+  cx.bf16 = true;
+  cx.err = fit_status_word();
+  if (!cx.err) return set_error(GCDF_ENOMEM, "fit status word unavailable");
+  return GCDF_OK;
+}
+
 int make_ctx(Ctx& cx, Ws& ws, const Shape& sh, int B, cudaStream_t s, float* partials, size_t pfl) {
   cx.s = s;
   cx.partials = partials;
@@ -519,6 +540,176 @@ int make_ctx(Ctx& cx, Ws& ws, const Shape& sh, int B, cudaStream_t s, float* par
   cx.bf16 = sh.bf16;
   cudaError_t e = cx.reserve(ws, B, std::max(sh.H, sh.d_in));
   if (e != cudaSuccess) return set_error(GCDF_ENOMEM, "fit operand images: %s", cudaGetErrorString(e));
+  return GCDF_OK;
+}
+
+// ---- BF16 path: operand images written by their producers -----------------------
+//
+// With BF16 products the operands are needed as BF16 images in two layouts:
+// row-major (batch x features: the A operand of the layer and back products,
+// whose K index is the feature) and transposed (features x batch: both
+// operands of the batch-length weight-gradient products).  Instead of rounding
+// FP32 arrays into images before every product, each producer writes them
+// directly: the input encoding writes both images of v; a layer product's
+// epilogue applies bias + SiLU and writes s'(z), the next layer's row image and
+// the transposed image; a back product's epilogue multiplies by s'(z_{l-1})
+// and writes both images of delta_{l-1} and its per-32-row column sums (the
+// bias gradient, summed over the row blocks in a fixed order).  The rounding
+// points are those of the generic path: every product operand is the BF16
+// rounding of the FP32 value the generic path would have computed.
+
+// v = [p, x, y, sin a, cos a, ...] as BF16 images Xr (B x ldr) and Xc (d_in x ldc)
+__global__ void encode_bf16_kernel(const float* __restrict__ q, const float* __restrict__ p, int B, int n, int d_in,
+                                   __nv_bfloat16* __restrict__ Xr, long long ldr, __nv_bfloat16* __restrict__ Xc,
+                                   long long ldc) {
+  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x) {
+    float x[3 + 2 + 2 * kMaxAngles];
+    const float* qb = q + b * n;
+    x[0] = p[3 * b];
+    x[1] = p[3 * b + 1];
+    x[2] = p[3 * b + 2];
+    x[3] = qb[0];
+    x[4] = qb[1];
+    for (int a = 0; a < n - 2; ++a) sincosf(qb[2 + a], &x[5 + 2 * a], &x[6 + 2 * a]);
+    for (int k = 0; k < d_in; ++k) {
+      const __nv_bfloat16 v = __float2bfloat16_rn(x[k]);
+      Xr[b * ldr + k] = v;
+      if (Xc) Xc[(long long)k * ldc + b] = v;
+    }
+  }
+}
+
+struct Bf16Fwd {
+  __nv_bfloat16* Xr = nullptr;  // v, B x ldx
+  __nv_bfloat16* Xc = nullptr;  // v^T, d_in x ldb (kept for dW_1)
+  long long ldx = 0, ldb = 0;
+  __nv_bfloat16* Hr[17] = {};   // h_l, B x H, l = 1 .. L-1
+  __nv_bfloat16* Hc[17] = {};   // h_l^T, H x ldb (kept for dW_{l+1})
+  __nv_bfloat16* Wr[17] = {};   // W_l, H x pad8(fan_in)
+  __nv_bfloat16* Wt[17] = {};   // W_l^T, fan_in x H
+};
+
+// Buffers of the BF16 path.  keep_cols: the transposed images for the weight
+// gradients; rev: the transposed weights for the back products.
+cudaError_t alloc_bf16(Ws& ws, const Shape& sh, int B, bool keep_cols, bool rev, Bf16Fwd& bf) {
+  cudaError_t e;
+  bf.ldx = pad8(sh.d_in);
+  bf.ldb = pad8(B);
+  if ((e = ws.get(&bf.Xr, (size_t)B * bf.ldx))) return e;
+  if (keep_cols && (e = ws.get(&bf.Xc, (size_t)sh.d_in * bf.ldb))) return e;
+  for (int l = 1; l < sh.L; ++l) {
+    if (l <= 2) {  // the row images are read by the next layer only: two alternate
+      if ((e = ws.get(&bf.Hr[l], (size_t)B * sh.H))) return e;
+    } else {
+      bf.Hr[l] = bf.Hr[l - 2];
+    }
+    if (keep_cols && (e = ws.get(&bf.Hc[l], (size_t)sh.H * bf.ldb))) return e;
+  }
+  for (int l = 1; l <= sh.L; ++l) {
+    if ((e = ws.get(&bf.Wr[l], (size_t)sh.H * pad8(sh.fan_in(l))))) return e;
+    if (rev && (e = ws.get(&bf.Wt[l], (size_t)sh.fan_in(l) * sh.H))) return e;
+  }
+  return cudaSuccess;
+}
+
+// Forward pass on images: S_l = s'(z_l) (Ss[l-1], may be NULL), s''(z_l) (S2s,
+// may be NULL), h_L in FP32 (HL), f (may be NULL).
+int forward_bf16(const Shape& sh, const float* w, const float* q, const float* p, int B, Bf16Fwd& bf, float** Ss,
+                 float** S2s, float* HL, float* f, Ctx& cx) {
+  const cudaStream_t s = cx.s;
+  cudaError_t e;
+  encode_bf16_kernel<<<grid1(B), 256, 0, s>>>(q, p, B, sh.n, sh.d_in, bf.Xr, bf.ldx, bf.Xc, bf.ldb);
+  for (int l = 1; l <= sh.L; ++l) {
+    const int K = sh.fan_in(l);
+    const float* W = w + sh.off(l);
+    if ((e = cx.image(W, K, 1, sh.H, K, bf.Wr[l], pad8(K))))
+      return set_error(GCDF_ECUDA, "weight image: %s", cudaGetErrorString(e));
+    if (bf.Wt[l] && (e = cx.image(W, 1, K, K, sh.H, bf.Wt[l], sh.H)))
+      return set_error(GCDF_ECUDA, "weight image: %s", cudaGetErrorString(e));
+    GemmEpilogue ep{};
+    ep.mode = kEpiBiasSilu;
+    ep.bias = W + (size_t)sh.H * K;
+    ep.s_out = Ss ? Ss[l - 1] : nullptr;
+    ep.s2_out = S2s ? S2s[l - 1] : nullptr;
+    ep.ld_s = sh.H;
+    if (l < sh.L) {
+      ep.img = bf.Hr[l];
+      ep.ld_img = sh.H;
+      ep.imgT = bf.Hc[l];
+      ep.ld_imgT = bf.ldb;
+    }
+    const __nv_bfloat16* A = l == 1 ? bf.Xr : bf.Hr[l - 1];
+    const long long lda = l == 1 ? bf.ldx : sh.H;
+    if ((e = cx.mm_images(A, lda, bf.Wr[l], pad8(K), B, sh.H, K, l == sh.L ? HL : nullptr, sh.H, false, false, &ep)))
+      return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+  }
+  if (f)
+    rowdot_kernel<<<(int)(((long long)B * 32 + 255) / 256), 256, 0, s>>>(HL, B, sh.H, w + sh.off_out,
+                                                                      w + sh.off_out + sh.H, f);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit forward launch: %s", cudaGetErrorString(e));
+  return GCDF_OK;
+}
+
+// Reverse sweep on images from delta_L (FP32, B x H): for l = L .. 1,
+//   with_grads: dW_l = delta_l^T h_{l-1} (transposed images) and db_l;
+//   delta_{l-1} = (delta_l W_l) * s'(z_{l-1}) through the back product's epilogue;
+//   at l = 1 (want_dv): dv = delta_1 W_1 (FP32) into dv.
+int reverse_bf16(const Shape& sh, int B, Bf16Fwd& bf, float** Ss, float* DL, bool with_grads, float* dweights,
+                 float* dv, Ws& ws, Ctx& cx) {
+  const cudaStream_t s = cx.s;
+  const int H = sh.H;
+  cudaError_t e;
+  __nv_bfloat16 *Dr[2] = {}, *Dc[2] = {};
+  float* cs = nullptr;
+  const long long nblk = (B + 31) / 32;
+  for (int k = 0; k < 2; ++k)
+    if ((e = ws.get(&Dr[k], (size_t)B * H)) || (with_grads && (e = ws.get(&Dc[k], (size_t)H * bf.ldb))))
+      return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  if (with_grads && (e = ws.get(&cs, (size_t)nblk * H))) return set_error(GCDF_ENOMEM, "cudaMallocAsync");
+  // delta_L images; its bias gradient from the FP32 array
+  if ((e = cx.image(DL, H, 1, B, H, Dr[0], H))) return set_error(GCDF_ECUDA, "image: %s", cudaGetErrorString(e));
+  if (with_grads) {
+    if ((e = cx.image(DL, 1, H, H, B, Dc[0], bf.ldb))) return set_error(GCDF_ECUDA, "image: %s", cudaGetErrorString(e));
+    if ((e = colsum(DL, B, H, nullptr, dweights + sh.off(sh.L) + (size_t)H * sh.fan_in(sh.L), cx.partials, cx.pfl, s)))
+      return set_error(GCDF_ECUDA, "colsum: %s", cudaGetErrorString(e));
+  }
+  int cur = 0;
+  for (int l = sh.L; l >= 1; --l) {
+    const int K = sh.fan_in(l);
+    if (with_grads) {
+      // dW_l (H x K) = delta_l^T (H x B) . h_{l-1} (B x K): both transposed images
+      const __nv_bfloat16* Bop = l == 1 ? bf.Xc : bf.Hc[l - 1];
+      if ((e = cx.mm_images(Dc[cur], bf.ldb, Bop, bf.ldb, H, K, B, dweights + sh.off(l), K, true, false, nullptr)))
+        return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+      // db_l for l < L: the column sums the back product of layer l + 1 left
+      if (l < sh.L && (e = colsum(cs, (int)nblk, H, nullptr, dweights + sh.off(l) + (size_t)H * K, cx.partials, cx.pfl, s)))
+        return set_error(GCDF_ECUDA, "colsum: %s", cudaGetErrorString(e));
+    }
+    if (l > 1) {
+      GemmEpilogue ep{};
+      ep.mode = kEpiMul;
+      ep.s_in = Ss[l - 2];
+      ep.ld_s = H;
+      ep.img = Dr[cur ^ 1];
+      ep.ld_img = H;
+      if (with_grads) {
+        ep.imgT = Dc[cur ^ 1];
+        ep.ld_imgT = bf.ldb;
+        ep.colsum = cs;
+        ep.ld_colsum = H;
+      }
+      // delta_{l-1} (B x K) = (delta_l (B x H) W_l (H x K)) * s'(z_{l-1}); B operand W_l^T (K x H)
+      if ((e = cx.mm_images(Dr[cur], H, bf.Wt[l], H, B, K, H, nullptr, K, false, false, &ep)))
+        return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+      cur ^= 1;
+    } else if (dv) {
+      if ((e = cx.mm_images(Dr[cur], H, bf.Wt[1], H, B, sh.d_in, H, dv, sh.d_in, false, false, nullptr)))
+        return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+    }
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit backward launch: %s", cudaGetErrorString(e));
   return GCDF_OK;
 }
 
@@ -555,6 +746,17 @@ int gcdf_fit_forward(const gcdf_fit_desc* desc, const float* weights, const floa
   float* Hs[18];
   float* Ss[17];
   cudaError_t e;
+  if (sh.bf16) {
+    Bf16Fwd bf;
+    float* HL = nullptr;
+    Ctx cx;
+    if ((e = alloc_bf16(ws, sh, batch, false, false, bf)) || (e = ws.get(&HL, (size_t)batch * sh.H)))
+      return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+    if ((rc = make_ctx_images(cx, s, nullptr, 0))) return rc;
+    if ((rc = forward_bf16(sh, weights, q, p, batch, bf, nullptr, nullptr, HL, f, cx))) return rc;
+    clear_error();
+    return GCDF_OK;
+  }
   if ((e = ws.get(&Hs[0], (size_t)batch * sh.d_in))) return set_error(GCDF_ENOMEM, "cudaMallocAsync");
   // two alternating activation buffers suffice without a backward pass
   float *h0, *h1, *sc;
@@ -594,6 +796,30 @@ int gcdf_fit_vjp(const gcdf_fit_desc* desc, const float* weights, const float* q
   float* Ss[17];
   float *D0, *D1, *partials;
   const size_t pfl = (size_t)64 * sh.H * (sh.H > sh.d_in ? sh.H : sh.d_in);
+  if (sh.bf16) {
+    const int H = sh.H;
+    Bf16Fwd bf;
+    float *HL = nullptr, *DL = nullptr, *dv = nullptr;
+    Ctx cx;
+    for (int l = 1; l <= sh.L; ++l)
+      if ((e = ws.get(&Ss[l - 1], (size_t)batch * H))) return set_error(GCDF_ENOMEM, "cudaMallocAsync");
+    if ((e = alloc_bf16(ws, sh, batch, true, true, bf)) || (e = ws.get(&HL, (size_t)batch * H)) ||
+        (e = ws.get(&DL, (size_t)batch * H)) || (e = ws.get(&partials, pfl)) ||
+        (dq && (e = ws.get(&dv, (size_t)batch * sh.d_in))))
+      return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+    if ((rc = make_ctx_images(cx, s, partials, pfl))) return rc;
+    if ((rc = forward_bf16(sh, weights, q, p, batch, bf, Ss, nullptr, HL, nullptr, cx))) return rc;
+    float* dwo = dweights + sh.off_out;
+    if ((e = colsum(HL, batch, H, g_f, dwo, partials, pfl, s)) || (e = colsum(g_f, batch, 1, nullptr, dwo + H, partials, pfl, s)))
+      return set_error(GCDF_ECUDA, "colsum: %s", cudaGetErrorString(e));
+    seed_kernel<<<grid1((long long)batch * H), 256, 0, s>>>(g_f, weights + sh.off_out, Ss[sh.L - 1], batch, H, DL);
+    if ((rc = reverse_bf16(sh, batch, bf, Ss, DL, true, dweights, dv, ws, cx))) return rc;
+    if (dq) dq_kernel<<<grid1(batch), 256, 0, s>>>(q, dv, batch, sh.n, sh.d_in, dq);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit backward launch: %s", cudaGetErrorString(e));
+    clear_error();
+    return GCDF_OK;
+  }
   if ((e = ws.get(&Hs[0], (size_t)batch * sh.d_in))) return set_error(GCDF_ENOMEM, "cudaMallocAsync");
   for (int l = 1; l <= sh.L; ++l)
     if ((e = ws.get(&Hs[l], (size_t)batch * sh.H)) || (e = ws.get(&Ss[l - 1], (size_t)batch * sh.H)))
@@ -658,6 +884,26 @@ int gcdf_fit_value_grad(const gcdf_fit_desc* desc, const float* weights, const f
   float* D[17];
   float *d0, *d1, *dv;
   cudaError_t e;
+  if (sh.bf16) {
+    Bf16Fwd bf;
+    float *HL = nullptr, *DL = nullptr;
+    Ctx cx;
+    for (int l = 1; l <= sh.L; ++l)
+      if ((e = ws.get(&Ss[l - 1], (size_t)batch * sh.H))) return set_error(GCDF_ENOMEM, "cudaMallocAsync");
+    if ((e = alloc_bf16(ws, sh, batch, false, true, bf)) || (e = ws.get(&HL, (size_t)batch * sh.H)) ||
+        (e = ws.get(&DL, (size_t)batch * sh.H)) || (e = ws.get(&dv, (size_t)batch * sh.d_in)))
+      return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+    if ((rc = make_ctx_images(cx, s, nullptr, 0))) return rc;
+    if ((rc = forward_bf16(sh, weights, q, p, batch, bf, Ss, nullptr, HL, f, cx))) return rc;
+    seed_kernel<<<grid1((long long)batch * sh.H), 256, 0, s>>>(nullptr, weights + sh.off_out, Ss[sh.L - 1], batch,
+                                                                sh.H, DL);
+    if ((rc = reverse_bf16(sh, batch, bf, Ss, DL, false, nullptr, dv, ws, cx))) return rc;
+    dq_kernel<<<grid1(batch), 256, 0, s>>>(q, dv, batch, sh.n, sh.d_in, dq);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit value/grad launch: %s", cudaGetErrorString(e));
+    clear_error();
+    return GCDF_OK;
+  }
   if ((e = ws.get(&Hs[0], (size_t)batch * sh.d_in)) || (e = ws.get(&dv, (size_t)batch * sh.d_in)) ||
       (e = ws.get(&d0, (size_t)batch * sh.H)) || (e = ws.get(&d1, (size_t)batch * sh.H)))
     return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));

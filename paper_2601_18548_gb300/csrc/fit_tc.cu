@@ -21,6 +21,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "fit_tc.cuh"
@@ -55,6 +56,7 @@ struct GemmArgs {
   long long zstride;   // elements between the outputs of consecutive splits
   int accumulate;
   int* err;
+  GemmEpilogue ep;
 };
 
 __device__ __forceinline__ uint32_t bar(uint32_t base, int i) { return base + kOffBar + 8 * i; }
@@ -187,35 +189,104 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
       ptx::tc_fence_after();
       // Each 32 x 32 block (lane = row after tcgen05.ld) is transposed through
       // shared memory, so that each store instruction writes 32 consecutive
-      // floats of one row of C (one 128-byte line) instead of one float in 32
-      // rows.  The operand ring is idle once the accumulator is complete (every
-      // MMA, and so every TMA load, has finished): warp q uses 33 x 32 floats
-      // of it (row stride 33: conflict-free in both directions).
+      // values of one row (one 128-byte line of FP32) instead of one value in
+      // 32 rows.  The operand ring is idle once the accumulator is complete
+      // (every MMA, and so every TMA load, has finished): warp q uses 33 x 32
+      // floats of it (row stride 33: conflict-free in both directions).
       float* tile = reinterpret_cast<float*>(gbase) + q * (32 * 33);
       const int row0 = tm * 2 * kRowsA + (int)rank * kRowsA + q * 32;
-      float* cz = a.C + (long long)blockIdx.y * a.zstride;
+      const int row = row0 + lane;
+      float* cz = a.C ? a.C + (long long)blockIdx.y * a.zstride : nullptr;
       const int n0 = tn * kTileN;
+      const GemmEpilogue& ep = a.ep;
 #pragma unroll 1
       for (int c0 = 0; c0 < kTileN; c0 += 32) {
-        uint32_t v[32];
-        ptx::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        const int nb = n0 + c0;  // first column of the block
+        if (nb >= a.N) break;
+        uint32_t u[32];
+        ptx::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, u);
         ptx::tmem_wait_ld();
+        float v[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(v[j]);
-        __syncwarp();
-        const int n = n0 + c0 + lane;
-        if (n < a.N) {
+        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(u[j]);
+        float sp[32], spp[32];
+        if (ep.mode == kEpiMul) {
+          // d = acc * S_in: the factor block comes in coalesced (lane = column)
 #pragma unroll 4
           for (int r = 0; r < 32; ++r) {
-            const int row = row0 + r;
-            if (row < a.M) {
-              float* c = cz + (long long)row * a.ldc + n;
-              const float x = tile[r * 33 + lane];
-              *c = a.accumulate ? *c + x : x;
-            }
+            const int rr = row0 + r, n = nb + lane;
+            tile[r * 33 + lane] = (rr < a.M && n < a.N) ? ep.s_in[(long long)rr * ep.ld_s + n] : 0.f;
+          }
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] *= tile[lane * 33 + j];
+          __syncwarp();
+        } else if (ep.mode == kEpiBiasSilu) {
+          // h = s(z), z = acc + b; s'(z) and s''(z) for the reverse sweeps
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = min(nb + j, a.N - 1);
+            const float z = v[j] + __ldg(ep.bias + n);
+            const float sg = 1.f / (1.f + expf(-z));
+            v[j] = z * sg;
+            sp[j] = sg * (1.f + z * (1.f - sg));
+            spp[j] = sg * (1.f - sg) * (2.f + z * (1.f - 2.f * sg));
           }
         }
-        __syncwarp();
+        // row-major FP32 outputs through the tile: C (or C += for split partials),
+        // then s'(z) and s''(z)
+        auto store_rows = [&](const float (&src)[32], float* dst, long long ld, bool add) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = src[j];
+          __syncwarp();
+          const int n = nb + lane;
+          if (n < a.N) {
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r) {
+              const int rr = row0 + r;
+              if (rr < a.M) {
+                float* c = dst + (long long)rr * ld + n;
+                const float x = tile[r * 33 + lane];
+                *c = add ? *c + x : x;
+              }
+            }
+          }
+          __syncwarp();
+        };
+        if (cz) store_rows(v, cz, a.ldc, a.accumulate != 0);
+        if (ep.mode == kEpiBiasSilu) {
+          if (ep.s_out) store_rows(sp, ep.s_out, ep.ld_s, false);
+          if (ep.s2_out) store_rows(spp, ep.s2_out, ep.ld_s, false);
+        }
+        if (ep.img || ep.colsum) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = v[j];
+          __syncwarp();
+          const int n = nb + lane;
+          float cs = 0.f;
+          if (n < a.N) {
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r) {
+              const int rr = row0 + r;
+              const float x = tile[r * 33 + lane];
+              if (rr < a.M) {
+                if (ep.img) ep.img[(long long)rr * ep.ld_img + n] = __float2bfloat16_rn(x);
+                cs += x;
+              }
+            }
+            // column sums of this block's 32 rows, summed later over the row
+            // blocks in a fixed order (blocks past the last row hold no rows)
+            if (ep.colsum && row0 < a.M) ep.colsum[(long long)(row0 >> 5) * ep.ld_colsum + n] = cs;
+          }
+          __syncwarp();
+        }
+        if (ep.imgT && row < a.M) {
+          // transposed BF16 image: for each column the 32 lanes write 32
+          // consecutive rows (64 contiguous bytes)
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (nb + j < a.N) ep.imgT[(long long)(nb + j) * ep.ld_imgT + row] = __float2bfloat16_rn(v[j]);
+        }
       }
     }
   }
@@ -286,7 +357,7 @@ int* fit_status_word() {
 
 cudaError_t tc_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, int M, int N, int K, float* C,
                          long long ldc, long long zstride, int splits, int kb_per_split, bool accumulate, int* err,
-                         cudaStream_t s, bool* encode_failed) {
+                         cudaStream_t s, bool* encode_failed, const GemmEpilogue* ep) {
   *encode_failed = false;
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   {
@@ -319,6 +390,12 @@ cudaError_t tc_gemm_bf16(const void* A, long long lda, const void* B, long long 
   g.zstride = zstride;
   g.accumulate = accumulate ? 1 : 0;
   g.err = err;
+  if (ep) {
+    g.ep = *ep;
+  } else {
+    memset(&g.ep, 0, sizeof(g.ep));
+    g.ep.mode = kEpiStore;
+  }
   const int tiles_m = (M + 2 * kRowsA - 1) / (2 * kRowsA);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2u * (unsigned)(tiles_m * g.tiles_n), (unsigned)splits, 1);
