@@ -579,6 +579,42 @@ __global__ void encode_bf16_kernel(const float* __restrict__ q, const float* __r
   }
 }
 
+// delta_L = g w_o * s'(z_L) (g NULL: 1) straight into its BF16 images: row-major
+// Dr (B x H) and transposed Dc (H x ldc, NULL: not written), with the column
+// sums of every 32-row block in cs (NULL: none).  Block (32, 8) per 32 x 32 tile.
+__global__ void seed_images_kernel(const float* __restrict__ g, const float* __restrict__ wo,
+                                   const float* __restrict__ S, int B, int H, __nv_bfloat16* __restrict__ Dr,
+                                   __nv_bfloat16* __restrict__ Dc, long long ldc, float* __restrict__ cs) {
+  __shared__ float t[32][33];
+  const long long r0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int c = c0 + tx;
+  for (int i = ty; i < 32; i += 8) {
+    const long long r = r0 + i;
+    float d = 0.f;
+    if (r < B && c < H) {
+      d = (g ? g[r] : 1.f) * wo[c] * S[r * H + c];
+      Dr[r * H + c] = __float2bfloat16_rn(d);
+    }
+    t[i][tx] = d;
+  }
+  __syncthreads();
+  if (cs && ty == 0 && c < H) {
+    float sum = 0.f;
+    for (int i = 0; i < 32; ++i)
+      if (r0 + i < B) sum += t[i][tx];
+    cs[(long long)blockIdx.x * H + c] = sum;
+  }
+  if (Dc) {
+    for (int i = ty; i < 32; i += 8) {
+      const int cc = c0 + i;
+      const long long r = r0 + tx;
+      if (cc < H && r < B) Dc[(long long)cc * ldc + r] = __float2bfloat16_rn(t[tx][i]);
+    }
+  }
+}
+
 struct Bf16Fwd {
   __nv_bfloat16* Xr = nullptr;  // v, B x ldx
   __nv_bfloat16* Xc = nullptr;  // v^T, d_in x ldb (kept for dW_1)
@@ -612,10 +648,10 @@ cudaError_t alloc_bf16(Ws& ws, const Shape& sh, int B, bool keep_cols, bool rev,
   return cudaSuccess;
 }
 
-// Forward pass on images: S_l = s'(z_l) (Ss[l-1], may be NULL), s''(z_l) (S2s,
-// may be NULL), h_L in FP32 (HL), f (may be NULL).
+// Forward pass on images: S_l = s'(z_l) (Ss[l-1], may be NULL), h_L in FP32
+// (HL), f (may be NULL).
 int forward_bf16(const Shape& sh, const float* w, const float* q, const float* p, int B, Bf16Fwd& bf, float** Ss,
-                 float** S2s, float* HL, float* f, Ctx& cx) {
+                 float* HL, float* f, Ctx& cx) {
   const cudaStream_t s = cx.s;
   cudaError_t e;
   encode_bf16_kernel<<<grid1(B), 256, 0, s>>>(q, p, B, sh.n, sh.d_in, bf.Xr, bf.ldx, bf.Xc, bf.ldb);
@@ -630,7 +666,6 @@ int forward_bf16(const Shape& sh, const float* w, const float* q, const float* p
     ep.mode = kEpiBiasSilu;
     ep.bias = W + (size_t)sh.H * K;
     ep.s_out = Ss ? Ss[l - 1] : nullptr;
-    ep.s2_out = S2s ? S2s[l - 1] : nullptr;
     ep.ld_s = sh.H;
     if (l < sh.L) {
       ep.img = bf.Hr[l];
@@ -651,12 +686,13 @@ int forward_bf16(const Shape& sh, const float* w, const float* q, const float* p
   return GCDF_OK;
 }
 
-// Reverse sweep on images from delta_L (FP32, B x H): for l = L .. 1,
-//   with_grads: dW_l = delta_l^T h_{l-1} (transposed images) and db_l;
+// Reverse sweep on images from delta_L = g w_o * s'(z_L) (g NULL: 1): for l = L .. 1,
+//   with_grads: dW_l = delta_l^T h_{l-1} (transposed images) and db_l (the
+//   per-32-row column sums of delta_l, summed over the row blocks in order);
 //   delta_{l-1} = (delta_l W_l) * s'(z_{l-1}) through the back product's epilogue;
-//   at l = 1 (want_dv): dv = delta_1 W_1 (FP32) into dv.
-int reverse_bf16(const Shape& sh, int B, Bf16Fwd& bf, float** Ss, float* DL, bool with_grads, float* dweights,
-                 float* dv, Ws& ws, Ctx& cx) {
+//   at l = 1 (dv not NULL): dv = delta_1 W_1 (FP32).
+int reverse_bf16(const Shape& sh, int B, Bf16Fwd& bf, float** Ss, const float* g, const float* wo, bool with_grads,
+                 float* dweights, float* dv, Ws& ws, Ctx& cx) {
   const cudaStream_t s = cx.s;
   const int H = sh.H;
   cudaError_t e;
@@ -667,12 +703,11 @@ int reverse_bf16(const Shape& sh, int B, Bf16Fwd& bf, float** Ss, float* DL, boo
     if ((e = ws.get(&Dr[k], (size_t)B * H)) || (with_grads && (e = ws.get(&Dc[k], (size_t)H * bf.ldb))))
       return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
   if (with_grads && (e = ws.get(&cs, (size_t)nblk * H))) return set_error(GCDF_ENOMEM, "cudaMallocAsync");
-  // delta_L images; its bias gradient from the FP32 array
-  if ((e = cx.image(DL, H, 1, B, H, Dr[0], H))) return set_error(GCDF_ECUDA, "image: %s", cudaGetErrorString(e));
-  if (with_grads) {
-    if ((e = cx.image(DL, 1, H, H, B, Dc[0], bf.ldb))) return set_error(GCDF_ECUDA, "image: %s", cudaGetErrorString(e));
-    if ((e = colsum(DL, B, H, nullptr, dweights + sh.off(sh.L) + (size_t)H * sh.fan_in(sh.L), cx.partials, cx.pfl, s)))
-      return set_error(GCDF_ECUDA, "colsum: %s", cudaGetErrorString(e));
+  // delta_L straight into its images and column sums
+  {
+    dim3 grid((unsigned)nblk, (unsigned)((H + 31) / 32));
+    seed_images_kernel<<<grid, dim3(32, 8), 0, s>>>(g, wo, Ss[sh.L - 1], B, H, Dr[0], with_grads ? Dc[0] : nullptr,
+                                                    bf.ldb, with_grads ? cs : nullptr);
   }
   int cur = 0;
   for (int l = sh.L; l >= 1; --l) {
@@ -682,8 +717,8 @@ int reverse_bf16(const Shape& sh, int B, Bf16Fwd& bf, float** Ss, float* DL, boo
       const __nv_bfloat16* Bop = l == 1 ? bf.Xc : bf.Hc[l - 1];
       if ((e = cx.mm_images(Dc[cur], bf.ldb, Bop, bf.ldb, H, K, B, dweights + sh.off(l), K, true, false, nullptr)))
         return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
-      // db_l for l < L: the column sums the back product of layer l + 1 left
-      if (l < sh.L && (e = colsum(cs, (int)nblk, H, nullptr, dweights + sh.off(l) + (size_t)H * K, cx.partials, cx.pfl, s)))
+      // db_l: the column sums left by the seed (l = L) or by the back product of layer l + 1
+      if ((e = colsum(cs, (int)nblk, H, nullptr, dweights + sh.off(l) + (size_t)H * K, cx.partials, cx.pfl, s)))
         return set_error(GCDF_ECUDA, "colsum: %s", cudaGetErrorString(e));
     }
     if (l > 1) {
@@ -753,7 +788,7 @@ int gcdf_fit_forward(const gcdf_fit_desc* desc, const float* weights, const floa
     if ((e = alloc_bf16(ws, sh, batch, false, false, bf)) || (e = ws.get(&HL, (size_t)batch * sh.H)))
       return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
     if ((rc = make_ctx_images(cx, s, nullptr, 0))) return rc;
-    if ((rc = forward_bf16(sh, weights, q, p, batch, bf, nullptr, nullptr, HL, f, cx))) return rc;
+    if ((rc = forward_bf16(sh, weights, q, p, batch, bf, nullptr, HL, f, cx))) return rc;
     clear_error();
     return GCDF_OK;
   }
@@ -799,21 +834,20 @@ int gcdf_fit_vjp(const gcdf_fit_desc* desc, const float* weights, const float* q
   if (sh.bf16) {
     const int H = sh.H;
     Bf16Fwd bf;
-    float *HL = nullptr, *DL = nullptr, *dv = nullptr;
+    float *HL = nullptr, *dv = nullptr;
     Ctx cx;
     for (int l = 1; l <= sh.L; ++l)
       if ((e = ws.get(&Ss[l - 1], (size_t)batch * H))) return set_error(GCDF_ENOMEM, "cudaMallocAsync");
     if ((e = alloc_bf16(ws, sh, batch, true, true, bf)) || (e = ws.get(&HL, (size_t)batch * H)) ||
-        (e = ws.get(&DL, (size_t)batch * H)) || (e = ws.get(&partials, pfl)) ||
+        (e = ws.get(&partials, pfl)) ||
         (dq && (e = ws.get(&dv, (size_t)batch * sh.d_in))))
       return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
     if ((rc = make_ctx_images(cx, s, partials, pfl))) return rc;
-    if ((rc = forward_bf16(sh, weights, q, p, batch, bf, Ss, nullptr, HL, nullptr, cx))) return rc;
+    if ((rc = forward_bf16(sh, weights, q, p, batch, bf, Ss, HL, nullptr, cx))) return rc;
     float* dwo = dweights + sh.off_out;
     if ((e = colsum(HL, batch, H, g_f, dwo, partials, pfl, s)) || (e = colsum(g_f, batch, 1, nullptr, dwo + H, partials, pfl, s)))
       return set_error(GCDF_ECUDA, "colsum: %s", cudaGetErrorString(e));
-    seed_kernel<<<grid1((long long)batch * H), 256, 0, s>>>(g_f, weights + sh.off_out, Ss[sh.L - 1], batch, H, DL);
-    if ((rc = reverse_bf16(sh, batch, bf, Ss, DL, true, dweights, dv, ws, cx))) return rc;
+    if ((rc = reverse_bf16(sh, batch, bf, Ss, g_f, weights + sh.off_out, true, dweights, dv, ws, cx))) return rc;
     if (dq) dq_kernel<<<grid1(batch), 256, 0, s>>>(q, dv, batch, sh.n, sh.d_in, dq);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit backward launch: %s", cudaGetErrorString(e));
@@ -886,18 +920,16 @@ int gcdf_fit_value_grad(const gcdf_fit_desc* desc, const float* weights, const f
   cudaError_t e;
   if (sh.bf16) {
     Bf16Fwd bf;
-    float *HL = nullptr, *DL = nullptr;
+    float* HL = nullptr;
     Ctx cx;
     for (int l = 1; l <= sh.L; ++l)
       if ((e = ws.get(&Ss[l - 1], (size_t)batch * sh.H))) return set_error(GCDF_ENOMEM, "cudaMallocAsync");
     if ((e = alloc_bf16(ws, sh, batch, false, true, bf)) || (e = ws.get(&HL, (size_t)batch * sh.H)) ||
-        (e = ws.get(&DL, (size_t)batch * sh.H)) || (e = ws.get(&dv, (size_t)batch * sh.d_in)))
+        (e = ws.get(&dv, (size_t)batch * sh.d_in)))
       return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
     if ((rc = make_ctx_images(cx, s, nullptr, 0))) return rc;
-    if ((rc = forward_bf16(sh, weights, q, p, batch, bf, Ss, nullptr, HL, f, cx))) return rc;
-    seed_kernel<<<grid1((long long)batch * sh.H), 256, 0, s>>>(nullptr, weights + sh.off_out, Ss[sh.L - 1], batch,
-                                                                sh.H, DL);
-    if ((rc = reverse_bf16(sh, batch, bf, Ss, DL, false, nullptr, dv, ws, cx))) return rc;
+    if ((rc = forward_bf16(sh, weights, q, p, batch, bf, Ss, HL, f, cx))) return rc;
+    if ((rc = reverse_bf16(sh, batch, bf, Ss, nullptr, weights + sh.off_out, false, nullptr, dv, ws, cx))) return rc;
     dq_kernel<<<grid1(batch), 256, 0, s>>>(q, dv, batch, sh.n, sh.d_in, dq);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit value/grad launch: %s", cudaGetErrorString(e));

@@ -38,7 +38,7 @@ constexpr int kStages = 4;
 constexpr int kABytes = kRowsA * 128;          // 16 KB
 constexpr int kBBytes = kRowsB * 128;          // 8 KB
 constexpr int kStageBytes = kABytes + kBBytes; // 24 KB, a multiple of the 1024-byte swizzle atom
-constexpr int kThreads = 192;                  // TMA warp, MMA warp, 4 epilogue warps
+constexpr int kThreads = 320;                  // TMA warp, MMA warp, 8 epilogue warps
 constexpr uint32_t kTmemCols = 128;
 constexpr int kOffBar = kStages * kStageBytes;
 constexpr int B_FULL0 = 0, B_EMPTY0 = kStages, B_ACC = 2 * kStages;
@@ -171,8 +171,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
       }
     }
   } else {
-    // ---- epilogue: warp w reads TMEM lanes [32 (w mod 4), +32) = its 32 rows of the CTA's 128
+    // ---- epilogue: 8 warps; warp w reads TMEM lanes [32 (w mod 4), +32) (its 32
+    // rows of the CTA's 128) and columns [64 ch, 64 ch + 64) of the tile, ch = (w - 2) / 4
     const int q = warp & 3;
+    const int ch = (warp - 2) >> 2;
     bool ok = true;
     {
       const long long t0 = clock64();
@@ -191,102 +193,81 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
       // shared memory, so that each store instruction writes 32 consecutive
       // values of one row (one 128-byte line of FP32) instead of one value in
       // 32 rows.  The operand ring is idle once the accumulator is complete
-      // (every MMA, and so every TMA load, has finished): warp q uses 33 x 32
-      // floats of it (row stride 33: conflict-free in both directions).
-      float* tile = reinterpret_cast<float*>(gbase) + q * (32 * 33);
+      // (every MMA, and so every TMA load, has finished): each warp uses two
+      // 33 x 32 float tiles of it (row stride 33: conflict-free both ways), one
+      // for the result and one for s'(z) or the incoming factor.
+      float* tile = reinterpret_cast<float*>(gbase) + (warp - 2) * (2 * 32 * 33);
+      float* tile2 = tile + 32 * 33;
       const int row0 = tm * 2 * kRowsA + (int)rank * kRowsA + q * 32;
-      const int row = row0 + lane;
       float* cz = a.C ? a.C + (long long)blockIdx.y * a.zstride : nullptr;
       const int n0 = tn * kTileN;
       const GemmEpilogue& ep = a.ep;
+      const bool silu = ep.mode == kEpiBiasSilu;
 #pragma unroll 1
-      for (int c0 = 0; c0 < kTileN; c0 += 32) {
+      for (int c0 = 64 * ch; c0 < 64 * ch + 64; c0 += 32) {
         const int nb = n0 + c0;  // first column of the block
         if (nb >= a.N) break;
-        uint32_t u[32];
-        ptx::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, u);
-        ptx::tmem_wait_ld();
-        float v[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(u[j]);
-        float sp[32], spp[32];
         if (ep.mode == kEpiMul) {
-          // d = acc * S_in: the factor block comes in coalesced (lane = column)
+          // the factor block comes in coalesced (lane = column)
 #pragma unroll 4
           for (int r = 0; r < 32; ++r) {
             const int rr = row0 + r, n = nb + lane;
-            tile[r * 33 + lane] = (rr < a.M && n < a.N) ? ep.s_in[(long long)rr * ep.ld_s + n] : 0.f;
+            tile2[r * 33 + lane] = (rr < a.M && n < a.N) ? ep.s_in[(long long)rr * ep.ld_s + n] : 0.f;
           }
           __syncwarp();
-#pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] *= tile[lane * 33 + j];
-          __syncwarp();
-        } else if (ep.mode == kEpiBiasSilu) {
-          // h = s(z), z = acc + b; s'(z) and s''(z) for the reverse sweeps
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = min(nb + j, a.N - 1);
-            const float z = v[j] + __ldg(ep.bias + n);
-            const float sg = 1.f / (1.f + expf(-z));
-            v[j] = z * sg;
-            sp[j] = sg * (1.f + z * (1.f - sg));
-            spp[j] = sg * (1.f - sg) * (2.f + z * (1.f - 2.f * sg));
-          }
         }
-        // row-major FP32 outputs through the tile: C (or C += for split partials),
-        // then s'(z) and s''(z)
-        auto store_rows = [&](const float (&src)[32], float* dst, long long ld, bool add) {
+        uint32_t u[32];
+        ptx::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, u);
+        ptx::tmem_wait_ld();
+        // this row's 32 results into the tile (s'(z) into the second tile)
 #pragma unroll
-          for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = src[j];
-          __syncwarp();
-          const int n = nb + lane;
-          if (n < a.N) {
-#pragma unroll 4
-            for (int r = 0; r < 32; ++r) {
-              const int rr = row0 + r;
-              if (rr < a.M) {
-                float* c = dst + (long long)rr * ld + n;
-                const float x = tile[r * 33 + lane];
-                *c = add ? *c + x : x;
-              }
-            }
+        for (int j = 0; j < 32; ++j) {
+          float v = __uint_as_float(u[j]);
+          if (ep.mode == kEpiMul) {
+            v *= tile2[lane * 33 + j];
+          } else if (silu) {
+            // h = s(z), z = acc + b; sigma through the exponential and the
+            // exactly rounded reciprocal
+            const float z = v + __ldg(ep.bias + min(nb + j, a.N - 1));
+            const float sg = __frcp_rn(1.f + __expf(-z));
+            v = z * sg;
+            tile2[lane * 33 + j] = sg * (1.f + z * (1.f - sg));
           }
-          __syncwarp();
-        };
-        if (cz) store_rows(v, cz, a.ldc, a.accumulate != 0);
-        if (ep.mode == kEpiBiasSilu) {
-          if (ep.s_out) store_rows(sp, ep.s_out, ep.ld_s, false);
-          if (ep.s2_out) store_rows(spp, ep.s2_out, ep.ld_s, false);
+          tile[lane * 33 + j] = v;
         }
-        if (ep.img || ep.colsum) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = v[j];
-          __syncwarp();
-          const int n = nb + lane;
+        __syncwarp();
+        // row-major outputs, lane = column: C (or C += for split partials),
+        // s'(z), the BF16 image and the column sums
+        const int n = nb + lane;
+        if (n < a.N) {
           float cs = 0.f;
-          if (n < a.N) {
 #pragma unroll 4
-            for (int r = 0; r < 32; ++r) {
-              const int rr = row0 + r;
+          for (int r = 0; r < 32; ++r) {
+            const int rr = row0 + r;
+            if (rr < a.M) {
               const float x = tile[r * 33 + lane];
-              if (rr < a.M) {
-                if (ep.img) ep.img[(long long)rr * ep.ld_img + n] = __float2bfloat16_rn(x);
-                cs += x;
+              if (cz) {
+                float* c = cz + (long long)rr * a.ldc + n;
+                *c = a.accumulate ? *c + x : x;
               }
+              if (silu && ep.s_out) ep.s_out[(long long)rr * ep.ld_s + n] = tile2[r * 33 + lane];
+              if (ep.img) ep.img[(long long)rr * ep.ld_img + n] = __float2bfloat16_rn(x);
+              cs += x;
             }
-            // column sums of this block's 32 rows, summed later over the row
-            // blocks in a fixed order (blocks past the last row hold no rows)
-            if (ep.colsum && row0 < a.M) ep.colsum[(long long)(row0 >> 5) * ep.ld_colsum + n] = cs;
           }
-          __syncwarp();
+          // column sums of this block's rows, summed later over the row blocks
+          // in a fixed order (blocks past the last row hold no rows)
+          if (ep.colsum && row0 < a.M) ep.colsum[(long long)(row0 >> 5) * ep.ld_colsum + n] = cs;
         }
-        if (ep.imgT && row < a.M) {
+        if (ep.imgT && row0 + lane < a.M) {
           // transposed BF16 image: for each column the 32 lanes write 32
           // consecutive rows (64 contiguous bytes)
-#pragma unroll
+#pragma unroll 4
           for (int j = 0; j < 32; ++j)
-            if (nb + j < a.N) ep.imgT[(long long)(nb + j) * ep.ld_imgT + row] = __float2bfloat16_rn(v[j]);
+            if (nb + j < a.N)
+              ep.imgT[(long long)(nb + j) * ep.ld_imgT + row0 + lane] = __float2bfloat16_rn(tile[lane * 33 + j]);
         }
+        __syncwarp();
       }
     }
   }

@@ -9,7 +9,7 @@ namespace gcdf {
 // What the GEMM's epilogue does with the FP32 accumulator tile before storing.
 enum GemmEpiMode : int {
   kEpiStore = 0,     // C = acc (or C += acc)
-  kEpiBiasSilu = 1,  // z = acc + bias[n]: C = s(z), s_out = s'(z), s2_out = s''(z)
+  kEpiBiasSilu = 1,  // z = acc + bias[n]: C = s(z), s_out = s'(z) (s2_out is not written)
   kEpiMul = 2        // C = acc * s_in[m, n]
 };
 
