@@ -226,10 +226,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
           if (ep.mode == kEpiMul) {
             v *= tile2[lane * 33 + j];
           } else if (silu) {
-            // h = s(z), z = acc + b; sigma through the exponential and the
-            // exactly rounded reciprocal
+            // h = s(z), z = acc + b, with the arithmetic of the element-wise
+            // kernel of the generic path (expf, an exactly rounded reciprocal
+            // equal to 1 / x): the same activations and s' to the bit
             const float z = v + __ldg(ep.bias + min(nb + j, a.N - 1));
-            const float sg = __frcp_rn(1.f + __expf(-z));
+            const float sg = __frcp_rn(1.f + expf(-z));
             v = z * sg;
             tile2[lane * 33 + j] = sg * (1.f + z * (1.f - sg));
           }

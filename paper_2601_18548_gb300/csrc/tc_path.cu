@@ -122,16 +122,6 @@ constexpr int B_FL0 = 2 * kStages + 8;
 
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
 
-// Epilogue column ownership.  kAllWarps: every epilogue warp processes 32
-// columns of both accumulator halves of every step (all 16 warps work on a
-// half as soon as its chain completes); otherwise 8 warps own each half with 64
-// columns per warp (the two halves' epilogues overlap each other instead).
-#ifndef GCDF_TC_ALLWARPS
-#define GCDF_TC_ALLWARPS 1
-#endif
-constexpr bool kAllWarps = GCDF_TC_ALLWARPS != 0;
-constexpr int kHalfArrivals = kAllWarps ? 2 * 16 : 16;  // epilogue-warp arrivals per half, both CTAs
-
 __device__ __forceinline__ uint32_t bar(uint32_t base, int i) { return base + kOffBar + 8 * i; }
 
 // Wait used by the single-thread producer and MMA roles: gives up early when
@@ -442,14 +432,14 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     }
     ptx::mbar_init(bar(base, B_ACC0 + 0), 1);
     ptx::mbar_init(bar(base, B_ACC0 + 1), 1);
-    ptx::mbar_init(bar(base, B_ED0 + 0), kHalfArrivals);  // the half's warps x 2 CTAs
-    ptx::mbar_init(bar(base, B_ED0 + 1), kHalfArrivals);
+    ptx::mbar_init(bar(base, B_ED0 + 0), kEpiWarps);  // 8 warps of the half x 2 CTAs
+    ptx::mbar_init(bar(base, B_ED0 + 1), kEpiWarps);
     ptx::mbar_init(bar(base, B_FD), kEpiThreads);
     ptx::mbar_init(bar(base, B_PD), kEpiWarps);
     ptx::mbar_init(bar(base, B_MD), 1);
     ptx::mbar_init(bar(base, B_ACCJ), 1);
-    ptx::mbar_init(bar(base, B_FL0 + 0), kHalfArrivals);
-    ptx::mbar_init(bar(base, B_FL0 + 1), kHalfArrivals);
+    ptx::mbar_init(bar(base, B_FL0 + 0), kEpiWarps);
+    ptx::mbar_init(bar(base, B_FL0 + 1), kEpiWarps);
     ptx::fence_barrier_init();
     ptx::prefetch_tensormap(&map_w);
     ptx::prefetch_tensormap(&map_j);
@@ -617,12 +607,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     const int e = warp - 2;
     const int quad = warp & 3;
     const int kq = e >> 2;                 // 0..3: split of the output stage's gradient components
-    const int hg = kq >> 1;                // split ownership: the half this warp processes in every step
-    const int cw = hg * kHalf + 64 * (kq & 1);  // split ownership: first of its 64 columns
-    // this warp's columns in half h: [col0(h), col0(h) + kCols); its A_i / 2 pairs start at aiw[aio(h)]
-    constexpr int kCols = kAllWarps ? 32 : 64;
-    auto col0 = [&](int h) -> int { return kAllWarps ? h * kHalf + 32 * kq : cw; };
-    auto aio = [&](int h) -> int { return kAllWarps ? 16 * h : 0; };
+    const int hg = kq >> 1;                // the half this warp processes in every step
+    const int cw = hg * kHalf + 64 * (kq & 1);  // first of its 64 columns
     const int row = quad * 32 + lane;
     const uint32_t t_lane = tmem + ((uint32_t)(quad * 32) << 16);
     const int n = w.n_dof;
@@ -630,8 +616,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     const int r7 = row & 7;
     uint32_t* aiw = s_aiw + e * 32;        // f16x2 A_i / 2 for this thread's 32 + 32 columns
     float* trigw = reinterpret_cast<float*>(gbase + kOffTrig) + e * 2 * 24;  // this warp's sin, cos (2 tiles)
-    uint32_t acc_n = 0;                    // completions of ACC half 0 (all-warps) / this warp's half consumed
-    uint32_t acc_n1 = 0;                   // all-warps: completions of ACC half 1 consumed
+    uint32_t acc_n = 0;                    // completions of this warp's ACC half consumed
     bool ok = true;
 
     int t = 0, wp = 0, start = 0, len = 0;
@@ -668,7 +653,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       }
     };
     auto epi_done = [&](int h) { arrive_lead(B_ED0 + h); };
-    auto fl_done = [&](int h) { arrive_lead(B_FL0 + h); };
+    auto fl_done = [&]() { arrive_lead(B_FL0 + hg); };
     auto load_tile = [&](int it) {
       t = 2 * (cluster + it * nclusters) + (int)rank;
       if (t < ntiles) {
@@ -690,33 +675,28 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       px2 = ptx::pack_f16x2(px, px);
       py2 = ptx::pack_f16x2(py, py);
       pz2 = ptx::pack_f16x2(pz, pz);
-      const float* Ai = w.A + (size_t)wp * kH;
-      const int ca = kAllWarps ? (lane < 16 ? col0(0) + 2 * lane : col0(1) + 2 * (lane - 16)) : cw + 2 * lane;
+      const float* Ai = w.A + (size_t)wp * kH + cw;
       __syncwarp();
-      aiw[lane] = ptx::pack_f16x2(0.5f * Ai[ca], 0.5f * Ai[ca + 1]);
+      aiw[lane] = ptx::pack_f16x2(0.5f * Ai[2 * lane], 0.5f * Ai[2 * lane + 1]);
       if (lane < 2 * w.n_ang) trigw[(it & 1) * 24 + lane] = w.trig[(size_t)wp * 2 * w.n_ang + lane];
       __syncwarp();
     };
     // h_1 = s(A_i + W_1p p) for this row and the warp's 64 columns -> A buffer (tile parity)
     auto first_layer = [&](int it) {
       const uint32_t abuf = base + ((tile_par(it) & 1) ? kOffA1 : kOffA0);
+      const int c0 = cw;
 #pragma unroll 1
-      for (int hh = 0; hh < (kAllWarps ? 2 : 1); ++hh) {
-        const int h = kAllWarps ? hh : hg;
-        const int c0 = col0(h);
-#pragma unroll 1
-        for (int cc = 0; cc < kCols; cc += 16) {
-          uint32_t o[8];
+      for (int cc = 0; cc < 64; cc += 16) {
+        uint32_t o[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const uint32_t u = first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[aio(h) + cc / 2 + i], px2, py2, pz2);
-            const uint32_t tt = ptx::htanh2(u);
-            o[i] = to_operand<kFmt>(ptx::hfma2(u, tt, u));
-          }
-          store8c(abuf, c0 + cc, o);
+        for (int i = 0; i < 8; ++i) {
+          const uint32_t u = first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2);
+          const uint32_t tt = ptx::htanh2(u);
+          o[i] = to_operand<kFmt>(ptx::hfma2(u, tt, u));
         }
-        fl_done(h);
+        store8c(abuf, c0 + cc, o);
       }
+      fl_done();
     };
     // With L = 4 and FP16 operands the next tile's h_1 is computed early, in the
     // slack of the last reverse step, into this warp's z_2 stash columns (read by
@@ -724,41 +704,30 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     // arithmetic).  Measured: 1.4 % faster with FP16 operands, 1.7 % slower with
     // BF16 ones, where the tile tail computes the first layer itself.
     const bool early_h1 = kF16 && L == 4 && !fwd;
+    const uint32_t t_h1 = t_lane + 256 + (cw >> 1);
     auto first_layer_tmem = [&]() {
 #pragma unroll 1
-      for (int hh = 0; hh < (kAllWarps ? 2 : 1); ++hh) {
-        const int h = kAllWarps ? hh : hg;
-        const int c0 = col0(h);
-        const uint32_t t_h1 = t_lane + 256 + (c0 >> 1);
-#pragma unroll 1
-        for (int cc = 0; cc < kCols; cc += 16) {
-          uint32_t o[8];
+      for (int cc = 0; cc < 64; cc += 16) {
+        uint32_t o[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const uint32_t u = first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[aio(h) + cc / 2 + i], px2, py2, pz2);
-            const uint32_t tt = ptx::htanh2(u);
-            o[i] = to_operand<kFmt>(ptx::hfma2(u, tt, u));
-          }
-          ptx::tmem_st8(t_h1 + cc / 2, o);
+        for (int i = 0; i < 8; ++i) {
+          const uint32_t u = first_layer_u2(s_w1p[(cw + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2);
+          const uint32_t tt = ptx::htanh2(u);
+          o[i] = to_operand<kFmt>(ptx::hfma2(u, tt, u));
         }
+        ptx::tmem_st8(t_h1 + cc / 2, o);
       }
       ptx::tmem_wait_st();
     };
     auto first_layer_copy = [&](int it) {
       const uint32_t abuf = base + ((tile_par(it) & 1) ? kOffA1 : kOffA0);
-#pragma unroll 1
-      for (int hh = 0; hh < (kAllWarps ? 2 : 1); ++hh) {
-        const int h = kAllWarps ? hh : hg;
-        const int c0 = col0(h);
-        const uint32_t t_h1 = t_lane + 256 + (c0 >> 1);
-        uint32_t v[32];
-        ptx::tmem_ld16(t_h1, v);
-        if (kCols > 32) ptx::tmem_ld16(t_h1 + 16, v + 16);
-        ptx::tmem_wait_ld();
+      uint32_t v[32];
+      ptx::tmem_ld16(t_h1, v);
+      ptx::tmem_ld16(t_h1 + 16, v + 16);
+      ptx::tmem_wait_ld();
 #pragma unroll
-        for (int q = 0; q < kCols / 16; ++q) store8c(abuf, c0 + 16 * q, v + 8 * q);
-        fl_done(h);
-      }
+      for (int q = 0; q < 4; ++q) store8c(abuf, cw + 16 * q, v + 8 * q);
+      fl_done();
     };
 
     if (my_tiles > 0) {
@@ -771,14 +740,12 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       const bool h1_early = early_h1 && it + 1 < my_tiles;
       for (int s = 0; s < n_steps && ok; ++s) {
         const uint32_t obuf = base + (((tile_par(it) + s + 1) & 1) ? kOffA1 : kOffA0);
-#pragma unroll 1
-        for (int hh = 0; hh < (kAllWarps ? 2 : 1); ++hh) {
-          const int h = kAllWarps ? hh : hg;
-          uint32_t& acc_cnt = (kAllWarps && h == 1) ? acc_n1 : acc_n;
-          if (!wait_epi_warp(bar(base, B_ACC0 + h), acc_cnt & 1u, abort_flag, tw.err)) { ok = false; break; }
-          ++acc_cnt;
+        {
+          const int h = hg;
+          if (!wait_epi_warp(bar(base, B_ACC0 + h), acc_n & 1u, abort_flag, tw.err)) { ok = false; break; }
+          ++acc_n;
           ptx::tc_fence_after();
-          const int c0 = col0(h);                 // first of this warp's columns in half h
+          const int c0 = cw;                      // first of this warp's 64 columns
           const uint32_t t_acc = t_lane + c0;     // accumulator half h starts at column h * 128
           if (s < L - 2) {
             // middle forward layer l = s + 2: h_l -> A, 2 s'(z_l) -> stash
@@ -788,7 +755,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
             // two 16-column chunks are loaded at once, so the second load's
             // latency hides behind the first chunk's arithmetic
 #pragma unroll 1
-            for (int cp = 0; cp < kCols; cp += 32) {
+            for (int cp = 0; cp < 64; cp += 32) {
             uint32_t va[16], vb[16];
             ptx::tmem_ld16(t_acc + cp, va);
             ptx::tmem_ld16(t_acc + cp + 16, vb);
@@ -803,9 +770,9 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               for (int i = 0; i < 8; ++i) {
                 const uint32_t zp = kF8 ? ptx::pack_f16x2(sc * __uint_as_float(v[2 * i]), sc * __uint_as_float(v[2 * i + 1]))
                                         : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-                uint32_t hq;
-                silu2(ptx::hfma2(zp, kHalf2, bh[i]), hq, st2[i]);
-                o[i] = to_operand<kFmt>(hq);
+                uint32_t hh;
+                silu2(ptx::hfma2(zp, kHalf2, bh[i]), hh, st2[i]);
+                o[i] = to_operand<kFmt>(hh);
               }
               store8c(obuf, c0 + cc, o);
               if (!fwd) ptx::tmem_st8(t_st + cc / 2, st2);
@@ -814,11 +781,11 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
             if (!fwd) ptx::tmem_wait_st();
           } else if (s == L - 2) {
             // last forward layer: f partial (FP32 sum), g_L = w_o s'(z_L) -> A
-            if (hh == 0) fpart = 0.f;
+            fpart = 0.f;
             const float sc = kF8 ? tw.fp8_scale[L - 2] : 1.f;
             const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + (L - 2) * (kH / 2) + (c0 >> 1));
 #pragma unroll 1
-            for (int cc = 0; cc < kCols; cc += 16) {
+            for (int cc = 0; cc < 64; cc += 16) {
               uint32_t v[16];
               ptx::tmem_ld16(t_acc + cc, v);
               const uint4 b0 = bh4[cc / 8], b1 = bh4[cc / 8 + 1];
@@ -832,18 +799,16 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               for (int i = 0; i < 8; ++i) {
                 const uint32_t zp = kF8 ? ptx::pack_f16x2(sc * __uint_as_float(v[2 * i]), sc * __uint_as_float(v[2 * i + 1]))
                                         : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-                uint32_t hq, s2;
-                silu2(ptx::hfma2(zp, kHalf2, bh[i]), hq, s2);
+                uint32_t hh, s2;
+                silu2(ptx::hfma2(zp, kHalf2, bh[i]), hh, s2);
                 const float2 wo = *reinterpret_cast<const float2*>(s_wo + c0 + cc + 2 * i);
-                fpart = fmaf(wo.x, ptx::f16lo(hq), fmaf(wo.y, ptx::f16hi(hq), fpart));
+                fpart = fmaf(wo.x, ptx::f16lo(hh), fmaf(wo.y, ptx::f16hi(hh), fpart));
                 o[i] = to_operand<kFmt>(ptx::hmul2(wh[i], s2));
               }
               if (!fwd) store8c(obuf, c0 + cc, o);
             }
-            if (hh == (kAllWarps ? 1 : 0)) {
-              s_f[kq * kTile + row] = fpart;
-              ptx::mbar_arrive(bar(base, B_FD));
-            }
+            s_f[kq * kTile + row] = fpart;
+            ptx::mbar_arrive(bar(base, B_FD));
           } else {
             // reverse step: g_{l-1} = acc * 2 s'(z_{l-1}), acc = (W_l^T / 2) g_l
             const int lm1 = 2 * L - 2 - s;
@@ -854,7 +819,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
             const int lsrc = (lm1 >= 2) ? lm1 : (L - 1);
             const bool stashed = lm1 >= 2 || L >= 3;
 #pragma unroll 1
-            for (int cc = 0; cc < kCols; cc += 16) {
+            for (int cc = 0; cc < 64; cc += 16) {
               uint32_t v[16], d2[8];
               ptx::tmem_ld16(t_acc + cc, v);
               if (stashed) ptx::tmem_ld8(t_lane + 256 + 128 * (lsrc - 2) + ((c0 + cc) >> 1), d2);
@@ -862,8 +827,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               if (!stashed) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                  uint32_t hq;
-                  silu2(first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[aio(h) + cc / 2 + i], px2, py2, pz2), hq, d2[i]);
+                  uint32_t hh;
+                  silu2(first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2), hh, d2[i]);
                 }
               }
               uint32_t o[8];
@@ -884,34 +849,28 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
           }
           // (forward-only: the last step produces no operand, so no MMA waits for it)
           if (!(fwd && s == n_steps - 1)) epi_done(h);
-        }
-        if (!ok) break;
-        if (s == L - 1 && L >= 3) {
-          // the first reverse step has read this warp's stash columns of z_{L-1}:
-          // recompute 2 s'(z_1) = 2 s'(A_i + W_1p p) into them while the tensor
-          // core runs the next reverse chains (the last reverse step loads it)
-#pragma unroll 1
-          for (int hh = 0; hh < (kAllWarps ? 2 : 1); ++hh) {
-            const int h = kAllWarps ? hh : hg;
-            const int c0 = col0(h);
+          if (s == L - 1 && L >= 3) {
+            // the first reverse step has read this warp's stash columns of z_{L-1}:
+            // recompute 2 s'(z_1) = 2 s'(A_i + W_1p p) into them while the tensor
+            // core runs the next reverse chains (the last reverse step loads it)
             const uint32_t t_r1 = t_lane + 256 + 128 * (L - 3) + (c0 >> 1);
 #pragma unroll 1
-            for (int cc = 0; cc < kCols; cc += 16) {
+            for (int cc = 0; cc < 64; cc += 16) {
               uint32_t d2[8];
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                uint32_t hq;
-                silu2(first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[aio(h) + cc / 2 + i], px2, py2, pz2), hq, d2[i]);
+                uint32_t hh;
+                silu2(first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2), hh, d2[i]);
               }
               ptx::tmem_st8(t_r1 + cc / 2, d2);
             }
+            ptx::tmem_wait_st();
           }
-          ptx::tmem_wait_st();
-        }
-        if (h1_early && s == 2 * L - 4) {
-          // the z_2 stash columns of this warp have been read: the next tile's h_1
-          load_tile(it + 1);
-          first_layer_tmem();
+          if (h1_early && s == 2 * L - 4) {
+            // the z_2 stash columns of this warp have been read: the next tile's h_1
+            load_tile(it + 1);
+            first_layer_tmem();
+          }
         }
       }
       if (!ok) break;
@@ -933,7 +892,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
           // the next first layer's buffer was last read by an earlier step, whose
           // MMAs completed before this step's accumulator; the half-1 wait keeps
           // both halves' warps one step apart, as in the full sweep
-          if (!kAllWarps && hg == 0) {
+          if (hg == 0) {
             if (!wait_epi_warp(bar(base, B_ACC0 + 1), (acc_n - 1u) & 1u, abort_flag, tw.err)) { ok = false; break; }
             ptx::tc_fence_after();
           }
@@ -949,8 +908,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         // step's chains read: the warps of half 0 have seen only their own chain
         // complete, so they wait for the half-1 chain (its commit follows every
         // earlier MMA; it cannot complete again before this first layer is done)
-        // (with all-warps ownership every warp has consumed the half-1 chain itself)
-        if (!kAllWarps && hg == 0) {
+        if (hg == 0) {
           if (!wait_epi_warp(bar(base, B_ACC0 + 1), (acc_n - 1u) & 1u, abort_flag, tw.err)) { ok = false; break; }
           ptx::tc_fence_after();
         }

@@ -246,6 +246,7 @@ def test_bf16_is_deterministic_and_reduces_to_the_first_order_vjp():
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
     # vjp2 at G = 0 is the first-order product; with BF16 operands vjp sums the
     # bias gradients per 32-row block first, so the two agree up to that order
+    # (the activations, s' and every product operand are the same to the bit)
     c = g.fit_vjp2((n, H, L), wd, qd, pd, gf, torch.zeros_like(qd), precision="bf16")
     assert float(torch.linalg.norm(c - a[0]) / torch.linalg.norm(a[0])) <= 1e-6
     f, _ = g.fit_value_grad((n, H, L), wd, qd, pd, precision="bf16")
