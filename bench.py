@@ -489,6 +489,18 @@ def gpu_extras(g, torch, dev, wl, net, args, peaks):
                         "peak_source": "measured FP32 FMA loop (gcdf_diag_fp32_fma): " + fma["launch"],
                         "bound": "alu"}
     peak = float(peaks["bf16_tflops"])
+    # value-only query (forward layers alone: the first pass of the HINGE / MIN active sets)
+    if args.precision in ("bf16", "fp16"):
+        fbuf = torch.empty(wl.n_pairs, device=dev)
+        msv = _kernel_ms(g, torch, net, lambda: g.query(net, q, p, with_grad=False, out=(fbuf, None)), 5, flush)
+        H, L = s.hidden, s.n_layers
+        fwd_fpp = (L - 1) * 2 * H * H + 2 * H + H
+        out["value_only_query"] = {"kernel_ms": msv, "pairs_per_s": wl.n_pairs / (msv / 1e3),
+                                   "flops_per_pair": fwd_fpp,
+                                   "achieved_tflops": fwd_fpp * wl.n_pairs / (msv / 1e3) / 1e12,
+                                   "frac": fwd_fpp * wl.n_pairs / (msv / 1e3) / 1e12 / peak,
+                                   "note": "f only (no reverse sweep), per-pair f written to HBM"}
+        del fbuf
     sweep = []
     if args.precision in ("bf16", "fp16"):
         for (N, M) in ((128, 65536), (512, 16384), (512, 65536), (2048, 16384), (2048, 65536)):

@@ -372,7 +372,9 @@ __device__ __forceinline__ void warp_combine_quads(int mode, float T, const Part
 }
 
 // kFmt: operand format, 0 = BF16, 1 = FP16, 2 = FP8 E4M3 (per-layer scales).
-template <int kFmt>
+// kFwd: value-only queries (the forward steps alone), a separate instantiation
+// so that the full sweep carries none of its branches.
+template <int kFmt, bool kFwd>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
                 const __grid_constant__ CUtensorMap map_j, const TcWeights tw) {
@@ -393,7 +395,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
   const int L = tw.L;
   // A query without a gradient output (value-only) runs the forward steps
   // alone: no stash, no reverse steps, no input-Jacobian chain.
-  const bool fwd = (w.mode == kQuery && w.g_out == nullptr);
+  constexpr bool fwd = kFwd;  // launched for w.mode == kQuery with w.g_out == nullptr
   const int n_steps = fwd ? (L - 1) : 2 * (L - 1);  // weight steps per tile (forward, then reverse)
   // A-buffer parity: step s of tile `it` reads buffer (tile_par(it) + s) & 1
   // and its epilogue writes the other one; a tile's first layer goes to
@@ -1117,7 +1119,7 @@ int tc_encode_maps(const void* image, int H, int L, int d_q, int fmt, TcWeights&
                    tc_nj(d_q) / 2, fmt);
 }
 
-template <int kFmt>
+template <int kFmt, bool kFwd>
 cudaError_t launch_tc_t(const WorkDesc& w, const TcWeights& tw, int num_sms, cudaStream_t s) {
   // clusters of 2 CTAs (one per SM); as many as can be resident at once, each
   // looping over pair tiles
@@ -1138,10 +1140,11 @@ cudaError_t launch_tc_t(const WorkDesc& w, const TcWeights& tw, int num_sms, cud
   cfg.numAttrs = 1;
   int mc = cached ? max_clusters[dev] : 0;
   if (mc <= 0) {
-    cudaError_t e = cudaFuncSetAttribute(tc_fused_kernel<kFmt>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(tc_fused_kernel<kFmt, kFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBytes);
     if (e != cudaSuccess) return e;
     cfg.gridDim = dim3(2);
-    e = cudaOccupancyMaxActiveClusters(&mc, (void*)tc_fused_kernel<kFmt>, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&mc, (void*)tc_fused_kernel<kFmt, kFwd>, &cfg);
     if (e != cudaSuccess) return e;
     if (mc <= 0) return cudaErrorLaunchOutOfResources;
     if (cached) max_clusters[dev] = mc;
@@ -1150,7 +1153,7 @@ cudaError_t launch_tc_t(const WorkDesc& w, const TcWeights& tw, int num_sms, cud
   const int npt = (w.n_tiles + 1) / 2;
   if (npt <= 0) return cudaSuccess;
   cfg.gridDim = dim3(2 * (npt < mc ? npt : mc));
-  return cudaLaunchKernelEx(&cfg, tc_fused_kernel<kFmt>, w, tw.map_w, tw.map_j, tw);
+  return cudaLaunchKernelEx(&cfg, tc_fused_kernel<kFmt, kFwd>, w, tw.map_w, tw.map_j, tw);
 }
 
 cudaError_t launch_wait_expiry_probe(int* err, long long limit_cycles, int* seen, cudaStream_t s) {
@@ -1159,8 +1162,12 @@ cudaError_t launch_wait_expiry_probe(int* err, long long limit_cycles, int* seen
 }
 
 cudaError_t launch_tc(const WorkDesc& w, const TcWeights& tw, int num_sms, cudaStream_t s) {
-  if (tw.fmt == 2) return launch_tc_t<2>(w, tw, num_sms, s);
-  return tw.fmt == 1 ? launch_tc_t<1>(w, tw, num_sms, s) : launch_tc_t<0>(w, tw, num_sms, s);
+  if (w.mode == kQuery && w.g_out == nullptr) {
+    if (tw.fmt == 2) return launch_tc_t<2, true>(w, tw, num_sms, s);
+    return tw.fmt == 1 ? launch_tc_t<1, true>(w, tw, num_sms, s) : launch_tc_t<0, true>(w, tw, num_sms, s);
+  }
+  if (tw.fmt == 2) return launch_tc_t<2, false>(w, tw, num_sms, s);
+  return tw.fmt == 1 ? launch_tc_t<1, false>(w, tw, num_sms, s) : launch_tc_t<0, false>(w, tw, num_sms, s);
 }
 
 }  // namespace gcdf
