@@ -96,8 +96,8 @@ constexpr int kOffWo = kOffW1p + (kH / 2) * 16;                 // [H] fp32 w_o
 constexpr int kOffWoh = kOffWo + kH * 4;                        // [H/2] f16x2 w_o / 2
 constexpr int kOffAiw = kOffWoh + (kH / 2) * 4;                 // [16 warps][32] f16x2 A_i / 2
 constexpr int kOffTrig = kOffAiw + kEpiWarps * 32 * 4;          // [16 warps][2 tiles][24] sin, cos
-constexpr int kOffF = kOffTrig + kEpiWarps * 2 * 24 * 4;        // [4][128] f partials
-constexpr int kOffPart = kOffF + 4 * kTile * 4;                 // 4 partial records
+constexpr int kOffF = kOffTrig + kEpiWarps * 2 * 24 * 4;        // [2 tiles][4][128] f partials
+constexpr int kOffPart = kOffF + 2 * 4 * kTile * 4;             // 4 partial records
 constexpr int kOffBar = kOffPart + 4 * (int)sizeof(Partial);
 constexpr int kNumBars = 2 * kStages + 10;
 constexpr int kOffSlot = kOffBar + kNumBars * 8;
@@ -809,7 +809,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               }
               if (!fwd) store8c(obuf, c0 + cc, o);
             }
-            s_f[kq * kTile + row] = fpart;
+            s_f[(it & 1) * 4 * kTile + kq * kTile + row] = fpart;
             ptx::mbar_arrive(bar(base, B_FD));
           } else {
             // reverse step: g_{l-1} = acc * 2 s'(z_{l-1}), acc = (W_l^T / 2) g_l
@@ -878,27 +878,24 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       if (!ok) break;
 
       if (fwd) {
-        // ---- forward-only tile tail: f of this tile, then the next tile's first
-        // layer.  The output comes first so that every warp has read this tile's
-        // f partials before it releases the next tile's first step (which
-        // rewrites them when L = 2).
+        // ---- forward-only tile tail: the next tile's first layer as soon as this
+        // warp's half of the last step is done (its buffer was last read by an
+        // earlier step, whose MMAs completed before this step's accumulator; the
+        // accumulator half it frees was read only by this half's warps), then f of
+        // this tile.  The f partials alternate between two buffers by tile parity:
+        // a tile two ahead, which rewrites this buffer, cannot start before every
+        // warp has released its first layer, which each does after this output.
+        if (it + 1 < my_tiles) {
+          load_tile(it + 1);
+          first_layer(it + 1);
+        }
         if (!wait_epi_warp(bar(base, B_FD), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }
         if (kq == 0 && row < cur_len) {
           int j;
           long long k;
           pair_at(w, cur_wp, cur_start + row, j, k);
-          w.f_out[k] = s_f[row] + s_f[kTile + row] + s_f[2 * kTile + row] + s_f[3 * kTile + row] + tw.bout;
-        }
-        if (it + 1 < my_tiles) {
-          load_tile(it + 1);
-          // the next first layer's buffer was last read by an earlier step, whose
-          // MMAs completed before this step's accumulator; the half-1 wait keeps
-          // both halves' warps one step apart, as in the full sweep
-          if (hg == 0) {
-            if (!wait_epi_warp(bar(base, B_ACC0 + 1), (acc_n - 1u) & 1u, abort_flag, tw.err)) { ok = false; break; }
-            ptx::tc_fence_after();
-          }
-          first_layer(it + 1);
+          const float* sf = s_f + (it & 1) * 4 * kTile;
+          w.f_out[k] = sf[row] + sf[kTile + row] + sf[2 * kTile + row] + sf[3 * kTile + row] + tw.bout;
         }
         continue;
       }
@@ -930,7 +927,8 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         const int d = kq + 4 * m;
         ptx::tmem_ld2(t_lane + 384 + (d < 2 ? 0 : 2 * d - 2), jv[m]);
       }
-      const float fval = s_f[row] + s_f[kTile + row] + s_f[2 * kTile + row] + s_f[3 * kTile + row] + tw.bout;
+      const float* sf = s_f + (it & 1) * 4 * kTile;
+      const float fval = sf[row] + sf[kTile + row] + sf[2 * kTile + row] + sf[3 * kTile + row] + tw.bout;
       ptx::tmem_wait_ld();
       const float* tr = trigw + (it & 1) * 24;
       if (kF8) {  // J = (s_J / 64) x the accumulator of FP8 W_1q^T and the x64 operand
