@@ -615,6 +615,108 @@ __global__ void seed_images_kernel(const float* __restrict__ g, const float* __r
   }
 }
 
+// u = C^T G (the adjoint of the sin/cos chain rule) as BF16 images Ur (B x ldr)
+// and Uc (d_in x ldc), with the arithmetic of dq_adjoint_kernel.
+__global__ void adjoint_images_kernel(const float* __restrict__ q, const float* __restrict__ G, int B, int n,
+                                      int d_in, __nv_bfloat16* __restrict__ Ur, long long ldr,
+                                      __nv_bfloat16* __restrict__ Uc, long long ldc) {
+  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x) {
+    float u[3 + 2 + 2 * kMaxAngles];
+    const float* gb = G + b * n;
+    u[0] = u[1] = u[2] = 0.f;
+    u[3] = gb[0];
+    u[4] = gb[1];
+    for (int a = 0; a < n - 2; ++a) {
+      float sn, cs;
+      sincosf(q[b * n + 2 + a], &sn, &cs);
+      u[5 + 2 * a] = cs * gb[2 + a];
+      u[6 + 2 * a] = -sn * gb[2 + a];
+    }
+    for (int k = 0; k < d_in; ++k) {
+      const __nv_bfloat16 v = __float2bfloat16_rn(u[k]);
+      Ur[b * ldr + k] = v;
+      Uc[(long long)k * ldc + b] = v;
+    }
+  }
+}
+
+// One layer of the second-order sweep, element-wise on a 32 x 32 tile (block
+// (32, 8)): E = r * a * s''(z) (a = A, or the broadcast row wo when A is NULL;
+// E may alias A) and rs = r * s'(z) as BF16 images (row-major rsr, transposed
+// rsc with row stride ldc; either may be NULL) and per-32-row column sums cs
+// (NULL: none); the arithmetic of second_kernel and mul2_kernel.
+__global__ void second_images_kernel(const float* __restrict__ R, const float* A, const float* __restrict__ wo,
+                                     const float* __restrict__ S1, const float* __restrict__ S2, int B, int H,
+                                     float* E, __nv_bfloat16* __restrict__ rsr, __nv_bfloat16* __restrict__ rsc,
+                                     long long ldc, float* __restrict__ cs) {
+  __shared__ float t[32][33];
+  const long long r0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int c = c0 + tx;
+  for (int i = ty; i < 32; i += 8) {
+    const long long r = r0 + i;
+    float v = 0.f;
+    if (r < B && c < H) {
+      const long long e = r * H + c;
+      const float rv = R[e];
+      E[e] = rv * (A ? A[e] : wo[c]) * S2[e];
+      v = rv * S1[e];
+      if (rsr) rsr[e] = __float2bfloat16_rn(v);
+    }
+    t[i][tx] = v;
+  }
+  __syncthreads();
+  if (cs && ty == 0 && c < H) {
+    float sum = 0.f;
+    for (int i = 0; i < 32; ++i)
+      if (r0 + i < B) sum += t[i][tx];
+    cs[(long long)blockIdx.x * H + c] = sum;
+  }
+  if (rsc) {
+    for (int i = ty; i < 32; i += 8) {
+      const int cc = c0 + i;
+      const long long r = r0 + tx;
+      if (cc < H && r < B) rsc[(long long)cc * ldc + r] = __float2bfloat16_rn(t[tx][i]);
+    }
+  }
+}
+
+// eps_L = E_L + g w_o * s'(z_L) as BF16 images (row-major Er, transposed Ec)
+// and per-32-row column sums cs; the arithmetic of seed_add_kernel.
+__global__ void eps_seed_images_kernel(const float* __restrict__ Ein, const float* __restrict__ g,
+                                       const float* __restrict__ wo, const float* __restrict__ S, int B, int H,
+                                       __nv_bfloat16* __restrict__ Er, __nv_bfloat16* __restrict__ Ec, long long ldc,
+                                       float* __restrict__ cs) {
+  __shared__ float t[32][33];
+  const long long r0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int c = c0 + tx;
+  for (int i = ty; i < 32; i += 8) {
+    const long long r = r0 + i;
+    float v = 0.f;
+    if (r < B && c < H) {
+      const long long e = r * H + c;
+      v = Ein[e] + g[r] * wo[c] * S[e];
+      Er[e] = __float2bfloat16_rn(v);
+    }
+    t[i][tx] = v;
+  }
+  __syncthreads();
+  if (ty == 0 && c < H) {
+    float sum = 0.f;
+    for (int i = 0; i < 32; ++i)
+      if (r0 + i < B) sum += t[i][tx];
+    cs[(long long)blockIdx.x * H + c] = sum;
+  }
+  for (int i = ty; i < 32; i += 8) {
+    const int cc = c0 + i;
+    const long long r = r0 + tx;
+    if (cc < H && r < B) Ec[(long long)cc * ldc + r] = __float2bfloat16_rn(t[tx][i]);
+  }
+}
+
 struct Bf16Fwd {
   __nv_bfloat16* Xr = nullptr;  // v, B x ldx
   __nv_bfloat16* Xc = nullptr;  // v^T, d_in x ldb (kept for dW_1)
@@ -648,10 +750,10 @@ cudaError_t alloc_bf16(Ws& ws, const Shape& sh, int B, bool keep_cols, bool rev,
   return cudaSuccess;
 }
 
-// Forward pass on images: S_l = s'(z_l) (Ss[l-1], may be NULL), h_L in FP32
-// (HL), f (may be NULL).
+// Forward pass on images: S_l = s'(z_l) (Ss[l-1], may be NULL), s''(z_l) (S2s,
+// may be NULL), h_L in FP32 (HL), f (may be NULL).
 int forward_bf16(const Shape& sh, const float* w, const float* q, const float* p, int B, Bf16Fwd& bf, float** Ss,
-                 float* HL, float* f, Ctx& cx) {
+                 float* HL, float* f, Ctx& cx, float** S2s = nullptr) {
   const cudaStream_t s = cx.s;
   cudaError_t e;
   encode_bf16_kernel<<<grid1(B), 256, 0, s>>>(q, p, B, sh.n, sh.d_in, bf.Xr, bf.ldx, bf.Xc, bf.ldb);
@@ -666,6 +768,7 @@ int forward_bf16(const Shape& sh, const float* w, const float* q, const float* p
     ep.mode = kEpiBiasSilu;
     ep.bias = W + (size_t)sh.H * K;
     ep.s_out = Ss ? Ss[l - 1] : nullptr;
+    ep.s2_out = S2s ? S2s[l - 1] : nullptr;
     ep.ld_s = sh.H;
     if (l < sh.L) {
       ep.img = bf.Hr[l];
@@ -745,6 +848,111 @@ int reverse_bf16(const Shape& sh, int B, Bf16Fwd& bf, float** Ss, const float* g
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit backward launch: %s", cudaGetErrorString(e));
+  return GCDF_OK;
+}
+
+// Second-order weight VJP (gcdf_fit_vjp2) on images: the generic scheme's
+// arithmetic and rounding points, with every product operand written as BF16
+// images by its producer (forward and back-product epilogues, the element-wise
+// kernels above) and the bias gradients summed per 32-row block.
+int vjp2_bf16(const Shape& sh, const float* w, const float* q, const float* p, int B, const float* g_f,
+              const float* G_q, float* dweights, Ws& ws, cudaStream_t s) {
+  const int H = sh.H, L = sh.L;
+  const long long n = (long long)B * H;
+  const long long nblk = (B + 31) / 32;
+  const size_t pfl = (size_t)64 * H * (H > sh.d_in ? H : sh.d_in);
+  cudaError_t e;
+  int rc;
+  Bf16Fwd bf;
+  float *S1[17], *S2[17], *AE[17];
+  float *HL = nullptr, *R = nullptr, *cs = nullptr, *partials = nullptr;
+  __nv_bfloat16 *Dr[2] = {}, *Dc[17] = {}, *Ur = nullptr, *Uc = nullptr, *rsr = nullptr, *rsc = nullptr;
+  __nv_bfloat16 *Er[2] = {}, *Ec = nullptr;
+  for (int l = 1; l <= L; ++l)
+    if ((e = ws.get(&S1[l - 1], (size_t)n)) || (e = ws.get(&S2[l - 1], (size_t)n)) || (e = ws.get(&AE[l - 1], (size_t)n)) ||
+        (e = ws.get(&Dc[l - 1], (size_t)H * pad8(B))))
+      return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  if ((e = alloc_bf16(ws, sh, B, true, true, bf)) || (e = ws.get(&HL, (size_t)n)) || (e = ws.get(&R, (size_t)n)) ||
+      (e = ws.get(&cs, (size_t)nblk * H)) || (e = ws.get(&partials, pfl)) || (e = ws.get(&Dr[0], (size_t)n)) ||
+      (e = ws.get(&Dr[1], (size_t)n)) || (e = ws.get(&Ur, (size_t)B * bf.ldx)) ||
+      (e = ws.get(&Uc, (size_t)sh.d_in * bf.ldb)) || (e = ws.get(&rsr, (size_t)n)) ||
+      (e = ws.get(&rsc, (size_t)H * bf.ldb)) || (e = ws.get(&Er[0], (size_t)n)) || (e = ws.get(&Er[1], (size_t)n)) ||
+      (e = ws.get(&Ec, (size_t)H * bf.ldb)))
+    return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  Ctx cx;
+  if ((rc = make_ctx_images(cx, s, partials, pfl))) return rc;
+  if ((rc = forward_bf16(sh, w, q, p, B, bf, S1, HL, nullptr, cx, S2))) return rc;
+  const float* wo = w + sh.off_out;
+  float* dwo = dweights + sh.off_out;
+  const dim3 tgrid((unsigned)nblk, (unsigned)((H + 31) / 32)), tblk(32, 8);
+  // the field's reverse sweep: delta_L = w_o s'(z_L); a_{l-1} = delta_l W_l (FP32,
+  // AE[l-2]), delta_{l-1} = a_{l-1} s'(z_{l-1}); transposed images of every delta
+  seed_images_kernel<<<tgrid, tblk, 0, s>>>(nullptr, wo, S1[L - 1], B, H, Dr[0], Dc[L - 1], bf.ldb, nullptr);
+  int cur = 0;
+  for (int l = L; l >= 2; --l) {
+    GemmEpilogue ep{};
+    ep.mode = kEpiMul;
+    ep.s_in = S1[l - 2];
+    ep.acc_out = AE[l - 2];
+    ep.ld_s = H;
+    ep.img = Dr[cur ^ 1];
+    ep.ld_img = H;
+    ep.imgT = Dc[l - 2];
+    ep.ld_imgT = bf.ldb;
+    if ((e = cx.mm_images(Dr[cur], H, bf.Wt[l], H, B, H, H, nullptr, H, false, false, &ep)))
+      return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+    cur ^= 1;
+  }
+  // first-derivative terms: u = C^T G; dW_1 = delta_1^T u; r_1 = u W_1^T
+  adjoint_images_kernel<<<grid1(B), 256, 0, s>>>(q, G_q, B, sh.n, sh.d_in, Ur, bf.ldx, Uc, bf.ldb);
+  if ((e = cx.mm_images(Dc[0], bf.ldb, Uc, bf.ldb, H, sh.d_in, B, dweights, sh.d_in, true, false, nullptr)) ||
+      (e = cx.mm_images(Ur, bf.ldx, bf.Wr[1], bf.ldx, B, H, sh.d_in, R, H, false, false, nullptr)))
+    return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+  for (int l = 1; l <= L; ++l) {
+    // e_l = r a_l s''(z_l) in place of a_l; rs = r s'(z_l)
+    second_images_kernel<<<tgrid, tblk, 0, s>>>(R, l < L ? AE[l - 1] : nullptr, wo, S1[l - 1], S2[l - 1], B, H,
+                                                AE[l - 1], l < L ? rsr : nullptr, l < L ? rsc : nullptr, bf.ldb,
+                                                l < L ? nullptr : cs);
+    if (l < L) {
+      // dW_{l+1} = delta_{l+1}^T rs;  r_{l+1} = rs W_{l+1}^T
+      if ((e = cx.mm_images(Dc[l], bf.ldb, rsc, bf.ldb, H, H, B, dweights + sh.off(l + 1), H, true, false, nullptr)) ||
+          (e = cx.mm_images(rsr, H, bf.Wr[l + 1], H, B, H, H, R, H, false, false, nullptr)))
+        return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+    } else if ((e = colsum(cs, (int)nblk, H, nullptr, dwo, partials, pfl, s))) {  // dw_o = sum_b r_L s'(z_L)
+      return set_error(GCDF_ECUDA, "colsum: %s", cudaGetErrorString(e));
+    }
+  }
+  // value and second-derivative terms (accumulated; biases written)
+  if ((e = colsum(HL, B, H, g_f, dwo, partials, pfl, s, true)) || (e = colsum(g_f, B, 1, nullptr, dwo + H, partials, pfl, s)))
+    return set_error(GCDF_ECUDA, "colsum: %s", cudaGetErrorString(e));
+  eps_seed_images_kernel<<<tgrid, tblk, 0, s>>>(AE[L - 1], g_f, wo, S1[L - 1], B, H, Er[0], Ec, bf.ldb, cs);
+  cur = 0;
+  for (int l = L; l >= 1; --l) {
+    const int K = sh.fan_in(l);
+    const __nv_bfloat16* Bop = l == 1 ? bf.Xc : bf.Hc[l - 1];
+    if ((e = cx.mm_images(Ec, bf.ldb, Bop, bf.ldb, H, K, B, dweights + sh.off(l), K, true, true, nullptr)) ||
+        (e = colsum(cs, (int)nblk, H, nullptr, dweights + sh.off(l) + (size_t)H * K, partials, pfl, s)))
+      return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+    if (l > 1) {
+      // eps_{l-1} = e_{l-1} + (eps_l W_l) s'(z_{l-1})
+      GemmEpilogue ep{};
+      ep.mode = kEpiMul;
+      ep.s_in = S1[l - 2];
+      ep.add_in = AE[l - 2];
+      ep.ld_s = H;
+      ep.img = Er[cur ^ 1];
+      ep.ld_img = H;
+      ep.imgT = Ec;
+      ep.ld_imgT = bf.ldb;
+      ep.colsum = cs;
+      ep.ld_colsum = H;
+      if ((e = cx.mm_images(Er[cur], H, bf.Wt[l], H, B, H, H, nullptr, H, false, false, &ep)))
+        return set_error(GCDF_ECUDA, "gemm: %s", cudaGetErrorString(e));
+      cur ^= 1;
+    }
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit vjp2 launch: %s", cudaGetErrorString(e));
   return GCDF_OK;
 }
 
@@ -975,6 +1183,12 @@ int gcdf_fit_vjp2(const gcdf_fit_desc* desc, const float* weights, const float* 
   }
   if (!g_f || !al16(g_f) || !G_q || !al16(G_q))
     return set_error(GCDF_EINVAL, "g_f or G_q NULL or not 16-byte aligned");
+  if (sh.bf16) {
+    Ws ws(s);
+    if ((rc = vjp2_bf16(sh, weights, q, p, batch, g_f, G_q, dweights, ws, s))) return rc;
+    clear_error();
+    return GCDF_OK;
+  }
   const int H = sh.H, L = sh.L;
   const long long n = (long long)batch * H;
   Ws ws(s);

@@ -237,12 +237,19 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
           const bool ok_rc = col_ok && rr < a.M;
           float x = tile[r * kTileStride + lane];
           if (mul) {
-            x *= ok_rc ? ep.s_in[(long long)rr * ep.ld_s + n] : 0.f;
+            const long long e = (long long)rr * ep.ld_s + n;
+            if (ok_rc && ep.acc_out) ep.acc_out[e] = x;
+            x *= ok_rc ? ep.s_in[e] : 0.f;
+            if (ep.add_in) x += ok_rc ? ep.add_in[e] : 0.f;
           } else if (silu) {
             const float z = x + bias;
             const float sg = __frcp_rn(1.f + expf(-z));
             x = z * sg;
-            if (ok_rc && ep.s_out) ep.s_out[(long long)rr * ep.ld_s + n] = sg * (1.f + z * (1.f - sg));
+            if (ok_rc) {
+              const long long e = (long long)rr * ep.ld_s + n;
+              if (ep.s_out) ep.s_out[e] = sg * (1.f + z * (1.f - sg));
+              if (ep.s2_out) ep.s2_out[e] = sg * (1.f - sg) * (2.f + z * (1.f - 2.f * sg));
+            }
           }
           if (ok_rc) {
             if (cz) {

@@ -9,8 +9,8 @@ namespace gcdf {
 // What the GEMM's epilogue does with the FP32 accumulator tile before storing.
 enum GemmEpiMode : int {
   kEpiStore = 0,     // C = acc (or C += acc)
-  kEpiBiasSilu = 1,  // z = acc + bias[n]: C = s(z), s_out = s'(z) (s2_out is not written)
-  kEpiMul = 2        // C = acc * s_in[m, n]
+  kEpiBiasSilu = 1,  // z = acc + bias[n]: C = s(z), s_out = s'(z), s2_out = s''(z)
+  kEpiMul = 2        // C = acc * s_in[m, n] (+ add_in[m, n] when given); acc_out = acc
 };
 
 // Outputs besides C (each optional, NULL = not written).  img: BF16 copy of
@@ -22,6 +22,8 @@ struct GemmEpilogue {
   int mode;
   const float* bias;
   const float* s_in;
+  const float* add_in;   // kEpiMul: added after the multiply (row stride ld_s), or NULL
+  float* acc_out;        // kEpiMul: the accumulator before the multiply (row stride ld_s), or NULL
   float* s_out;
   float* s2_out;
   long long ld_s;
