@@ -26,8 +26,11 @@
  *    (cudaMalloc and PyTorch allocations are).  Exception: weights_host.
  *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
  *    default stream) and return once the work is enqueued.  Outputs are valid
- *    after the stream reaches that point.  Temporary device memory is taken
- *    with cudaMallocAsync on the same stream and released on it.
+ *    after the stream reaches that point.  Temporary device memory is taken,
+ *    stream-ordered on the same stream, from a memory pool per device that the
+ *    library owns and that keeps freed memory for the next call (so the pool
+ *    holds the largest temporaries used so far; gcdf_release_cached_memory
+ *    returns the unused part to the driver).
  *  - Return value: GCDF_OK or an error code; gcdf_last_error() gives a
  *    message (per calling thread).  Argument errors are detected before any
  *    work is enqueued.
@@ -521,6 +524,11 @@ GCDF_API int gcdf_server_stats_get(gcdf_server *server, gcdf_server_stats *out);
 /* Stop the server thread (after the step in progress) and free its memory.
  * Unfinished requests are dropped.  NULL is a no-op. */
 GCDF_API int gcdf_server_destroy(gcdf_server *server);
+
+/* Return the unused memory of the library's temporary-memory pool on the
+ * current device to the driver (cudaMemPoolTrimTo 0).  Memory of calls still
+ * in flight stays; synchronise first to release everything.  Errors: ECUDA. */
+GCDF_API int gcdf_release_cached_memory(void);
 
 /* Message for the last error returned on the calling thread ("" if none). */
 GCDF_API const char *gcdf_last_error(void);

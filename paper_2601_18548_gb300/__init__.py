@@ -229,6 +229,11 @@ def diag_fp32_fma(blocks: int, threads: int, iters: int, sink: torch.Tensor, str
     return int(r)
 
 
+def release_cached_memory() -> None:
+    """gcdf_release_cached_memory: trim the library's temporary-memory pool."""
+    _lib.check(_lib.load().gcdf_release_cached_memory())
+
+
 def last_error() -> str:
     """gcdf_last_error."""
     m = _lib.load().gcdf_last_error()

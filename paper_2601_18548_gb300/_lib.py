@@ -90,6 +90,7 @@ SIGNATURES = {
     "gcdf_server_stats_get": (_i, [_vp, ctypes.POINTER(ServerStats)]),
     "gcdf_plan_request_bytes": (ctypes.c_size_t, [_vp, _i, _i]),
     "gcdf_server_destroy": (_i, [_vp]),
+    "gcdf_release_cached_memory": (_i, []),
     "gcdf_last_error": (ctypes.c_char_p, []),
 }
 

@@ -282,7 +282,7 @@ struct Ws {
   template <class T>
   cudaError_t get(T** out, size_t count) {
     size_t bytes = count * sizeof(T);
-    cudaError_t e = cudaMallocAsync((void**)out, bytes < 16 ? 16 : bytes, s);
+    cudaError_t e = lib_malloc_async((void**)out, bytes < 16 ? 16 : bytes, s);
     if (e == cudaSuccess) ptrs.push_back(*out);
     return e;
   }

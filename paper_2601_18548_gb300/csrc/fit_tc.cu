@@ -46,9 +46,8 @@ constexpr int B_FULL0 = 0, B_EMPTY0 = kStages, B_ACC = 2 * kStages;
 constexpr int kNumBars = 2 * kStages + 1;
 constexpr int kOffSlot = kOffBar + kNumBars * 8;
 constexpr int kSmemBytes = kOffSlot + 16 + 1024;  // + alignment slack
-// the epilogue's 32 x kTileStride float tile per epilogue warp reuses the idle ring
-constexpr int kTileStride = 36;
-static_assert(8 * 32 * kTileStride * 4 <= kStages * kStageBytes, "epilogue tiles fit in the ring");
+// the epilogue's two 33 x 32 float tiles per epilogue warp reuse the idle ring
+static_assert(8 * 2 * 33 * 32 * 4 <= kStages * kStageBytes, "epilogue tiles fit in the ring");
 constexpr long long kWaitCycles = 2000000000LL;   // ~1 s
 
 struct GemmArgs {
@@ -193,17 +192,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
     ok = __all_sync(0xffffffffu, ok);
     if (ok) {
       ptx::tc_fence_after();
-      // Each 32 x 32 block is transposed through shared memory: the lanes put
-      // their rows of raw accumulators in (lane = row after tcgen05.ld, 128-bit
-      // stores), then work on it column by column (lane = column), so that the
-      // element-wise epilogue loads each column's bias or factor once per block
-      // and every global store writes 32 consecutive values of one row.  The
-      // transposed image goes out from the rows again (lane = row: 64 contiguous
-      // bytes per column).  The operand ring is idle once the accumulator is
-      // complete (every MMA, and so every TMA load, has finished): each warp
-      // uses one 32 x 36 float tile of it (row stride 36: the 128-bit accesses
-      // of every 8-lane phase and the column reads are conflict-free).
-      float* tile = reinterpret_cast<float*>(gbase) + (warp - 2) * (32 * kTileStride);
+      // Each 32 x 32 block (lane = row after tcgen05.ld) is transposed through
+      // shared memory, so that each store instruction writes 32 consecutive
+      // values of one row (one 128-byte line of FP32) instead of one value in
+      // 32 rows.  The operand ring is idle once the accumulator is complete
+      // (every MMA, and so every TMA load, has finished): each warp uses two
+      // 33 x 32 float tiles of it (row stride 33: conflict-free both ways), one
+      // for the result and one for s'(z) or the incoming factor.
+      float* tile = reinterpret_cast<float*>(gbase) + (warp - 2) * (2 * 32 * 33);
+      float* tile2 = tile + 32 * 33;
       const int row0 = tm * 2 * kRowsA + (int)rank * kRowsA + q * 32;
       float* cz = a.C ? a.C + (long long)blockIdx.y * a.zstride : nullptr;
       const int n0 = tn * kTileN;
@@ -214,69 +211,91 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
       for (int c0 = 64 * ch; c0 < 64 * ch + 64; c0 += 32) {
         const int nb = n0 + c0;  // first column of the block
         if (nb >= a.N) break;
+        if (ep.mode == kEpiMul) {
+          // the factor block (and the added block) come in coalesced (lane = column)
+#pragma unroll 4
+          for (int r = 0; r < 32; ++r) {
+            const int rr = row0 + r, n = nb + lane;
+            const bool ok_rc = rr < a.M && n < a.N;
+            tile2[r * 33 + lane] = ok_rc ? ep.s_in[(long long)rr * ep.ld_s + n] : 0.f;
+            if (ep.add_in) tile[r * 33 + lane] = ok_rc ? ep.add_in[(long long)rr * ep.ld_s + n] : 0.f;
+          }
+          __syncwarp();
+        }
         uint32_t u[32];
         ptx::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, u);
         ptx::tmem_wait_ld();
+        // this row's 32 results into the tile (s'(z) into the second tile)
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
-          *reinterpret_cast<uint4*>(tile + lane * kTileStride + 4 * jj) =
-              make_uint4(u[4 * jj], u[4 * jj + 1], u[4 * jj + 2], u[4 * jj + 3]);
-        __syncwarp();
-        // column phase: C (or C += for split partials), s'(z), the BF16 image and
-        // the column sums; the result goes back into the tile for the transposed image
-        const int n = nb + lane;
-        const bool col_ok = n < a.N;
-        // h = s(z), z = acc + b, with the arithmetic of the element-wise kernel of
-        // the generic path (expf, an exactly rounded reciprocal equal to 1 / x):
-        // the same activations and s' to the bit
-        const float bias = (silu && col_ok) ? __ldg(ep.bias + n) : 0.f;
-        float cs = 0.f;
-#pragma unroll 4
-        for (int r = 0; r < 32; ++r) {
-          const int rr = row0 + r;
-          const bool ok_rc = col_ok && rr < a.M;
-          float x = tile[r * kTileStride + lane];
-          if (mul) {
-            const long long e = (long long)rr * ep.ld_s + n;
-            if (ok_rc && ep.acc_out) ep.acc_out[e] = x;
-            x *= ok_rc ? ep.s_in[e] : 0.f;
-            if (ep.add_in) x += ok_rc ? ep.add_in[e] : 0.f;
+        for (int j = 0; j < 32; ++j) {
+          float v = __uint_as_float(u[j]);
+          if (ep.mode == kEpiMul) {
+            const float raw = v;
+            v *= tile2[lane * 33 + j];
+            if (ep.add_in) v += tile[lane * 33 + j];
+            if (ep.acc_out) tile2[lane * 33 + j] = raw;  // (this thread's own element, read above)
           } else if (silu) {
-            const float z = x + bias;
+            // h = s(z), z = acc + b, with the arithmetic of the element-wise
+            // kernel of the generic path (expf, an exactly rounded reciprocal
+            // equal to 1 / x): the same activations and s' to the bit
+            const float z = v + __ldg(ep.bias + min(nb + j, a.N - 1));
             const float sg = __frcp_rn(1.f + expf(-z));
-            x = z * sg;
-            if (ok_rc) {
-              const long long e = (long long)rr * ep.ld_s + n;
-              if (ep.s_out) ep.s_out[e] = sg * (1.f + z * (1.f - sg));
-              if (ep.s2_out) ep.s2_out[e] = sg * (1.f - sg) * (2.f + z * (1.f - 2.f * sg));
-            }
+            v = z * sg;
+            tile2[lane * 33 + j] = sg * (1.f + z * (1.f - sg));
           }
-          if (ok_rc) {
-            if (cz) {
-              float* c = cz + (long long)rr * a.ldc + n;
-              *c = a.accumulate ? *c + x : x;
-            }
-            if (ep.img) ep.img[(long long)rr * ep.ld_img + n] = __float2bfloat16_rn(x);
-            cs += x;
-          }
-          tile[r * kTileStride + lane] = x;
+          tile[lane * 33 + j] = v;
         }
-        // column sums of this block's rows, summed later over the row blocks in a
-        // fixed order (blocks past the last row hold no rows)
-        if (ep.colsum && col_ok && row0 < a.M) ep.colsum[(long long)(row0 >> 5) * ep.ld_colsum + n] = cs;
         __syncwarp();
+        // row-major outputs, lane = column: C (or C += for split partials),
+        // s'(z), the BF16 image and the column sums
+        const int n = nb + lane;
+        if (n < a.N) {
+          float cs = 0.f;
+#pragma unroll 4
+          for (int r = 0; r < 32; ++r) {
+            const int rr = row0 + r;
+            if (rr < a.M) {
+              const float x = tile[r * 33 + lane];
+              if (cz) {
+                float* c = cz + (long long)rr * a.ldc + n;
+                *c = a.accumulate ? *c + x : x;
+              }
+              if (silu && ep.s_out) ep.s_out[(long long)rr * ep.ld_s + n] = tile2[r * 33 + lane];
+              if (mul && ep.acc_out) ep.acc_out[(long long)rr * ep.ld_s + n] = tile2[r * 33 + lane];
+              if (ep.img) ep.img[(long long)rr * ep.ld_img + n] = __float2bfloat16_rn(x);
+              cs += x;
+            }
+          }
+          // column sums of this block's rows, summed later over the row blocks
+          // in a fixed order (blocks past the last row hold no rows)
+          if (ep.colsum && row0 < a.M) ep.colsum[(long long)(row0 >> 5) * ep.ld_colsum + n] = cs;
+        }
+        if (silu && ep.s2_out) {
+          // s''(z) for the second-order products: recomputed from the accumulators
+          // still in registers, then stored row by row like s'(z)
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float z = __uint_as_float(u[j]) + __ldg(ep.bias + min(nb + j, a.N - 1));
+            const float sg = __frcp_rn(1.f + expf(-z));
+            tile2[lane * 33 + j] = sg * (1.f - sg) * (2.f + z * (1.f - 2.f * sg));
+          }
+          __syncwarp();
+          if (n < a.N) {
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r) {
+              const int rr = row0 + r;
+              if (rr < a.M) ep.s2_out[(long long)rr * ep.ld_s + n] = tile2[r * 33 + lane];
+            }
+          }
+        }
         if (ep.imgT && row0 + lane < a.M) {
           // transposed BF16 image: for each column the 32 lanes write 32
           // consecutive rows (64 contiguous bytes)
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            const float4 x4 = *reinterpret_cast<const float4*>(tile + lane * kTileStride + 4 * jj);
-            const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-              if (nb + 4 * jj + i < a.N)
-                ep.imgT[(long long)(nb + 4 * jj + i) * ep.ld_imgT + row0 + lane] = __float2bfloat16_rn(xv[i]);
-          }
+#pragma unroll 4
+          for (int j = 0; j < 32; ++j)
+            if (nb + j < a.N)
+              ep.imgT[(long long)(nb + j) * ep.ld_imgT + row0 + lane] = __float2bfloat16_rn(tile[lane * 33 + j]);
         }
         __syncwarp();
       }

@@ -186,6 +186,15 @@ __device__ __forceinline__ Partial partial_warp_reduce(int mode, float T, Partia
   return a;
 }
 
+// Stream-ordered device allocation of the library's temporaries, from a
+// library-owned memory pool per device that keeps freed memory for reuse
+// (defined in gcdf_api.cu); freed with cudaFreeAsync.
+cudaError_t lib_malloc_async(void** out, size_t bytes, cudaStream_t s);
+template <class T>
+inline cudaError_t lib_malloc_async(T** out, size_t bytes, cudaStream_t s) {
+  return lib_malloc_async(reinterpret_cast<void**>(out), bytes, s);
+}
+
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_prep(const WorkDesc& w, const float* W1, const float* b1, int H, int d_in,
                         const float* shift, float* A, float* trig, cudaStream_t s);

@@ -299,7 +299,7 @@ int plan_partition(const float* base, int bstride, int rows, const float* points
                    const int* plen, float radius, int* offsets, int** idx, long long* n_pairs, cudaStream_t s) {
   cudaError_t e;
   int* counts = nullptr;
-  if ((e = cudaMallocAsync((void**)&counts, (size_t)(rows > 0 ? rows : 1) * sizeof(int), s)))
+  if ((e = lib_malloc_async((void**)&counts, (size_t)(rows > 0 ? rows : 1) * sizeof(int), s)))
     return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
   e = launch_partition_offsets(base, bstride, rows, points, pbegin, plen, radius, counts, offsets, s);
   cudaFreeAsync(counts, s);
@@ -308,7 +308,7 @@ int plan_partition(const float* base, int bstride, int rows, const float* points
   if ((e = cudaMemcpyAsync(&total, offsets + rows, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
       (e = cudaStreamSynchronize(s)))
     return set_error(GCDF_ECUDA, "partition read-back: %s", cudaGetErrorString(e));
-  if ((e = cudaMallocAsync((void**)idx, (size_t)(total > 0 ? total : 1) * sizeof(int), s)))
+  if ((e = lib_malloc_async((void**)idx, (size_t)(total > 0 ? total : 1) * sizeof(int), s)))
     return set_error(GCDF_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
   if ((e = launch_partition_indices(base, bstride, rows, points, pbegin, plen, radius, offsets, *idx, s)))
     return set_error(GCDF_ECUDA, "partition launch: %s", cudaGetErrorString(e));
@@ -341,7 +341,7 @@ struct Scratch {
   template <class T>
   cudaError_t get(T** out, size_t count) {
     size_t bytes = count * sizeof(T);
-    cudaError_t e = cudaMallocAsync((void**)out, bytes < 16 ? 16 : bytes, s);
+    cudaError_t e = lib_malloc_async((void**)out, bytes < 16 ? 16 : bytes, s);
     if (e == cudaSuccess) ptrs.push_back(*out);
     return e;
   }

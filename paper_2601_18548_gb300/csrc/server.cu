@@ -131,7 +131,7 @@ int admit(gcdf_server* s, Req* r) {
   const int n = r->n, N = r->N;
   const size_t b_state = align256(plan_state_bytes(N, n));
   const size_t b_in = align256((size_t)(2 * n) * 4) + align256((size_t)r->M * 12) + align256((size_t)N * n * 4);
-  cudaError_t e = cudaMallocAsync(&r->dmem, b_state + b_in + 256, s->stream);
+  cudaError_t e = lib_malloc_async(&r->dmem, b_state + b_in + 256, s->stream);
   if (e != cudaSuccess) return fail_server(s, GCDF_ENOMEM, "cudaMallocAsync", e);
   char* p = (char*)r->dmem;
   PlanTraj& t = r->tr;
@@ -185,7 +185,7 @@ int build_group(gcdf_server* s, Group& g, const gcdf_plan_params& prm) {
   const size_t b_tr = align256(g.reqs.size() * sizeof(PlanTraj));
   const size_t b_qf = align256((size_t)rows * n * 4), b_cg = b_qf, b_cc = align256((size_t)rows * 4);
   const size_t b_p = align256((size_t)pts * 12), b_off = align256((size_t)(rows + 1) * 4), b_pb = b_cc;
-  cudaError_t e = cudaMallocAsync(&g.dmem, b_tr + b_qf + b_cg + b_cc + b_p + b_off + b_pb, s->stream);
+  cudaError_t e = lib_malloc_async(&g.dmem, b_tr + b_qf + b_cg + b_cc + b_p + b_off + b_pb, s->stream);
   if (e != cudaSuccess) return fail_server(s, GCDF_ENOMEM, "cudaMallocAsync", e);
   char* p = (char*)g.dmem;
   g.trajs = (PlanTraj*)p; p += b_tr;
@@ -238,9 +238,9 @@ int build_group(gcdf_server* s, Group& g, const gcdf_plan_params& prm) {
     // each row's point count, then the lists over the rows' point ranges
     float* base = nullptr;
     int* plen = nullptr;
-    if ((e = cudaMallocAsync(&base, (size_t)(rows > 0 ? rows : 1) * n * 4, s->stream)) ||
-        (e = cudaMallocAsync(&plen, (size_t)(rows > 0 ? rows : 1) * 4, s->stream)) ||
-        (e = cudaMallocAsync(&g.part_off, (size_t)(rows + 1) * 4, s->stream)))
+    if ((e = lib_malloc_async(&base, (size_t)(rows > 0 ? rows : 1) * n * 4, s->stream)) ||
+        (e = lib_malloc_async(&plen, (size_t)(rows > 0 ? rows : 1) * 4, s->stream)) ||
+        (e = lib_malloc_async(&g.part_off, (size_t)(rows + 1) * 4, s->stream)))
       return fail_server(s, GCDF_ENOMEM, "cudaMallocAsync", e);
     std::vector<int> h_len;
     long long r0 = 0;
@@ -305,7 +305,7 @@ void worker_loop(gcdf_server* s) {
       if (admit(s, r)) return;
       // one init launch per admitted request (a one-entry table)
       PlanTraj* d_tr = nullptr;
-      cudaError_t e = cudaMallocAsync(&d_tr, sizeof(PlanTraj), s->stream);
+      cudaError_t e = lib_malloc_async(&d_tr, sizeof(PlanTraj), s->stream);
       if (e != cudaSuccess) { fail_server(s, GCDF_ENOMEM, "cudaMallocAsync", e); return; }
       if ((e = cudaMemcpyAsync(d_tr, &r->tr, sizeof(PlanTraj), cudaMemcpyHostToDevice, s->stream))) {
         fail_server(s, GCDF_ECUDA, "cudaMemcpyAsync", e);

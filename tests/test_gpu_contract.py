@@ -131,3 +131,21 @@ def test_expired_wait_sets_the_status_word_and_the_context_survives():
     torch.cuda.synchronize()
     assert np.isfinite(c.cpu().numpy()).all()
     assert g.device_status(net) == 0
+
+
+def test_temporary_pool_trim_keeps_results_identical():
+    """The temporaries come from a library-owned pool that keeps freed memory;
+    trimming it between calls changes nothing in the results."""
+    torch = need_gpu()
+    g = lib()
+    wl = synth.box_scene(n_waypoints=9, n_points=3000)
+    s = wl.shape
+    net = g.create_net(s.n_dof, s.hidden, s.n_layers, wl.weights, "bf16")
+    q, p = to_dev(torch, wl.q), to_dev(torch, wl.p)
+    a = [x.cpu().numpy() for x in g.collision_cost(net, q, p, "softmin", 0.02)]
+    torch.cuda.synchronize()
+    g.release_cached_memory()
+    b = [x.cpu().numpy() for x in g.collision_cost(net, q, p, "softmin", 0.02)]
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert g.device_status(net) == 0
