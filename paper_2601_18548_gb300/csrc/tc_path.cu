@@ -216,6 +216,18 @@ __device__ __forceinline__ void silu2(uint32_t u, uint32_t& h, uint32_t& s2) {
   s2 = ptx::hfma2(h, ptx::hsub2(kOne2, t), ptx::hadd2(kOne2, t));
 }
 
+// The same for the BF16 operand path: s(z) = u (1 + t) is formed exactly in
+// FP32 from the FP16 factors and rounded once to BF16 (no FP16 rounding of s(z)
+// and no FP16 -> BF16 conversion); 2 s'(z) = (1 + t) + (1 + t)(u - u t).
+__device__ __forceinline__ void silu2_bf16(uint32_t u, uint32_t& h_bf16, uint32_t& s2) {
+  const uint32_t t = ptx::htanh2(u);
+  const uint32_t tp1 = ptx::hadd2(kOne2, t);
+  float h0, h1;
+  ptx::f16x2_products(u, tp1, h0, h1);
+  h_bf16 = ptx::pack_bf16x2(h0, h1);
+  s2 = ptx::hfma2(tp1, ptx::hfnms2(u, t), tp1);
+}
+
 template <int kFmt>
 __device__ __forceinline__ uint32_t to_operand(uint32_t f16pair) {
   // BF16 converts here; FP16 is the operand; FP8 is converted where it is stored
@@ -772,9 +784,14 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               for (int i = 0; i < 8; ++i) {
                 const uint32_t zp = kF8 ? ptx::pack_f16x2(sc * __uint_as_float(v[2 * i]), sc * __uint_as_float(v[2 * i + 1]))
                                         : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-                uint32_t hh;
-                silu2(ptx::hfma2(zp, kHalf2, bh[i]), hh, st2[i]);
-                o[i] = to_operand<kFmt>(hh);
+                const uint32_t u = ptx::hfma2(zp, kHalf2, bh[i]);
+                if constexpr (kFmt == 0) {
+                  silu2_bf16(u, o[i], st2[i]);
+                } else {
+                  uint32_t hh;
+                  silu2(u, hh, st2[i]);
+                  o[i] = to_operand<kFmt>(hh);
+                }
               }
               store8c(obuf, c0 + cc, o);
               if (!fwd) ptx::tmem_st8(t_st + cc / 2, st2);
@@ -801,11 +818,24 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               for (int i = 0; i < 8; ++i) {
                 const uint32_t zp = kF8 ? ptx::pack_f16x2(sc * __uint_as_float(v[2 * i]), sc * __uint_as_float(v[2 * i + 1]))
                                         : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-                uint32_t hh, s2;
-                silu2(ptx::hfma2(zp, kHalf2, bh[i]), hh, s2);
+                const uint32_t u = ptx::hfma2(zp, kHalf2, bh[i]);
                 const float2 wo = *reinterpret_cast<const float2*>(s_wo + c0 + cc + 2 * i);
-                fpart = fmaf(wo.x, ptx::f16lo(hh), fmaf(wo.y, ptx::f16hi(hh), fpart));
-                o[i] = to_operand<kFmt>(ptx::hmul2(wh[i], s2));
+                if constexpr (kFmt == 0) {
+                  // s(z) = u (1 + t) exactly in FP32 for f; g_L = (w_o / 2) 2 s'(z)
+                  // exactly in FP32, rounded once to BF16
+                  const uint32_t t = ptx::htanh2(u);
+                  const uint32_t tp1 = ptx::hadd2(kOne2, t);
+                  float h0, h1, g0, g1;
+                  ptx::f16x2_products(u, tp1, h0, h1);
+                  fpart = fmaf(wo.x, h0, fmaf(wo.y, h1, fpart));
+                  ptx::f16x2_products(wh[i], ptx::hfma2(tp1, ptx::hfnms2(u, t), tp1), g0, g1);
+                  o[i] = ptx::pack_bf16x2(g0, g1);
+                } else {
+                  uint32_t hh, s2;
+                  silu2(u, hh, s2);
+                  fpart = fmaf(wo.x, ptx::f16lo(hh), fmaf(wo.y, ptx::f16hi(hh), fpart));
+                  o[i] = to_operand<kFmt>(ptx::hmul2(wh[i], s2));
+                }
               }
               if (!fwd) store8c(obuf, c0 + cc, o);
             }

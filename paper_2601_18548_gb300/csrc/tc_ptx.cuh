@@ -254,6 +254,19 @@ __device__ __forceinline__ uint32_t htanh2(uint32_t a) {
   asm("tanh.approx.f16x2 %0, %1;" : "=r"(d) : "r"(a));
   return d;
 }
+// (a - a b) for FP16 pairs: one fused multiply-add of the negated product
+__device__ __forceinline__ uint32_t hfnms2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("{\n .reg .b32 na;\n neg.f16x2 na, %1;\n fma.rn.f16x2 %0, na, %2, %1;\n}" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+// Products of two FP16 pairs in FP32 (mixed-precision multiply-add with -0:
+// the product of two FP16 values is exact in FP32, so nothing is rounded)
+__device__ __forceinline__ void f16x2_products(uint32_t a, uint32_t b, float& lo, float& hi) {
+  asm("{\n .reg .b16 al, ah, bl, bh;\n mov.b32 {al, ah}, %2;\n mov.b32 {bl, bh}, %3;\n"
+      " fma.rn.f32.f16 %0, al, bl, %4;\n fma.rn.f32.f16 %1, ah, bh, %4;\n}"
+      : "=f"(lo), "=f"(hi) : "r"(a), "r"(b), "f"(-0.0f));
+}
 // FP16 pair -> BF16 pair (through FP32; exact widening, one rounding)
 __device__ __forceinline__ uint32_t f16x2_to_bf16x2(uint32_t v) { return pack_bf16x2(f16lo(v), f16hi(v)); }
 // Four FP16 values (two f16x2 words, low halves first) -> four E4M3 bytes in

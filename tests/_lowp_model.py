@@ -57,8 +57,20 @@ def _silu_f16(u):
     return h, s2
 
 
+def _silu_bf16(u):
+    """The BF16-operand epilogue of the hidden layers 2..L: t and 1 + t in FP16,
+    s(z) = u (1 + t) exact (the product of two FP16 values, formed in FP32), and
+    2 s'(z) = (1 + t) + (1 + t)(u - u t) by FP16 multiply-adds."""
+    t = round_f16(np.tanh(u))
+    tp1 = round_f16(1.0 + t)
+    h = u * tp1
+    s2 = round_f16(tp1 + tp1 * round_f16(u - u * t))
+    return h, s2
+
+
 def lowp_eval(n_dof, H, L, weights, q_rows, p_rows, shift_rows=None, fmt="bf16"):
     R = round_bf16 if fmt == "bf16" else round_f16
+    silu = _silu_bf16 if fmt == "bf16" else _silu_f16
     lay = _layers(n_dof, H, L, weights)
     q = np.asarray(q_rows, dtype=np.float64)
     p = np.asarray(p_rows, dtype=np.float64).copy()
@@ -89,15 +101,17 @@ def lowp_eval(n_dof, H, L, weights, q_rows, p_rows, shift_rows=None, fmt="bf16")
         W, b = lay[l]
         zp = round_f16(h @ R(W).T)
         u = round_f16(zp * 0.5 + round_f16(0.5 * b))
-        hl, stash[l] = _silu_f16(u)
+        hl, stash[l] = silu(u)
         h = R(hl)
     W, b = lay[L - 1]
     zp = round_f16(h @ R(W).T)
     u = round_f16(zp * 0.5 + round_f16(0.5 * b))
-    hL, s2L = _silu_f16(u)
+    hL, s2L = silu(u)
     wo, bo = lay[L]
     f = hL @ wo[0] + bo[0]
-    g = R(round_f16(round_f16(0.5 * wo[0])[None, :] * s2L))
+    woh = round_f16(0.5 * wo[0])[None, :]
+    # BF16: the product (w_o / 2) 2 s'(z_L) is exact in FP32 and rounded once
+    g = R(woh * s2L) if fmt == "bf16" else R(round_f16(woh * s2L))
     for l in range(L - 1, 0, -1):  # reverse through W_{l+1} (0-based l)
         acc = g @ R(0.5 * lay[l][0])
         d2 = stash[l - 1] if l - 1 >= 1 else s2_1
