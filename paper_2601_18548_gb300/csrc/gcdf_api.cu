@@ -658,7 +658,7 @@ const char* gcdf_last_error(void) { return g_err; }
 
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = 16u << 20;  // 16 MiB per device, held until the process exits
+constexpr size_t kNoAllocScratchBytes = 64u << 20;  // 64 MiB per device, held until the process exits
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -704,7 +704,9 @@ int gcdf_collision_cost_noalloc(gcdf_net* net, const float* q, int N, const floa
   const size_t b_trig = round256((size_t)N * 2 * w.n_ang * sizeof(float));
   const size_t b_ts = part_offsets ? round256((size_t)(N + 1) * sizeof(int)) : 0;
   const size_t b_part = round256((size_t)(w.n_tiles > 0 ? w.n_tiles : 1) * sizeof(Partial));
-  const size_t need = b_A + b_trig + b_ts + b_part;
+  // the tensor-core kernel's stash of 2 s'(z_l) (per CTA, at most one CTA per SM)
+  const size_t b_stash = net->precision == GCDF_FP32 ? 0 : round256(tc_stash_bytes(net->L, net->num_sms));
+  const size_t need = b_A + b_trig + b_ts + b_part + b_stash;
   if (need > kNoAllocScratchBytes)
     return fail(GCDF_EINVAL,
                 "request needs %zu bytes of scratch; the allocation-free entry point has %zu "
@@ -720,6 +722,7 @@ int gcdf_collision_cost_noalloc(gcdf_net* net, const float* q, int N, const floa
   w.A = A;
   w.trig = trig;
   w.partials = parts;
+  w.stash = b_stash ? sp + b_A + b_trig + b_ts + b_part : nullptr;
 
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;

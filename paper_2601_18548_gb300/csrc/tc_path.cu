@@ -16,46 +16,51 @@
 // SM receives half the weight bytes (weight streaming from L2 is what bounds a
 // CTA that reloads the whole network for each tile).
 //
-// Each H x H product of the forward pass and of the reverse sweep ("a step")
-// is two MMA chains of N = 128 output columns ("halves" a and b), each
-// D (TMEM, FP32) = A (shared, 16-bit, 128 pairs x 256 per CTA) x B (shared,
-// 16-bit weight rows, 64 per CTA).  The A operand is double buffered: step s
-// reads buffer (tile + s) mod 2 and its epilogue writes the other, so the
-// epilogue of half a runs while the tensor core computes half b, and the
-// epilogue of half b runs while the next step's half a consumes its first 128
-// input columns (written by half a's epilogue).  Weights stream through a ring
-// of 16 KB stages (K = 128 of one chain) loaded by TMA; both CTAs' loads of a
-// stage complete on one barrier of the even CTA, and the even CTA's commit
-// releases the stage in both.  The reverse operands are stored copies of
-// W_l^T scaled by 1/2 (exact), so both directions are K-major.
+// Two tiles in flight per CTA pair ("slots" 0 and 1).  Each H x H product of
+// the forward pass or the reverse sweep ("a step") is two MMA chains of N = 128
+// output columns ("halves" a and b), each D (TMEM, FP32) = A (shared, 16-bit,
+// 128 pairs x 256 per CTA) x B (shared, 16-bit weight rows, 64 per CTA).  The
+// tensor core alternates between the slots: while it computes a step of one
+// slot, the epilogue turns the other slot's last step into that slot's next
+// operand, so neither waits for the other as long as an epilogue step is
+// shorter than a step of MMAs.  Each slot has one A buffer (its step's
+// epilogue writes the next operand into it once the step's MMAs have read it)
+// and one 256-column accumulator.  Weights stream through a ring of 16 KB
+// stages (K = 128 of one chain) loaded by TMA in the order the MMAs consume
+// them; both CTAs' loads of a stage complete on one barrier of the even CTA,
+// and the even CTA's commit releases the stage in both.  The reverse operands
+// are stored copies of W_l^T scaled by 1/2 (exact), so both directions are
+// K-major.
 //
 // Epilogue arithmetic (packed FP16 pairs):
 //   u = z / 2 = acc / 2 + b / 2,  t = tanh(u),  s(z) = z sigma(z) = u (1 + t),
 //   2 s'(z) = (1 + t) + s(z) (1 - t)
-// 2 s'(z_l) of layers 2..L-1 stays in TMEM as FP16 pairs; the halved reverse
-// operands cancel the factor 2.  s'(z_1) is recomputed from A_i + W_1p p_j.
-// The output sum f = w_o . s(z_L) accumulates in FP32.
+// (BF16 operands: s(z) = u (1 + t) formed exactly in FP32 and rounded once).
+// 2 s'(z_l) of layers 2..L-1 goes to a per-CTA stash in global memory as FP16
+// pairs ([slot][layer][8-column chunk][row], 16 bytes: each warp store or load
+// covers 512 contiguous bytes; 256 KB per CTA and stashed layer, so it stays
+// in L2), read back by the reverse step that needs it; the halved reverse
+// operands cancel the factor 2.  s'(z_1) is recomputed from A_i + W_1p p_j in
+// the last reverse step.  The output sum f = w_o . s(z_L) accumulates in FP32.
 //
-// TMEM columns (512, allocated for the CTA pair): [0, 128) accumulator half a,
-// [128, 256) half b, [256 + 128 s, 384 + 128 s) FP16-pair stash of layer
-// s + 2, s = 0..L-3; the input-Jacobian chain (N = 32) writes [384, 416) after
-// the stash is consumed (the next tile refills those columns only after its
-// outputs are read).
+// TMEM columns (512, allocated for the CTA pair): slot s's accumulator is
+// [256 s, 256 s + 256), half a first; the input-Jacobian chain (N = 32) of a
+// slot writes the first 32 columns of its half b after the last reverse step
+// has been read.
 //
-// Tile boundary: as soon as the last reverse chain has finished reading its
-// A buffer, each group writes the next tile's first layer into it, so the
-// next tile's chains start while this tile's outputs (chain rule, reduction)
-// are still being produced.
+// Tile boundary: the tail of a slot's tile reads the Jacobian and writes the
+// next tile's first layer into the slot's A buffer before its output stage
+// (chain rule, reduction), so the slot's next chains can start early; slot 0
+// runs a few items ahead, so the two slots' tile boundaries do not coincide.
 //
 // Warp roles (608 threads per CTA): warp 0 issues TMA loads, warp 1 allocates
 // TMEM and (even CTA) issues the pair's MMAs, warp 18 merges each tile's four
-// row-quad partial records into the tile's record, warps 2..17 are the epilogue:
-// 8 warps process half a of every step and 8 warps half b, so the epilogue of
-// half b starts as soon as its accumulator is ready instead of after half a's;
-// thread = one pair row (TMEM lane) and 64 columns of its half; each warp
-// signals the end of a half to the MMA issuer with one arrival.  The output
-// stage uses all 16 warps.  The input-Jacobian operand W_1q^T streams through the
-// same ring as the weights.
+// row-quad partial records into the tile's record, warps 2..17 are the
+// epilogue: thread = one pair row (TMEM lane) and 64 columns; the 8 warps of
+// columns [0, 128) and the 8 of [128, 256) each signal their half to the MMA
+// issuer with one arrival per warp (the next step's first K = 128 stage needs
+// only half a).  The input-Jacobian operand W_1q^T streams through the same
+// ring as the weights.
 //
 // Every cross-warp and cross-CTA handoff is an mbarrier and every wait on one
 // is bounded (about a second).  On expiry the kernel records an error in a
@@ -76,7 +81,8 @@ constexpr int kTile = 128;             // pairs per CTA tile; a CTA pair shares 
 constexpr int kH = 256;                // hidden width handled by this kernel
 constexpr int kHalf = 128;             // output columns per MMA chain
 constexpr int kRowsCta = kHalf / 2;    // weight rows of a chain held by each CTA of the pair
-constexpr int kStages = 5;             // weight ring depth
+constexpr int kSlots = 2;              // tiles in flight per CTA pair
+constexpr int kStages = 4;             // weight ring depth
 constexpr int kSlabBytes = kRowsCta * 128;  // 64 rows x 64 16-bit values (one K = 64 slab)
 constexpr int kStageBytes = 2 * kSlabBytes; // K = 128 of one chain per stage
 constexpr int kABytes = kTile * kH * 2;
@@ -84,41 +90,42 @@ constexpr int kThreads = 608;          // 19 warps
 constexpr int kMergeWarp = 18;         // merges each tile's four row-quad records
 constexpr int kEpiThreads = 512;       // epilogue threads (16 warps)
 constexpr int kEpiWarps = 16;
-constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kTmemCols = 512;    // one 256-column FP32 accumulator per slot
 
 // shared memory map (offsets from the 1024-aligned base)
-constexpr int kOffA0 = 0;
-constexpr int kOffA1 = kABytes;
+constexpr int kOffA0 = 0;                                       // slot 0's operand buffer
+constexpr int kOffA1 = kABytes;                                 // slot 1's
 constexpr int kOffRing = 2 * kABytes;                           // 131072
 constexpr int kOffBiasH = kOffRing + kStages * kStageBytes;      // [(L-1) x H/2] f16x2 b_l / 2, L <= 4
 constexpr int kOffW1p = kOffBiasH + 3 * (kH / 2) * 4;           // [H/2] uint4: f16x2 W_1p / 2 (x, y, z pairs)
 constexpr int kOffWo = kOffW1p + (kH / 2) * 16;                 // [H] fp32 w_o
 constexpr int kOffWoh = kOffWo + kH * 4;                        // [H/2] f16x2 w_o / 2
-constexpr int kOffAiw = kOffWoh + (kH / 2) * 4;                 // [16 warps][32] f16x2 A_i / 2
-constexpr int kOffTrig = kOffAiw + kEpiWarps * 32 * 4;          // [16 warps][2 tiles][24] sin, cos
-constexpr int kOffF = kOffTrig + kEpiWarps * 2 * 24 * 4;        // [2 tiles][4][128] f partials
-constexpr int kOffPart = kOffF + 2 * 4 * kTile * 4;             // 4 partial records
+constexpr int kOffAiw = kOffWoh + (kH / 2) * 4;                 // [2 slots][16 warps][32] f16x2 A_i / 2
+constexpr int kOffPt = kOffAiw + kSlots * kEpiWarps * 32 * 4;   // [2 slots][128 rows] uint4: the row's point, packed
+constexpr int kOffTrig = kOffPt + kSlots * kTile * 16;          // [2 slots][16 warps][24] sin, cos
+constexpr int kOffF = kOffTrig + kSlots * kEpiWarps * 24 * 4;   // [2 slots][2 tiles][4][128] f partials
+constexpr int kOffPart = kOffF + kSlots * 2 * 4 * kTile * 4;    // 4 partial records
 constexpr int kOffBar = kOffPart + 4 * (int)sizeof(Partial);
-constexpr int kNumBars = 2 * kStages + 10;
+constexpr int kNumBars = 2 * kStages + 16;
 constexpr int kOffSlot = kOffBar + kNumBars * 8;
 constexpr int kSmemBytes = kOffSlot + 16 + 1024;                // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024 - 64, "shared memory budget");
+static_assert(kOffPt % 16 == 0 && kOffBar % 8 == 0, "alignment");
 
 // barrier indices
 constexpr int B_FULL0 = 0;              // + stage: both CTAs' slabs landed (used in the even CTA)
 constexpr int B_EMPTY0 = kStages;       // + stage: its MMAs completed (commit to both CTAs)
-constexpr int B_ACC0 = 2 * kStages;     // + half: accumulator half complete (commit to both CTAs)
-constexpr int B_ED0 = 2 * kStages + 2;  // + half: epilogues of both CTAs done (even CTA, 16 warp arrivals)
-constexpr int B_FD = 2 * kStages + 4;   // f partials written (512 arrivals)
-constexpr int B_PD = 2 * kStages + 5;   // partial-record parts written (16 warp arrivals)
-constexpr int B_MD = 2 * kStages + 6;   // the merge warp has read them (1 arrival)
-constexpr int B_ACCJ = 2 * kStages + 7; // input-Jacobian chain complete (commit to both CTAs)
-// + half: a tile's first layer written (even CTA, 16 warp arrivals).  Kept apart
-// from B_ED0: a warp arrives for its last reverse step and then for the next
-// tile's first layer with no wait in between that would prove the first phase
-// complete, so on one barrier a fast warp's second arrival could complete the
-// phase that still waits for a slow warp's first.
-constexpr int B_FL0 = 2 * kStages + 8;
+constexpr int B_ACC0 = 2 * kStages;     // + slot: the slot's step complete, both chains (commit to both CTAs)
+constexpr int B_ACCJ0 = 2 * kStages + 2;  // + slot: input-Jacobian chain complete (commit to both CTAs)
+constexpr int B_FD0 = 2 * kStages + 4;  // + slot: f partials written (512 arrivals)
+constexpr int B_ED0 = 2 * kStages + 6;  // + 2 slot + half: epilogues of both CTAs done (even CTA, 16 warp arrivals)
+// + 2 slot + half: a tile's first layer written (even CTA, 16 warp arrivals).
+// Kept apart from B_ED0: a warp arrives for its last reverse step and later for
+// the next tile's first layer; on one barrier a fast warp's second arrival could
+// complete the phase that still waits for a slow warp's first.
+constexpr int B_FL0 = 2 * kStages + 10;
+constexpr int B_PD = 2 * kStages + 14;  // partial-record parts written (16 warp arrivals)
+constexpr int B_MD = 2 * kStages + 15;  // the merge warp has read them (1 arrival)
 
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at GB300 clocks
 
@@ -383,6 +390,28 @@ __device__ __forceinline__ void warp_combine_quads(int mode, float T, const Part
   out[lane] = acc;
 }
 
+// The order in which every role of a CTA pair (TMA producer, MMA issuer,
+// epilogue, merge warp) takes its work items.  Slot 0 holds the cluster's even
+// local tiles, slot 1 the odd ones; a tile is n_items items (its weight steps,
+// then its tail: the input-Jacobian chain and output stage).  Slot 0 runs
+// `lead` items alone, then the two slots alternate, so that while the tensor
+// core computes one slot's step the epilogue turns the other slot's previous
+// step into its next operand, and the two slots' tile boundaries fall apart.
+struct Schedule {
+  int n_items, ni0, ni1, k0, k1, lead;
+  __device__ __forceinline__ bool next(int& slot, int& tile_local, int& step) {
+    const bool have0 = k0 < ni0, have1 = k1 < ni1;
+    if (!have0 && !have1) return false;
+    const bool one = !have0 || (have1 && k0 >= lead && k1 <= k0 - lead);
+    const int kk = one ? k1 : k0;
+    if (one) ++k1; else ++k0;
+    slot = one ? 1 : 0;
+    tile_local = kk / n_items;
+    step = kk - tile_local * n_items;
+    return true;
+  }
+};
+
 // kFmt: operand format, 0 = BF16, 1 = FP16, 2 = FP8 E4M3 (per-layer scales).
 // kFwd: value-only queries (the forward steps alone), a separate instantiation
 // so that the full sweep carries none of its branches.
@@ -409,13 +438,6 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
   // alone: no stash, no reverse steps, no input-Jacobian chain.
   constexpr bool fwd = kFwd;  // launched for w.mode == kQuery with w.g_out == nullptr
   const int n_steps = fwd ? (L - 1) : 2 * (L - 1);  // weight steps per tile (forward, then reverse)
-  // A-buffer parity: step s of tile `it` reads buffer (tile_par(it) + s) & 1
-  // and its epilogue writes the other one; a tile's first layer goes to
-  // buffer tile_par(it) & 1.  With the full sweep (n_steps even, plus the
-  // input-Jacobian chain on the same buffer as the last reverse step) that is
-  // (it + s) & 1; forward-only tiles continue the alternation across tiles, so
-  // the next tile's first layer never lands in the buffer its last step reads.
-  auto tile_par = [&](int it) -> int { return fwd ? it * (L - 1) : it; };
   const int nj = tw.nj;
   const int ntiles = total_tiles(w);
   // CTA pairs (clusters of 2) take pair tiles round robin; CTA `rank` of the pair
@@ -432,7 +454,6 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
   uint4* s_w1p = reinterpret_cast<uint4*>(gbase + kOffW1p);
   float* s_wo = reinterpret_cast<float*>(gbase + kOffWo);
   uint32_t* s_woh = reinterpret_cast<uint32_t*>(gbase + kOffWoh);
-  uint32_t* s_aiw = reinterpret_cast<uint32_t*>(gbase + kOffAiw);
   float* s_f = reinterpret_cast<float*>(gbase + kOffF);
   Partial* s_part = reinterpret_cast<Partial*>(gbase + kOffPart);
   uint32_t* s_slot = reinterpret_cast<uint32_t*>(gbase + kOffSlot);
@@ -444,16 +465,17 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       ptx::mbar_init(bar(base, B_FULL0 + s), 1);
       ptx::mbar_init(bar(base, B_EMPTY0 + s), 1);
     }
-    ptx::mbar_init(bar(base, B_ACC0 + 0), 1);
-    ptx::mbar_init(bar(base, B_ACC0 + 1), 1);
-    ptx::mbar_init(bar(base, B_ED0 + 0), kEpiWarps);  // 8 warps of the half x 2 CTAs
-    ptx::mbar_init(bar(base, B_ED0 + 1), kEpiWarps);
-    ptx::mbar_init(bar(base, B_FD), kEpiThreads);
+    for (int sl = 0; sl < kSlots; ++sl) {
+      ptx::mbar_init(bar(base, B_ACC0 + sl), 1);
+      ptx::mbar_init(bar(base, B_ACCJ0 + sl), 1);
+      ptx::mbar_init(bar(base, B_FD0 + sl), kEpiThreads);
+      for (int h = 0; h < 2; ++h) {
+        ptx::mbar_init(bar(base, B_ED0 + 2 * sl + h), kEpiWarps);  // 8 warps of the half x 2 CTAs
+        ptx::mbar_init(bar(base, B_FL0 + 2 * sl + h), kEpiWarps);
+      }
+    }
     ptx::mbar_init(bar(base, B_PD), kEpiWarps);
     ptx::mbar_init(bar(base, B_MD), 1);
-    ptx::mbar_init(bar(base, B_ACCJ), 1);
-    ptx::mbar_init(bar(base, B_FL0 + 0), kEpiWarps);
-    ptx::mbar_init(bar(base, B_FL0 + 1), kEpiWarps);
     ptx::fence_barrier_init();
     ptx::prefetch_tensormap(&map_w);
     ptx::prefetch_tensormap(&map_j);
@@ -481,6 +503,20 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
   ptx::tc_fence_after();
   const uint32_t tmem = *s_slot;
 
+  // Every role walks the same sequence of work items (Schedule): slot 0 takes
+  // the cluster's even local tiles, slot 1 the odd ones; a tile is n_steps
+  // weight steps and one tail item.
+  const int n_items = n_steps + 1;
+  auto make_sched = [&]() {
+    Schedule sc;
+    sc.n_items = n_items;
+    sc.ni0 = ((my_tiles + 1) >> 1) * n_items;
+    sc.ni1 = (my_tiles >> 1) * n_items;
+    sc.k0 = sc.k1 = 0;
+    sc.lead = n_items >> 1;
+    return sc;
+  };
+
   if (warp == 0) {
     // ================= TMA producer (both CTAs) =================
     // Stage g mod kStages holds K = 128 of one chain: this CTA's kRowsCta weight
@@ -505,15 +541,18 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         if (++pst == kStages) { pst = 0; puse ^= 1u; }
         return true;
       };
-      for (int it = 0; it < my_tiles && ok; ++it) {
-        for (int s = 0; s < n_steps && ok; ++s) {
+      Schedule sc = make_sched();
+      int slot, jl, s;
+      while (ok && sc.next(slot, jl, s)) {
+        if (s < n_steps) {
           const int row0 = (s < L - 1) ? s * kH : (L - 1 + (2 * L - 3 - s)) * kH;
           for (int hh = 0; hh < 2 && ok; ++hh)
             for (int pr = 0; pr < 2 && ok; ++pr)
               ok = load_stage(&map_w, pr * 128, row0 + hh * kHalf + (int)rank * kRowsCta, kSlabBytes);
+        } else if (!fwd) {  // W_1q^T: nj rows, nj / 2 per CTA
+          for (int pr = 0; pr < 2 && ok; ++pr)
+            ok = load_stage(&map_j, pr * 128, (int)rank * (nj / 2), (uint32_t)(nj / 2) * 128u);
         }
-        for (int pr = 0; pr < 2 && ok && !fwd; ++pr)  // W_1q^T: nj rows, nj / 2 per CTA
-          ok = load_stage(&map_j, pr * 128, (int)rank * (nj / 2), (uint32_t)(nj / 2) * 128u);
       }
       // drain (even CTA): the last kStages stages are the only ones that can be
       // in flight; their FULL phases cover both CTAs' loads
@@ -534,7 +573,9 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       long long g = 0;         // stages consumed
       int cst = 0;             // ring stage of g
       uint32_t cph = 0;        // its FULL phase parity
-      uint32_t ea = 0, eb = 0;
+      // ED completions consumed per slot and half (scalars: a runtime-indexed
+      // array would live in local memory)
+      uint32_t ed00 = 0, ed01 = 0, ed10 = 0, ed11 = 0;
       bool ok = true;
       // Shared-memory descriptors are linear in the start address (bits 0-13 hold
       // address / 16), so every operand descriptor is a base plus a small offset;
@@ -562,40 +603,50 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         ++g;
         if (++cst == kStages) { cst = 0; cph ^= 1u; }
       };
-      for (int it = 0; it < my_tiles && ok; ++it) {
-        for (int s = 0; s <= (fwd ? n_steps - 1 : n_steps) && ok; ++s) {
-          const uint64_t dAbuf = ((tile_par(it) + s) & 1) ? dA1 : dA0;
-          // the input Jacobian df/denc = W_1q^T g_1 goes to TMEM columns [384, 384 + nj):
-          // the stash is free by then, so the next tile's first chain need not wait for it
-          const bool jstep = (s == n_steps);
-          const uint32_t idd = jstep ? idj : id128;
-          for (int hh = 0; hh < (jstep ? 1 : 2) && ok; ++hh) {
-            const uint32_t dtm = tmem + (jstep ? 384 : hh * kHalf);
+      Schedule sc = make_sched();
+      int slot, jl, s;
+      while (ok && sc.next(slot, jl, s)) {
+        const bool jstep = (s == n_steps);
+        if (fwd && jstep) continue;  // forward-only tiles have no MMA in their tail
+        const uint64_t dAbuf = slot ? dA1 : dA0;
+        // the input Jacobian df/denc = W_1q^T g_1 goes to the first nj columns of
+        // the slot's accumulator half b (its last reverse step's epilogue has read
+        // them).  Half b: the next tile's chain a, which may start when only the
+        // half-a warps have written their first layer, does not touch it; chain b
+        // starts after every warp has, and every warp reads the Jacobian first.
+        const uint32_t idd = jstep ? idj : id128;
+        for (int hh = 0; hh < (jstep ? 1 : 2) && ok; ++hh) {
+          const uint32_t dtm = tmem + (uint32_t)(slot * kH) + (jstep ? (uint32_t)kHalf : (uint32_t)(hh * kHalf));
 #pragma unroll
-            for (int pr = 0; pr < 2; ++pr) {
-              if (hh == 0) {
-                // input columns [128 pr, 128 pr + 128) come from the previous step's half pr
-                // (both CTAs' epilogues arrive)
-                // (step 0: the tile's first layer, on its own barriers)
-                const bool ok_w = (s == 0)
-                    ? wait_role(bar(base, B_FL0 + pr), (uint32_t)it & 1u, abort_flag, tw.err)
-                    : wait_role(bar(base, B_ED0 + pr), (pr ? eb : ea) & 1u, abort_flag, tw.err);
-                if (!ok_w) {
-                  ok = false;
-                  break;
-                }
-                if (s != 0) {
-                  if (pr) ++eb; else ++ea;
-                }
-                ptx::tc_fence_after();
+          for (int pr = 0; pr < 2; ++pr) {
+            if (hh == 0) {
+              // input columns [128 pr, 128 pr + 128) come from the slot's previous
+              // step's half pr (both CTAs' epilogues arrive); step 0: the tile's
+              // first layer, on its own barriers.  Either also proves that half of
+              // the slot's accumulator has been read.
+              const int bi = 2 * slot + pr;
+              const uint32_t edn = slot ? (pr ? ed11 : ed10) : (pr ? ed01 : ed00);
+              const bool ok_w = (s == 0)
+                  ? wait_role(bar(base, B_FL0 + bi), (uint32_t)jl & 1u, abort_flag, tw.err)
+                  : wait_role(bar(base, B_ED0 + bi), edn & 1u, abort_flag, tw.err);
+              if (!ok_w) {
+                ok = false;
+                break;
               }
-              // both CTAs' slabs written by TMA: the transaction barrier orders them before the MMAs
-              if (!wait_role(bar(base, B_FULL0 + cst), cph, abort_flag, tw.err)) { ok = false; break; }
-              stage_mmas(dtm, dAbuf + (uint64_t)((kSlabsPerStage * pr) * (kTile * 128) >> 4), idd, pr == 0);
+              if (s != 0) {
+                if (slot) { if (pr) ++ed11; else ++ed10; }
+                else { if (pr) ++ed01; else ++ed00; }
+              }
+              ptx::tc_fence_after();
             }
-            if (ok) ptx::mma_commit_pair(bar(base, jstep ? B_ACCJ : B_ACC0 + hh));
+            // both CTAs' slabs written by TMA: the transaction barrier orders them before the MMAs
+            if (!wait_role(bar(base, B_FULL0 + cst), cph, abort_flag, tw.err)) { ok = false; break; }
+            stage_mmas(dtm, dAbuf + (uint64_t)((kSlabsPerStage * pr) * (kTile * 128) >> 4), idd, pr == 0);
           }
         }
+        // one commit per step: it tracks every earlier MMA of this thread, so
+        // both chains (and with them every read of the slot's A buffer) are done
+        if (ok) ptx::mma_commit_pair(bar(base, jstep ? B_ACCJ0 + slot : B_ACC0 + slot));
       }
       // all issued MMAs complete before TMEM is released: wait for the last
       // EMPTY arrivals (they follow every earlier MMA of this thread)
@@ -608,33 +659,44 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
   } else if (warp == kMergeWarp) {
     // ================= merge warp: one partial record per tile =================
     if (w.mode != kQuery) {
-      for (int it = 0; it < my_tiles; ++it) {
-        if (!wait_epi_warp(bar(base, B_PD), (uint32_t)it & 1u, abort_flag, tw.err)) break;
+      Schedule sc = make_sched();
+      int slot, jl, s;
+      uint32_t n_out = 0;
+      while (sc.next(slot, jl, s)) {
+        if (s != n_steps) continue;
+        if (!wait_epi_warp(bar(base, B_PD), n_out & 1u, abort_flag, tw.err)) break;
+        const int it = 2 * jl + slot;
         const int t = 2 * (cluster + it * nclusters) + (int)rank;
         if (t < ntiles) warp_combine_quads(w.mode, w.param, s_part, &w.partials[t]);
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(bar(base, B_MD));  // s_part may be rewritten
+        ++n_out;
       }
     }
   } else {
-    // ================= epilogue: 16 warps, one pair row, 32 columns of each half ========
+    // ================= epilogue: 16 warps, one pair row, 64 columns each ========
     const int e = warp - 2;
     const int quad = warp & 3;
     const int kq = e >> 2;                 // 0..3: split of the output stage's gradient components
-    const int hg = kq >> 1;                // the half this warp processes in every step
+    const int hg = kq >> 1;                // the half (and ED / FL barrier) this warp reports to
     const int cw = hg * kHalf + 64 * (kq & 1);  // first of its 64 columns
     const int row = quad * 32 + lane;
     const uint32_t t_lane = tmem + ((uint32_t)(quad * 32) << 16);
     const int n = w.n_dof;
     const uint32_t rbase = (row >> 3) * 1024 + (row & 7) * 128;
     const int r7 = row & 7;
-    uint32_t* aiw = s_aiw + e * 32;        // f16x2 A_i / 2 for this thread's 32 + 32 columns
-    float* trigw = reinterpret_cast<float*>(gbase + kOffTrig) + e * 2 * 24;  // this warp's sin, cos (2 tiles)
-    uint32_t acc_n = 0;                    // completions of this warp's ACC half consumed
+    uint32_t* aiw_base = reinterpret_cast<uint32_t*>(gbase + kOffAiw) + e * 32;  // + slot * kEpiWarps * 32
+    float* trig_base = reinterpret_cast<float*>(gbase + kOffTrig) + e * 24;     // + slot * kEpiWarps * 24
+    uint4* pt_base = reinterpret_cast<uint4*>(gbase + kOffPt) + row;            // + slot * kTile
+    // global stash of 2 s'(z_l), layers 2..L-1: [slot][layer][8-column chunk][row], 16 bytes
+    uint4* stash_cta = reinterpret_cast<uint4*>(w.stash) +
+                       (size_t)blockIdx.x * kSlots * (L > 2 ? L - 2 : 0) * (kH / 8) * kTile + row;
+    uint32_t acc_n0 = 0, acc_n1 = 0;       // ACC completions consumed per slot
+    uint32_t n_out = 0;                    // output stages done (partial records)
     bool ok = true;
-
-    int t = 0, wp = 0, start = 0, len = 0;
-    uint32_t px2 = 0, py2 = 0, pz2 = 0;  // this row's point, packed (p, p) in FP16
+    // per slot: the tile in flight (waypoint, first list position, length);
+    // scalars, selected by slot (a runtime-indexed array would live in local memory)
+    int wp0 = 0, wp1 = 0, start0 = 0, start1 = 0, len0 = 0, len1 = 0;
 
     // byte offset (within an A buffer) of columns c0 + 8 q .. c0 + 8 q + 7 of this row
     auto aoff = [&](int c0, int q) -> uint32_t {
@@ -652,11 +714,12 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         ptx::st_shared_v4(abuf + aoff(c0, 1), o[4], o[5], o[6], o[7]);
       }
     };
-    // the half's epilogue is done in this warp: release the accumulator half and
-    // the A-buffer columns it wrote to the even CTA's MMA issuer, one arrival per
-    // warp.  Every lane's TMEM loads have completed (wait::ld) and are ordered by
-    // the tcgen05 fence; its shared-memory stores are made visible to the async
-    // proxy (which the tensor core reads through) before the warp synchronises.
+    // the half's epilogue is done in this warp: release the A-buffer columns it
+    // wrote (and the accumulator half it read) to the even CTA's MMA issuer, one
+    // arrival per warp.  Every lane's TMEM loads have completed (wait::ld) and
+    // are ordered by the tcgen05 fence; its shared-memory stores are made visible
+    // to the async proxy (which the tensor core reads through) before the warp
+    // synchronises.
     auto arrive_lead = [&](int b) {
       ptx::tc_fence_before();
       ptx::fence_proxy_async_smem();
@@ -666,17 +729,15 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         else ptx::mbar_arrive_remote(ptx::mapa_shared(bar(base, b), 0));
       }
     };
-    auto epi_done = [&](int h) { arrive_lead(B_ED0 + h); };
-    auto fl_done = [&]() { arrive_lead(B_FL0 + hg); };
+    // tile `it` (local index) into slot it & 1: its waypoint's A_i / 2 for this
+    // warp's columns, its sin / cos, and this row's point
     auto load_tile = [&](int it) {
-      t = 2 * (cluster + it * nclusters) + (int)rank;
-      if (t < ntiles) {
-        tile_lookup(w, t, wp, start, len);
-      } else {  // the odd CTA's half of the last pair tile when the tile count is odd
-        wp = 0;
-        start = 0;
-        len = 0;
-      }
+      const int sl = it & 1;
+      const int t = 2 * (cluster + it * nclusters) + (int)rank;
+      int wp = 0, start = 0, len = 0;
+      if (t < ntiles) tile_lookup(w, t, wp, start, len);  // else: the odd CTA's half of the last pair tile
+      if (sl) { wp1 = wp; start1 = start; len1 = len; }
+      else { wp0 = wp; start0 = start; len0 = len; }
       float px = 0.f, py = 0.f, pz = 0.f;
       if (row < len) {
         int j;
@@ -686,90 +747,75 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         py = w.p[3 * (size_t)j + 1];
         pz = w.p[3 * (size_t)j + 2];
       }
-      px2 = ptx::pack_f16x2(px, px);
-      py2 = ptx::pack_f16x2(py, py);
-      pz2 = ptx::pack_f16x2(pz, pz);
       const float* Ai = w.A + (size_t)wp * kH + cw;
+      uint32_t* aiw = aiw_base + sl * kEpiWarps * 32;
+      float* trigw = trig_base + sl * kEpiWarps * 24;
       __syncwarp();
+      // (the four warps of a row quad store the same point: each reads back its own store)
+      pt_base[sl * kTile] = make_uint4(ptx::pack_f16x2(px, px), ptx::pack_f16x2(py, py), ptx::pack_f16x2(pz, pz), 0u);
       aiw[lane] = ptx::pack_f16x2(0.5f * Ai[2 * lane], 0.5f * Ai[2 * lane + 1]);
-      if (lane < 2 * w.n_ang) trigw[(it & 1) * 24 + lane] = w.trig[(size_t)wp * 2 * w.n_ang + lane];
+      if (lane < 2 * w.n_ang) trigw[lane] = w.trig[(size_t)wp * 2 * w.n_ang + lane];
       __syncwarp();
     };
-    // h_1 = s(A_i + W_1p p) for this row and the warp's 64 columns -> A buffer (tile parity)
-    auto first_layer = [&](int it) {
-      const uint32_t abuf = base + ((tile_par(it) & 1) ? kOffA1 : kOffA0);
-      const int c0 = cw;
+    // h_1 = s(A_i + W_1p p) for this row and the warp's 64 columns -> the slot's A buffer
+    auto first_layer = [&](int sl) {
+      const uint32_t abuf = base + (sl ? kOffA1 : kOffA0);
+      const uint32_t* aiw = aiw_base + sl * kEpiWarps * 32;
+      const uint4 pt = pt_base[sl * kTile];
 #pragma unroll 1
       for (int cc = 0; cc < 64; cc += 16) {
         uint32_t o[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const uint32_t u = first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2);
+          const uint32_t u = first_layer_u2(s_w1p[(cw + cc) / 2 + i], aiw[cc / 2 + i], pt.x, pt.y, pt.z);
           const uint32_t tt = ptx::htanh2(u);
           o[i] = to_operand<kFmt>(ptx::hfma2(u, tt, u));
         }
-        store8c(abuf, c0 + cc, o);
+        store8c(abuf, cw + cc, o);
       }
-      fl_done();
-    };
-    // With L = 4 and FP16 operands the next tile's h_1 is computed early, in the
-    // slack of the last reverse step, into this warp's z_2 stash columns (read by
-    // then); the tile tail copies it into the A buffer (TMEM -> shared memory, no
-    // arithmetic).  Measured: 1.4 % faster with FP16 operands, 1.7 % slower with
-    // BF16 ones, where the tile tail computes the first layer itself.
-    const bool early_h1 = kF16 && L == 4 && !fwd;
-    const uint32_t t_h1 = t_lane + 256 + (cw >> 1);
-    auto first_layer_tmem = [&]() {
-#pragma unroll 1
-      for (int cc = 0; cc < 64; cc += 16) {
-        uint32_t o[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const uint32_t u = first_layer_u2(s_w1p[(cw + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2);
-          const uint32_t tt = ptx::htanh2(u);
-          o[i] = to_operand<kFmt>(ptx::hfma2(u, tt, u));
-        }
-        ptx::tmem_st8(t_h1 + cc / 2, o);
-      }
-      ptx::tmem_wait_st();
-    };
-    auto first_layer_copy = [&](int it) {
-      const uint32_t abuf = base + ((tile_par(it) & 1) ? kOffA1 : kOffA0);
-      uint32_t v[32];
-      ptx::tmem_ld16(t_h1, v);
-      ptx::tmem_ld16(t_h1 + 16, v + 16);
-      ptx::tmem_wait_ld();
-#pragma unroll
-      for (int q = 0; q < 4; ++q) store8c(abuf, cw + 16 * q, v + 8 * q);
-      fl_done();
+      arrive_lead(B_FL0 + 2 * sl + hg);
     };
 
-    if (my_tiles > 0) {
-      load_tile(0);
-      first_layer(0);
+    // the first tile of each slot
+    for (int it = 0; it < kSlots && it < my_tiles; ++it) {
+      load_tile(it);
+      first_layer(it);
     }
     float fpart = 0.f;  // sum of w_o s(z_L) over this thread's 64 columns
-    for (int it = 0; it < my_tiles && ok; ++it) {
-      const int cur_wp = wp, cur_start = start, cur_len = len;
-      const bool h1_early = early_h1 && it + 1 < my_tiles;
-      for (int s = 0; s < n_steps && ok; ++s) {
-        const uint32_t obuf = base + (((tile_par(it) + s + 1) & 1) ? kOffA1 : kOffA0);
-        {
-          const int h = hg;
-          if (!wait_epi_warp(bar(base, B_ACC0 + h), acc_n & 1u, abort_flag, tw.err)) { ok = false; break; }
-          ++acc_n;
-          ptx::tc_fence_after();
-          const int c0 = cw;                      // first of this warp's 64 columns
-          const uint32_t t_acc = t_lane + c0;     // accumulator half h starts at column h * 128
-          if (s < L - 2) {
-            // middle forward layer l = s + 2: h_l -> A, 2 s'(z_l) -> stash
-            const uint32_t t_st = t_lane + 256 + 128 * s + (c0 >> 1);
-            const float sc = kF8 ? tw.fp8_scale[s] : 1.f;  // FP8: the layer's weight scale
-            const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + s * (kH / 2) + (c0 >> 1));
-            // two 16-column chunks are loaded at once, so the second load's
-            // latency hides behind the first chunk's arithmetic
+    Schedule sc = make_sched();
+    int slot, jl, s;
+    while (ok && sc.next(slot, jl, s)) {
+      const int it = 2 * jl + slot;
+      const uint32_t abuf = base + (slot ? kOffA1 : kOffA0);
+      if (s < n_steps) {
+        // a reverse step whose factor 2 s'(z_{l-1}) is stashed starts loading its
+        // first 16 columns before it waits for the accumulator
+        const int lm1 = 2 * L - 2 - s;
+        const bool stashed = !fwd && s >= L - 1 && lm1 >= 2;
+        const uint4* st_r = stashed ? stash_cta + ((size_t)(slot * (L - 2) + (lm1 - 2)) * (kH / 8) + (cw >> 3)) * kTile
+                                    : stash_cta;
+        uint4 dn0 = make_uint4(0u, 0u, 0u, 0u), dn1 = dn0;  // the next chunk's stash
+        if (stashed) {
+          dn0 = st_r[0];
+          dn1 = st_r[kTile];
+        }
+        if (!wait_epi_warp(bar(base, B_ACC0 + slot), (slot ? acc_n1 : acc_n0) & 1u, abort_flag, tw.err)) {
+          ok = false;
+          break;
+        }
+        if (slot) ++acc_n1; else ++acc_n0;
+        ptx::tc_fence_after();
+        const int c0 = cw;                                         // first of this warp's 64 columns
+        const uint32_t t_acc = t_lane + (uint32_t)(slot * kH) + c0;  // the slot's accumulator
+        if (s < L - 2) {
+          // middle forward layer l = s + 2: h_l -> A, 2 s'(z_l) -> stash
+          uint4* st_g = fwd ? stash_cta : stash_cta + ((size_t)(slot * (L - 2) + s) * (kH / 8) + (c0 >> 3)) * kTile;
+          const float sc8 = kF8 ? tw.fp8_scale[s] : 1.f;  // FP8: the layer's weight scale
+          const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + s * (kH / 2) + (c0 >> 1));
+          // two 16-column chunks are loaded at once, so the second load's
+          // latency hides behind the first chunk's arithmetic
 #pragma unroll 1
-            for (int cp = 0; cp < 64; cp += 32) {
+          for (int cp = 0; cp < 64; cp += 32) {
             uint32_t va[16], vb[16];
             ptx::tmem_ld16(t_acc + cp, va);
             ptx::tmem_ld16(t_acc + cp + 16, vb);
@@ -782,7 +828,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
               uint32_t o[8], st2[8];
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                const uint32_t zp = kF8 ? ptx::pack_f16x2(sc * __uint_as_float(v[2 * i]), sc * __uint_as_float(v[2 * i + 1]))
+                const uint32_t zp = kF8 ? ptx::pack_f16x2(sc8 * __uint_as_float(v[2 * i]), sc8 * __uint_as_float(v[2 * i + 1]))
                                         : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
                 const uint32_t u = ptx::hfma2(zp, kHalf2, bh[i]);
                 if constexpr (kFmt == 0) {
@@ -793,174 +839,159 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
                   o[i] = to_operand<kFmt>(hh);
                 }
               }
-              store8c(obuf, c0 + cc, o);
-              if (!fwd) ptx::tmem_st8(t_st + cc / 2, st2);
-            }
-            }
-            if (!fwd) ptx::tmem_wait_st();
-          } else if (s == L - 2) {
-            // last forward layer: f partial (FP32 sum), g_L = w_o s'(z_L) -> A
-            fpart = 0.f;
-            const float sc = kF8 ? tw.fp8_scale[L - 2] : 1.f;
-            const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + (L - 2) * (kH / 2) + (c0 >> 1));
-#pragma unroll 1
-            for (int cc = 0; cc < 64; cc += 16) {
-              uint32_t v[16];
-              ptx::tmem_ld16(t_acc + cc, v);
-              const uint4 b0 = bh4[cc / 8], b1 = bh4[cc / 8 + 1];
-              const uint32_t bh[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-              const uint4* wh4 = reinterpret_cast<const uint4*>(s_woh + (c0 + cc) / 2);
-              const uint4 w0 = wh4[0], w1 = wh4[1];
-              const uint32_t wh[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-              ptx::tmem_wait_ld();
-              uint32_t o[8];
-#pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                const uint32_t zp = kF8 ? ptx::pack_f16x2(sc * __uint_as_float(v[2 * i]), sc * __uint_as_float(v[2 * i + 1]))
-                                        : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-                const uint32_t u = ptx::hfma2(zp, kHalf2, bh[i]);
-                const float2 wo = *reinterpret_cast<const float2*>(s_wo + c0 + cc + 2 * i);
-                if constexpr (kFmt == 0) {
-                  // s(z) = u (1 + t) exactly in FP32 for f; g_L = (w_o / 2) 2 s'(z)
-                  // exactly in FP32, rounded once to BF16
-                  const uint32_t t = ptx::htanh2(u);
-                  const uint32_t tp1 = ptx::hadd2(kOne2, t);
-                  float h0, h1, g0, g1;
-                  ptx::f16x2_products(u, tp1, h0, h1);
-                  fpart = fmaf(wo.x, h0, fmaf(wo.y, h1, fpart));
-                  ptx::f16x2_products(wh[i], ptx::hfma2(tp1, ptx::hfnms2(u, t), tp1), g0, g1);
-                  o[i] = ptx::pack_bf16x2(g0, g1);
-                } else {
-                  uint32_t hh, s2;
-                  silu2(u, hh, s2);
-                  fpart = fmaf(wo.x, ptx::f16lo(hh), fmaf(wo.y, ptx::f16hi(hh), fpart));
-                  o[i] = to_operand<kFmt>(ptx::hmul2(wh[i], s2));
-                }
+              store8c(abuf, c0 + cc, o);
+              if (!fwd) {
+                st_g[(cc / 8) * kTile] = make_uint4(st2[0], st2[1], st2[2], st2[3]);
+                st_g[(cc / 8 + 1) * kTile] = make_uint4(st2[4], st2[5], st2[6], st2[7]);
               }
-              if (!fwd) store8c(obuf, c0 + cc, o);
-            }
-            s_f[(it & 1) * 4 * kTile + kq * kTile + row] = fpart;
-            ptx::mbar_arrive(bar(base, B_FD));
-          } else {
-            // reverse step: g_{l-1} = acc * 2 s'(z_{l-1}), acc = (W_l^T / 2) g_l
-            const int lm1 = 2 * L - 2 - s;
-            // FP8: acc = (64 / s_rev) (W^T / 2) g, so acc * s_rev is the next
-            // operand already carrying its x64
-            const float sc = kF8 ? tw.fp8_scale[L - 1 + (2 * L - 3 - s)] : 1.f;
-            // 2 s'(z_1) sits in the stash columns of z_{L-1} when there is a stash
-            const int lsrc = (lm1 >= 2) ? lm1 : (L - 1);
-            const bool stashed = lm1 >= 2 || L >= 3;
-#pragma unroll 1
-            for (int cc = 0; cc < 64; cc += 16) {
-              uint32_t v[16], d2[8];
-              ptx::tmem_ld16(t_acc + cc, v);
-              if (stashed) ptx::tmem_ld8(t_lane + 256 + 128 * (lsrc - 2) + ((c0 + cc) >> 1), d2);
-              ptx::tmem_wait_ld();
-              if (!stashed) {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                  uint32_t hh;
-                  silu2(first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2), hh, d2[i]);
-                }
-              }
-              uint32_t o[8];
-#pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                if constexpr (kFmt == 0) {
-                  // BF16: the product in FP32, one rounding to BF16 (one pack instead of two)
-                  o[i] = ptx::pack_bf16x2(__uint_as_float(v[2 * i]) * ptx::f16lo(d2[i]),
-                                          __uint_as_float(v[2 * i + 1]) * ptx::f16hi(d2[i]));
-                } else {
-                  const uint32_t ap = kF8 ? ptx::pack_f16x2(sc * __uint_as_float(v[2 * i]), sc * __uint_as_float(v[2 * i + 1]))
-                                          : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-                  o[i] = to_operand<kFmt>(ptx::hmul2(ap, d2[i]));
-                }
-              }
-              store8c(obuf, c0 + cc, o);
             }
           }
-          // (forward-only: the last step produces no operand, so no MMA waits for it)
-          if (!(fwd && s == n_steps - 1)) epi_done(h);
-          if (s == L - 1 && L >= 3) {
-            // the first reverse step has read this warp's stash columns of z_{L-1}:
-            // recompute 2 s'(z_1) = 2 s'(A_i + W_1p p) into them while the tensor
-            // core runs the next reverse chains (the last reverse step loads it)
-            const uint32_t t_r1 = t_lane + 256 + 128 * (L - 3) + (c0 >> 1);
+        } else if (s == L - 2) {
+          // last forward layer: f partial (FP32 sum), g_L = w_o s'(z_L) -> A
+          fpart = 0.f;
+          const float sc8 = kF8 ? tw.fp8_scale[L - 2] : 1.f;
+          const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + (L - 2) * (kH / 2) + (c0 >> 1));
 #pragma unroll 1
-            for (int cc = 0; cc < 64; cc += 16) {
-              uint32_t d2[8];
+          for (int cc = 0; cc < 64; cc += 16) {
+            uint32_t v[16];
+            ptx::tmem_ld16(t_acc + cc, v);
+            const uint4 b0 = bh4[cc / 8], b1 = bh4[cc / 8 + 1];
+            const uint32_t bh[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            const uint4* wh4 = reinterpret_cast<const uint4*>(s_woh + (c0 + cc) / 2);
+            const uint4 w0 = wh4[0], w1 = wh4[1];
+            const uint32_t wh[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            ptx::tmem_wait_ld();
+            uint32_t o[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const uint32_t zp = kF8 ? ptx::pack_f16x2(sc8 * __uint_as_float(v[2 * i]), sc8 * __uint_as_float(v[2 * i + 1]))
+                                      : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+              const uint32_t u = ptx::hfma2(zp, kHalf2, bh[i]);
+              const float2 wo = *reinterpret_cast<const float2*>(s_wo + c0 + cc + 2 * i);
+              if constexpr (kFmt == 0) {
+                // s(z) = u (1 + t) exactly in FP32 for f; g_L = (w_o / 2) 2 s'(z)
+                // exactly in FP32, rounded once to BF16
+                const uint32_t t = ptx::htanh2(u);
+                const uint32_t tp1 = ptx::hadd2(kOne2, t);
+                float h0, h1, g0, g1;
+                ptx::f16x2_products(u, tp1, h0, h1);
+                fpart = fmaf(wo.x, h0, fmaf(wo.y, h1, fpart));
+                ptx::f16x2_products(wh[i], ptx::hfma2(tp1, ptx::hfnms2(u, t), tp1), g0, g1);
+                o[i] = ptx::pack_bf16x2(g0, g1);
+              } else {
+                uint32_t hh, s2;
+                silu2(u, hh, s2);
+                fpart = fmaf(wo.x, ptx::f16lo(hh), fmaf(wo.y, ptx::f16hi(hh), fpart));
+                o[i] = to_operand<kFmt>(ptx::hmul2(wh[i], s2));
+              }
+            }
+            if (!fwd) store8c(abuf, c0 + cc, o);
+          }
+          s_f[((2 * slot + (jl & 1)) * 4 + kq) * kTile + row] = fpart;
+          ptx::mbar_arrive(bar(base, B_FD0 + slot));
+        } else {
+          // reverse step: g_{l-1} = acc * 2 s'(z_{l-1}), acc = (W_l^T / 2) g_l
+          // FP8: acc = (64 / s_rev) (W^T / 2) g, so acc * s_rev is the next
+          // operand already carrying its x64
+          const float sc8 = kF8 ? tw.fp8_scale[L - 1 + (2 * L - 3 - s)] : 1.f;
+          const uint32_t* aiw = aiw_base + slot * kEpiWarps * 32;
+          const uint4 pt = pt_base[slot * kTile];
+#pragma unroll
+          for (int cc = 0; cc < 64; cc += 16) {
+            uint32_t v[16], d2[8];
+            ptx::tmem_ld16(t_acc + cc, v);
+            if (stashed) {
+              d2[0] = dn0.x; d2[1] = dn0.y; d2[2] = dn0.z; d2[3] = dn0.w;
+              d2[4] = dn1.x; d2[5] = dn1.y; d2[6] = dn1.z; d2[7] = dn1.w;
+              if (cc + 16 < 64) {
+                dn0 = st_r[((cc + 16) / 8) * kTile];
+                dn1 = st_r[((cc + 16) / 8 + 1) * kTile];
+              }
+            } else {
+              // 2 s'(z_1) recomputed from A_i + W_1p p
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
                 uint32_t hh;
-                silu2(first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[cc / 2 + i], px2, py2, pz2), hh, d2[i]);
+                silu2(first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[cc / 2 + i], pt.x, pt.y, pt.z), hh, d2[i]);
               }
-              ptx::tmem_st8(t_r1 + cc / 2, d2);
             }
-            ptx::tmem_wait_st();
-          }
-          if (h1_early && s == 2 * L - 4) {
-            // the z_2 stash columns of this warp have been read: the next tile's h_1
-            load_tile(it + 1);
-            first_layer_tmem();
+            ptx::tmem_wait_ld();
+            uint32_t o[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              if constexpr (kFmt == 0) {
+                // BF16: the product in FP32, one rounding to BF16 (one pack instead of two)
+                o[i] = ptx::pack_bf16x2(__uint_as_float(v[2 * i]) * ptx::f16lo(d2[i]),
+                                        __uint_as_float(v[2 * i + 1]) * ptx::f16hi(d2[i]));
+              } else {
+                const uint32_t ap = kF8 ? ptx::pack_f16x2(sc8 * __uint_as_float(v[2 * i]), sc8 * __uint_as_float(v[2 * i + 1]))
+                                        : ptx::pack_f16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+                o[i] = to_operand<kFmt>(ptx::hmul2(ap, d2[i]));
+              }
+            }
+            store8c(abuf, c0 + cc, o);
           }
         }
+        // (forward-only: the last step produces no operand, so no MMA waits for it)
+        if (!(fwd && s == n_steps - 1)) arrive_lead(B_ED0 + 2 * slot + hg);
+        continue;
       }
-      if (!ok) break;
 
+      // ---- tail item of the slot's tile -------------------------------------------
+      const int cur_wp = slot ? wp1 : wp0, cur_start = slot ? start1 : start0, cur_len = slot ? len1 : len0;
+      const bool more = it + kSlots < my_tiles;
       if (fwd) {
-        // ---- forward-only tile tail: the next tile's first layer as soon as this
-        // warp's half of the last step is done (its buffer was last read by an
-        // earlier step, whose MMAs completed before this step's accumulator; the
-        // accumulator half it frees was read only by this half's warps), then f of
-        // this tile.  The f partials alternate between two buffers by tile parity:
-        // a tile two ahead, which rewrites this buffer, cannot start before every
-        // warp has released its first layer, which each does after this output.
-        if (it + 1 < my_tiles) {
-          load_tile(it + 1);
-          first_layer(it + 1);
+        // the next tile of the slot can start at once: the last step's MMAs have
+        // completed (its accumulator was read) and no MMA reads the A buffer
+        if (more) {
+          load_tile(it + kSlots);
+          first_layer(slot);
         }
-        if (!wait_epi_warp(bar(base, B_FD), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }
+        if (!wait_epi_warp(bar(base, B_FD0 + slot), (uint32_t)jl & 1u, abort_flag, tw.err)) { ok = false; break; }
         if (kq == 0 && row < cur_len) {
           int j;
           long long k;
           pair_at(w, cur_wp, cur_start + row, j, k);
-          const float* sf = s_f + (it & 1) * 4 * kTile;
+          const float* sf = s_f + (2 * slot + (jl & 1)) * 4 * kTile;
           w.f_out[k] = sf[row] + sf[kTile + row] + sf[2 * kTile + row] + sf[3 * kTile + row] + tw.bout;
         }
         continue;
       }
-
-      // ---- tile tail ------------------------------------------------------------
-      if (it + 1 < my_tiles) {
-        if (!h1_early) load_tile(it + 1);
-        // the next tile's first layer overwrites the A buffer that the last reverse
-        // step's chains read: the warps of half 0 have seen only their own chain
-        // complete, so they wait for the half-1 chain (its commit follows every
-        // earlier MMA; it cannot complete again before this first layer is done)
-        if (hg == 0) {
-          if (!wait_epi_warp(bar(base, B_ACC0 + 1), (acc_n - 1u) & 1u, abort_flag, tw.err)) { ok = false; break; }
-          ptx::tc_fence_after();
-        }
-        if (h1_early) first_layer_copy(it + 1);
-        else first_layer(it + 1);
-      }
-      // the input-Jacobian chain of this tile
-      if (!wait_epi_warp(bar(base, B_ACCJ), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }
+      // the input-Jacobian chain of this tile (it has read the A buffer)
+      if (!wait_epi_warp(bar(base, B_ACCJ0 + slot), (uint32_t)jl & 1u, abort_flag, tw.err)) { ok = false; break; }
       ptx::tc_fence_after();
-      // output stage, shared by all 16 warps: the 4 warps of a row quad split the
-      // gradient components (d = kq, kq + 4, kq + 8) and each reads only the
-      // Jacobian columns they need (warp-uniform columns, no indexed registers)
-      if (!wait_epi_warp(bar(base, B_FD), (uint32_t)it & 1u, abort_flag, tw.err)) { ok = false; break; }
+      // the 4 warps of a row quad split the gradient components (d = kq, kq + 4,
+      // kq + 8) and each reads only the Jacobian columns they need (warp-uniform
+      // columns, no indexed registers), and the sin / cos they need, before the
+      // next tile replaces them
       uint32_t jv[3][2];
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         const int d = kq + 4 * m;
-        ptx::tmem_ld2(t_lane + 384 + (d < 2 ? 0 : 2 * d - 2), jv[m]);
+        ptx::tmem_ld2(t_lane + (uint32_t)(slot * kH + kHalf) + (d < 2 ? 0 : 2 * d - 2), jv[m]);
       }
-      const float* sf = s_f + (it & 1) * 4 * kTile;
-      const float fval = sf[row] + sf[kTile + row] + sf[2 * kTile + row] + sf[3 * kTile + row] + tw.bout;
+      float trs[3], trc[3];
+      {
+        const float* tr = trig_base + slot * kEpiWarps * 24;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          const int a = kq + 4 * m - 2;
+          trs[m] = (a >= 0 && a < w.n_ang) ? tr[2 * a] : 0.f;
+          trc[m] = (a >= 0 && a < w.n_ang) ? tr[2 * a + 1] : 0.f;
+        }
+      }
       ptx::tmem_wait_ld();
-      const float* tr = trigw + (it & 1) * 24;
+      // the slot's next tile: its first layer goes into the A buffer (free: the
+      // Jacobian chain has completed) and its first MMAs into the accumulator
+      // (free: the Jacobian columns were just read, ordered by the arrival)
+      if (more) {
+        load_tile(it + kSlots);
+        first_layer(slot);
+      }
+      // output stage, shared by all 16 warps
+      if (!wait_epi_warp(bar(base, B_FD0 + slot), (uint32_t)jl & 1u, abort_flag, tw.err)) { ok = false; break; }
+      const float* sf = s_f + (2 * slot + (jl & 1)) * 4 * kTile;
+      const float fval = sf[row] + sf[kTile + row] + sf[2 * kTile + row] + sf[3 * kTile + row] + tw.bout;
       if (kF8) {  // J = (s_J / 64) x the accumulator of FP8 W_1q^T and the x64 operand
         const float js = tw.fp8_scale[2 * L - 2] * (1.f / kGradScale8);
 #pragma unroll
@@ -976,8 +1007,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         if (d < 2) {
           dqm[m] = __uint_as_float(d == 0 ? jv[m][0] : jv[m][1]);
         } else if (d < n) {  // angle a = d - 2: (sin, cos) chain rule of Eq. (10)
-          const int a = d - 2;
-          dqm[m] = tr[2 * a + 1] * __uint_as_float(jv[m][0]) - tr[2 * a] * __uint_as_float(jv[m][1]);
+          dqm[m] = trc[m] * __uint_as_float(jv[m][0]) - trs[m] * __uint_as_float(jv[m][1]);
         } else {
           dqm[m] = 0.f;
         }
@@ -998,13 +1028,14 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         }
       } else {
         // the merge warp has read the previous tile's records
-        if (it > 0 && !wait_epi_warp(bar(base, B_MD), (uint32_t)(it - 1) & 1u, abort_flag, tw.err)) {
+        if (n_out > 0 && !wait_epi_warp(bar(base, B_MD), (n_out - 1u) & 1u, abort_flag, tw.err)) {
           ok = false;
           break;
         }
         warp_partial_part(w.mode, w.param, valid, fval, dqm, kq, n, j, cur_start + row, &s_part[quad]);
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(bar(base, B_PD));
+        ++n_out;
       }
     }
   }
@@ -1066,6 +1097,11 @@ uint16_t to_bits(float x, bool f16) {
 }  // namespace
 
 int tc_tile_pairs() { return kTile; }
+
+// [slot][layer 2..L-1][8-column chunk][row] of 16 bytes per CTA
+static size_t stash_bytes_per_cta(int L) { return L > 2 ? (size_t)kSlots * (L - 2) * (kH / 8) * kTile * 16 : 0; }
+
+size_t tc_stash_bytes(int L, int num_sms) { return stash_bytes_per_cta(L) * (size_t)(num_sms > 1 ? num_sms : 2); }
 
 bool tc_supported(int H, int L, int n_dof) { return H == kH && L >= 2 && L <= 4 && n_dof >= 3 && n_dof <= kMaxDof; }
 
@@ -1180,8 +1216,18 @@ cudaError_t launch_tc_t(const WorkDesc& w, const TcWeights& tw, int num_sms, cud
   if (num_sms > 0 && 2 * mc > num_sms) mc = num_sms / 2 > 0 ? num_sms / 2 : 1;
   const int npt = (w.n_tiles + 1) / 2;
   if (npt <= 0) return cudaSuccess;
-  cfg.gridDim = dim3(2 * (npt < mc ? npt : mc));
-  return cudaLaunchKernelEx(&cfg, tc_fused_kernel<kFmt, kFwd>, w, tw.map_w, tw.map_j, tw);
+  const int grid = 2 * (npt < mc ? npt : mc);
+  cfg.gridDim = dim3(grid);
+  const size_t stash_bytes = kFwd ? 0 : stash_bytes_per_cta(tw.L) * (size_t)grid;
+  if (stash_bytes == 0 || w.stash != nullptr)
+    return cudaLaunchKernelEx(&cfg, tc_fused_kernel<kFmt, kFwd>, w, tw.map_w, tw.map_j, tw);
+  // the stash from the library's pool, stream-ordered around the launch
+  WorkDesc ws = w;
+  cudaError_t e = lib_malloc_async(&ws.stash, stash_bytes, s);
+  if (e != cudaSuccess) return e;
+  e = cudaLaunchKernelEx(&cfg, tc_fused_kernel<kFmt, kFwd>, ws, tw.map_w, tw.map_j, tw);
+  const cudaError_t ef = cudaFreeAsync(ws.stash, s);
+  return e != cudaSuccess ? e : ef;
 }
 
 cudaError_t launch_wait_expiry_probe(int* err, long long limit_cycles, int* seen, cudaStream_t s) {

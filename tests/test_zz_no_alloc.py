@@ -82,12 +82,12 @@ def test_noalloc_rejects_requests_beyond_its_array():
     g = lib()
     shape, w = small_net()
     net = g.create_net(9, 256, 4, w, "bf16")
-    q = to_dev(torch, random_traj(20000, 9, 3))  # 20000 x 256 floats of first-layer terms > 16 MiB
+    q = to_dev(torch, random_traj(70000, 9, 3))  # 70000 x 256 floats of first-layer terms > 64 MiB
     p = to_dev(torch, synth.uniform_points(synth.SplitMix64(4), 10, [0, 0, 0], [1, 1, 1]))
     raw = g._lib.load()
-    cost = torch.empty(20000, device="cuda")
-    grad = torch.empty(20000, 9, device="cuda")
-    rc = raw.gcdf_collision_cost_noalloc(net.handle, ctypes.c_void_p(q.data_ptr()), 20000,
+    cost = torch.empty(70000, device="cuda")
+    grad = torch.empty(70000, 9, device="cuda")
+    rc = raw.gcdf_collision_cost_noalloc(net.handle, ctypes.c_void_p(q.data_ptr()), 70000,
                                          ctypes.c_void_p(p.data_ptr()), 10, None, None, 0, None, 1, 0.1,
                                          ctypes.c_void_p(cost.data_ptr()), ctypes.c_void_p(grad.data_ptr()), None,
                                          None)
