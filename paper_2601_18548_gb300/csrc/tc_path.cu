@@ -84,7 +84,7 @@ constexpr int kRowsCta = kHalf / 2;    // weight rows of a chain held by each CT
 constexpr int kSlots = 2;              // tiles in flight per CTA pair
 constexpr int kStages = 4;             // weight ring depth
 constexpr int kSlabBytes = kRowsCta * 128;  // 64 rows x 64 16-bit values (one K = 64 slab)
-constexpr int kStageBytes = 2 * kSlabBytes; // K = 128 of one chain per stage
+constexpr int kStageBytes = 2 * kSlabBytes; // one stage: 16 KB per CTA
 constexpr int kABytes = kTile * kH * 2;
 constexpr int kThreads = 608;          // 19 warps
 constexpr int kMergeWarp = 18;         // merges each tile's four row-quad records
@@ -421,9 +421,12 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
                 const __grid_constant__ CUtensorMap map_j, const TcWeights tw) {
   constexpr bool kF16 = kFmt == 1;
   constexpr bool kF8 = kFmt == 2;
-  // 16-bit operands: a K = 128 stage is two 64-element slabs of 128-byte rows;
-  // FP8: one 128-element slab (the shared-memory map is the same, half used)
-  constexpr int kSlabsPerStage = kF8 ? 1 : 2;
+  // A 128-byte slab row holds K = 64 16-bit or K = 128 FP8 values; a weight
+  // step (N = 256, K = 256) takes 4 or 2 ring stages of one slab each.  An
+  // input-Jacobian stage (N = 32) holds K = 128: two 16-bit slabs or one FP8 slab.
+  constexpr int kSlabK = kF8 ? 128 : 64;
+  constexpr int kStagesPerStep = kH / kSlabK;
+  constexpr int kSlabsPerStage = kF8 ? 1 : 2;  // input-Jacobian stages
   extern __shared__ uint8_t smem_raw[];
   const uint32_t base = (ptx::smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - ptx::smem_u32(smem_raw));
@@ -519,24 +522,30 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
 
   if (warp == 0) {
     // ================= TMA producer (both CTAs) =================
-    // Stage g mod kStages holds K = 128 of one chain: this CTA's kRowsCta weight
-    // rows (two 64-wide slabs).  Both CTAs' loads complete on the even CTA's
-    // FULL barrier; each CTA refills a stage once the MMAs that read it have
-    // completed (the even CTA's commit arrives on both CTAs' EMPTY barriers).
+    // A step's stage holds one 128-byte-wide K slab (K = 64 of 16-bit operands,
+    // K = 128 of FP8) of this CTA's 128 weight rows (the step's N = 256 output
+    // rows are split between the two CTAs), loaded as two 64-row boxes; an
+    // input-Jacobian stage holds K = 128 of its nj / 2 rows.  Both CTAs' loads
+    // complete on the even CTA's FULL barrier; each CTA refills a stage once the
+    // MMAs that read it have completed (the even CTA's commit arrives on both
+    // CTAs' EMPTY barriers).
     if (lane == 0 && my_tiles > 0) {
       const uint32_t full_lead = ptx::mapa_shared(bar(base, B_FULL0), 0);
       long long g = 0;         // stages issued
       int pst = 0;             // ring stage of g
       uint32_t puse = 0;       // (g / kStages) & 1
       bool ok = true;
-      auto load_stage = [&](const CUtensorMap* map, int x0, int y, uint32_t slab_bytes) -> bool {
+      // dx, dy: offset of the second box (the next K slab of the same rows, or
+      // the next 64 rows of the same K slab); none for FP8 Jacobian stages
+      auto load_stage = [&](const CUtensorMap* map, int x0, int y, int dx, int dy, bool two,
+                            uint32_t box_bytes) -> bool {
         const int st = pst;
         if (g >= kStages && !wait_role(bar(base, B_EMPTY0 + st), puse ^ 1u, abort_flag, tw.err)) return false;
         const uint32_t fb = full_lead + 8u * (uint32_t)st;
-        // slabs x 2 CTAs
-        if (leader) ptx::mbar_arrive_expect_tx(bar(base, B_FULL0 + st), 2u * kSlabsPerStage * slab_bytes);
+        // boxes x 2 CTAs
+        if (leader) ptx::mbar_arrive_expect_tx(bar(base, B_FULL0 + st), 2u * (two ? 2u : 1u) * box_bytes);
         ptx::tma_load_2d_pair(base + kOffRing + st * kStageBytes, map, x0, y, fb);
-        if (!kF8) ptx::tma_load_2d_pair(base + kOffRing + st * kStageBytes + kSlabBytes, map, x0 + 64, y, fb);
+        if (two) ptx::tma_load_2d_pair(base + kOffRing + st * kStageBytes + kSlabBytes, map, x0 + dx, y + dy, fb);
         ++g;
         if (++pst == kStages) { pst = 0; puse ^= 1u; }
         return true;
@@ -546,12 +555,11 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       while (ok && sc.next(slot, jl, s)) {
         if (s < n_steps) {
           const int row0 = (s < L - 1) ? s * kH : (L - 1 + (2 * L - 3 - s)) * kH;
-          for (int hh = 0; hh < 2 && ok; ++hh)
-            for (int pr = 0; pr < 2 && ok; ++pr)
-              ok = load_stage(&map_w, pr * 128, row0 + hh * kHalf + (int)rank * kRowsCta, kSlabBytes);
+          for (int k = 0; k < kStagesPerStep && ok; ++k)
+            ok = load_stage(&map_w, k * kSlabK, row0 + (int)rank * kHalf, 0, kRowsCta, true, kSlabBytes);
         } else if (!fwd) {  // W_1q^T: nj rows, nj / 2 per CTA
           for (int pr = 0; pr < 2 && ok; ++pr)
-            ok = load_stage(&map_j, pr * 128, (int)rank * (nj / 2), (uint32_t)(nj / 2) * 128u);
+            ok = load_stage(&map_j, pr * 128, (int)rank * (nj / 2), 64, 0, !kF8, (uint32_t)(nj / 2) * 128u);
         }
       }
       // drain (even CTA): the last kStages stages are the only ones that can be
@@ -568,7 +576,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     // ================= MMA issuer (even CTA, for both) =================
     if (lane == 0 && my_tiles > 0 && leader) {
       // (E4M3 x E4M3 has the format code 0 of FP16 x FP16 in the same fields)
-      const uint32_t id128 = ptx::idesc_f16kind(2 * kTile, kHalf, kF16 || kF8);
+      const uint32_t id256 = ptx::idesc_f16kind(2 * kTile, kH, kF16 || kF8);
       const uint32_t idj = ptx::idesc_f16kind(2 * kTile, nj, kF16 || kF8);
       long long g = 0;         // stages consumed
       int cst = 0;             // ring stage of g
@@ -583,7 +591,22 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       // (selected, never indexed: a dynamically indexed array would live in local memory)
       const uint64_t dA0 = ptx::smem_desc_sw128(base + kOffA0, 1024), dA1 = ptx::smem_desc_sw128(base + kOffA1, 1024);
       const uint64_t dRing = ptx::smem_desc_sw128(base + kOffRing, 1024);
-      // one stage: K = 128 of a chain (8 MMAs of K = 16), then release the stage in both CTAs
+      // one weight-step stage: one K slab, 4 MMAs of N = 256 (32 bytes of K each),
+      // then release the stage in both CTAs
+      auto stage_mmas_w = [&](uint32_t dtm, uint64_t da, bool first) {
+        const uint64_t db = dRing + (uint64_t)(cst * (kStageBytes >> 4));
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          if constexpr (kF8)
+            ptx::mma_pair_f8(dtm, da + (uint64_t)(2 * ks), db + (uint64_t)(2 * ks), id256, (first && ks == 0) ? 0u : 1u);
+          else
+            ptx::mma_pair(dtm, da + (uint64_t)(2 * ks), db + (uint64_t)(2 * ks), id256, (first && ks == 0) ? 0u : 1u);
+        }
+        ptx::mma_commit_pair(bar(base, B_EMPTY0 + cst));
+        ++g;
+        if (++cst == kStages) { cst = 0; cph ^= 1u; }
+      };
+      // one input-Jacobian stage: K = 128 (8 MMAs of K = 16, or 4 of FP8 K = 32)
       auto stage_mmas = [&](uint32_t dtm, uint64_t da, uint32_t idd, bool first) {
         const uint64_t db = dRing + (uint64_t)(cst * (kStageBytes >> 4));
         // 32 bytes of K per MMA: K = 16 of 16-bit operands over two slabs, K = 32 of FP8 over one
@@ -609,43 +632,49 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         const bool jstep = (s == n_steps);
         if (fwd && jstep) continue;  // forward-only tiles have no MMA in their tail
         const uint64_t dAbuf = slot ? dA1 : dA0;
-        // the input Jacobian df/denc = W_1q^T g_1 goes to the first nj columns of
-        // the slot's accumulator half b (its last reverse step's epilogue has read
-        // them).  Half b: the next tile's chain a, which may start when only the
-        // half-a warps have written their first layer, does not touch it; chain b
-        // starts after every warp has, and every warp reads the Jacobian first.
-        const uint32_t idd = jstep ? idj : id128;
-        for (int hh = 0; hh < (jstep ? 1 : 2) && ok; ++hh) {
-          const uint32_t dtm = tmem + (uint32_t)(slot * kH) + (jstep ? (uint32_t)kHalf : (uint32_t)(hh * kHalf));
+        // The operand's columns [128 h, 128 h + 128) come from the slot's previous
+        // step's half h (both CTAs' epilogues arrive); step 0: the tile's first
+        // layer, on its own barriers.  Either also proves that the warps of that
+        // half have read their columns of the slot's accumulator (or, at step 0,
+        // the Jacobian columns).  Every chain waits for both halves before its
+        // first MMA: a step's first MMA writes the whole accumulator, and the
+        // Jacobian chain writes columns of half b.
+        auto wait_half = [&](int h) -> bool {
+          const int bi = 2 * slot + h;
+          const uint32_t edn = slot ? (h ? ed11 : ed10) : (h ? ed01 : ed00);
+          const bool ok_w = (s == 0) ? wait_role(bar(base, B_FL0 + bi), (uint32_t)jl & 1u, abort_flag, tw.err)
+                                     : wait_role(bar(base, B_ED0 + bi), edn & 1u, abort_flag, tw.err);
+          if (ok_w && s != 0) {
+            if (slot) { if (h) ++ed11; else ++ed10; }
+            else { if (h) ++ed01; else ++ed00; }
+          }
+          ptx::tc_fence_after();
+          return ok_w;
+        };
+        if (jstep) {
+          // the input Jacobian df/denc = W_1q^T g_1 goes to the first nj columns of
+          // the slot's accumulator half b (every warp reads it before it writes its
+          // part of the next tile's first layer)
+          const uint32_t dtm = tmem + (uint32_t)(slot * kH + kHalf);
+          ok = wait_half(0) && wait_half(1);
 #pragma unroll
-          for (int pr = 0; pr < 2; ++pr) {
-            if (hh == 0) {
-              // input columns [128 pr, 128 pr + 128) come from the slot's previous
-              // step's half pr (both CTAs' epilogues arrive); step 0: the tile's
-              // first layer, on its own barriers.  Either also proves that half of
-              // the slot's accumulator has been read.
-              const int bi = 2 * slot + pr;
-              const uint32_t edn = slot ? (pr ? ed11 : ed10) : (pr ? ed01 : ed00);
-              const bool ok_w = (s == 0)
-                  ? wait_role(bar(base, B_FL0 + bi), (uint32_t)jl & 1u, abort_flag, tw.err)
-                  : wait_role(bar(base, B_ED0 + bi), edn & 1u, abort_flag, tw.err);
-              if (!ok_w) {
-                ok = false;
-                break;
-              }
-              if (s != 0) {
-                if (slot) { if (pr) ++ed11; else ++ed10; }
-                else { if (pr) ++ed01; else ++ed00; }
-              }
-              ptx::tc_fence_after();
-            }
-            // both CTAs' slabs written by TMA: the transaction barrier orders them before the MMAs
+          for (int pr = 0; pr < 2 && ok; ++pr) {
             if (!wait_role(bar(base, B_FULL0 + cst), cph, abort_flag, tw.err)) { ok = false; break; }
-            stage_mmas(dtm, dAbuf + (uint64_t)((kSlabsPerStage * pr) * (kTile * 128) >> 4), idd, pr == 0);
+            stage_mmas(dtm, dAbuf + (uint64_t)((kSlabsPerStage * pr) * (kTile * 128) >> 4), idj, pr == 0);
+          }
+        } else {
+          // one chain of N = 256 into the slot's accumulator: its A operand is read
+          // once per step
+          const uint32_t dtm = tmem + (uint32_t)(slot * kH);
+          ok = wait_half(0) && wait_half(1);
+#pragma unroll
+          for (int k = 0; k < kStagesPerStep && ok; ++k) {
+            if (!wait_role(bar(base, B_FULL0 + cst), cph, abort_flag, tw.err)) { ok = false; break; }
+            stage_mmas_w(dtm, dAbuf + (uint64_t)(k * (kTile * 128 >> 4)), k == 0);
           }
         }
-        // one commit per step: it tracks every earlier MMA of this thread, so
-        // both chains (and with them every read of the slot's A buffer) are done
+        // one commit per step: it tracks every earlier MMA of this thread, so the
+        // chain (and with it every read of the slot's A buffer) is done
         if (ok) ptx::mma_commit_pair(bar(base, jstep ? B_ACCJ0 + slot : B_ACC0 + slot));
       }
       // all issued MMAs complete before TMEM is released: wait for the last
