@@ -181,14 +181,14 @@ GCDF_API int gcdf_collision_cost(gcdf_net *net, const float *q, int n_waypoints,
  * memory is budgeted up front).  Arguments, outputs and results are those of
  * gcdf_collision_cost.
  *
- * Every temporary comes from one 64 MiB array that is part of the library's
+ * Every temporary comes from one 96 MiB array that is part of the library's
  * image on each device (every GPU that loads the library holds it until the
  * process exits).  A request needing more — per-waypoint terms
  * (n_waypoints x (hidden + 2 (n_dof - 2)) floats), the tile prefix of point
  * lists, one 64-byte record per tile (tiles: 128 pairs on BF16/FP16,
  * 8192 / hidden pairs on FP32) and, on BF16/FP16/FP8 nets, the tensor-core
- * kernel's stash of 2 s'(z_l) for the hidden layers 2..L-1 (256 KiB per SM
- * and stashed layer) — is rejected with GCDF_EINVAL before any work is
+ * kernel's stash of 2 s'(z_l) for the hidden layers 1..L-1 (128 KiB per SM
+ * and layer) — is rejected with GCDF_EINVAL before any work is
  * enqueued.  Nothing in the array needs to start at zero: each call writes
  * every word it later reads.
  *

@@ -658,7 +658,7 @@ const char* gcdf_last_error(void) { return g_err; }
 
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = 64u << 20;  // 64 MiB per device, held until the process exits
+constexpr size_t kNoAllocScratchBytes = 96u << 20;  // 96 MiB per device, held until the process exits
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }

@@ -55,7 +55,7 @@ struct WorkDesc {
   float* f_out;          // query: (n_pairs)
   float* g_out;          // query: (n_pairs, n) or nullptr
   Partial* partials;     // reductions: (n_tiles)
-  // tensor-core path with gradients: per-CTA stash of 2 s'(z_l), layers 2..L-1
+  // tensor-core path with gradients: per-CTA stash of 2 s'(z_l), layers 1..L-1
   // (tc_stash_bytes); nullptr lets launch_tc take it from the library's pool
   void* stash;
 };
@@ -235,8 +235,8 @@ struct TcWeights {
   int* err;                    // device status word (set when a bounded wait gives up)
 };
 cudaError_t launch_tc(const WorkDesc& w, const TcWeights& tw, int num_sms, cudaStream_t s);
-// Bytes of the stash a launch with L layers uses on at most num_sms SMs (0 when
-// it needs none: value-only queries, L = 2).
+// Bytes of the stash a launch with L layers uses on at most num_sms SMs (value-
+// only queries use none).
 size_t tc_stash_bytes(int L, int num_sms);
 size_t tc_image_elems(int H, int L, int d_q);
 // Operand image (16-bit elements, or bytes for FP8) and, for FP8, the scales.

@@ -36,12 +36,13 @@
 //   u = z / 2 = acc / 2 + b / 2,  t = tanh(u),  s(z) = z sigma(z) = u (1 + t),
 //   2 s'(z) = (1 + t) + s(z) (1 - t)
 // (BF16 operands: s(z) = u (1 + t) formed exactly in FP32 and rounded once).
-// 2 s'(z_l) of layers 2..L-1 goes to a per-CTA stash in global memory as FP16
+// 2 s'(z_l) of layers 1..L-1 goes to a per-CTA stash in global memory as FP16
 // pairs ([slot][layer][8-column chunk][row], 16 bytes: each warp store or load
-// covers 512 contiguous bytes; 256 KB per CTA and stashed layer, so it stays
-// in L2), read back by the reverse step that needs it; the halved reverse
-// operands cancel the factor 2.  s'(z_1) is recomputed from A_i + W_1p p_j in
-// the last reverse step.  The output sum f = w_o . s(z_L) accumulates in FP32.
+// covers 512 contiguous bytes; 128 KB per CTA and layer, so it stays in L2),
+// written by the epilogue that computes s(z_l) (the first layer's by the tile's
+// first-layer pass) and read back by the reverse step that needs it; the
+// halved reverse operands cancel the factor 2.  The output sum
+// f = w_o . s(z_L) accumulates in FP32.
 //
 // TMEM columns (512, allocated for the CTA pair): slot s's accumulator is
 // [256 s, 256 s + 256), half a first; the input-Jacobian chain (N = 32) of a
@@ -717,9 +718,12 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     uint32_t* aiw_base = reinterpret_cast<uint32_t*>(gbase + kOffAiw) + e * 32;  // + slot * kEpiWarps * 32
     float* trig_base = reinterpret_cast<float*>(gbase + kOffTrig) + e * 24;     // + slot * kEpiWarps * 24
     uint4* pt_base = reinterpret_cast<uint4*>(gbase + kOffPt) + row;            // + slot * kTile
-    // global stash of 2 s'(z_l), layers 2..L-1: [slot][layer][8-column chunk][row], 16 bytes
-    uint4* stash_cta = reinterpret_cast<uint4*>(w.stash) +
-                       (size_t)blockIdx.x * kSlots * (L > 2 ? L - 2 : 0) * (kH / 8) * kTile + row;
+    // global stash of 2 s'(z_l), layers 1..L-1 (index l - 1):
+    // [slot][layer][8-column chunk][row], 16 bytes
+    uint4* stash_cta = reinterpret_cast<uint4*>(w.stash) + (size_t)blockIdx.x * kSlots * (L - 1) * (kH / 8) * kTile + row;
+    auto stash_at = [&](int sl, int l, int c0) -> uint4* {
+      return stash_cta + ((size_t)(sl * (L - 1) + (l - 1)) * (kH / 8) + (c0 >> 3)) * kTile;
+    };
     uint32_t acc_n0 = 0, acc_n1 = 0;       // ACC completions consumed per slot
     uint32_t n_out = 0;                    // output stages done (partial records)
     bool ok = true;
@@ -786,21 +790,32 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       if (lane < 2 * w.n_ang) trigw[lane] = w.trig[(size_t)wp * 2 * w.n_ang + lane];
       __syncwarp();
     };
-    // h_1 = s(A_i + W_1p p) for this row and the warp's 64 columns -> the slot's A buffer
+    // h_1 = s(A_i + W_1p p) for this row and the warp's 64 columns -> the slot's
+    // A buffer; 2 s'(z_1) -> the stash (the last reverse step reads it)
     auto first_layer = [&](int sl) {
       const uint32_t abuf = base + (sl ? kOffA1 : kOffA0);
       const uint32_t* aiw = aiw_base + sl * kEpiWarps * 32;
       const uint4 pt = pt_base[sl * kTile];
+      uint4* st_g = fwd ? stash_cta : stash_at(sl, 1, cw);
 #pragma unroll 1
       for (int cc = 0; cc < 64; cc += 16) {
-        uint32_t o[8];
+        uint32_t o[8], st2[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const uint32_t u = first_layer_u2(s_w1p[(cw + cc) / 2 + i], aiw[cc / 2 + i], pt.x, pt.y, pt.z);
-          const uint32_t tt = ptx::htanh2(u);
-          o[i] = to_operand<kFmt>(ptx::hfma2(u, tt, u));
+          if constexpr (kFmt == 0) {
+            silu2_bf16(u, o[i], st2[i]);
+          } else {
+            uint32_t hh;
+            silu2(u, hh, st2[i]);
+            o[i] = to_operand<kFmt>(hh);
+          }
         }
         store8c(abuf, cw + cc, o);
+        if (!fwd) {
+          st_g[(cc / 8) * kTile] = make_uint4(st2[0], st2[1], st2[2], st2[3]);
+          st_g[(cc / 8 + 1) * kTile] = make_uint4(st2[4], st2[5], st2[6], st2[7]);
+        }
       }
       arrive_lead(B_FL0 + 2 * sl + hg);
     };
@@ -817,12 +832,11 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       const int it = 2 * jl + slot;
       const uint32_t abuf = base + (slot ? kOffA1 : kOffA0);
       if (s < n_steps) {
-        // a reverse step whose factor 2 s'(z_{l-1}) is stashed starts loading its
-        // first 16 columns before it waits for the accumulator
+        // a reverse step starts loading the first 16 columns of its stashed factor
+        // 2 s'(z_{l-1}) before it waits for the accumulator
         const int lm1 = 2 * L - 2 - s;
-        const bool stashed = !fwd && s >= L - 1 && lm1 >= 2;
-        const uint4* st_r = stashed ? stash_cta + ((size_t)(slot * (L - 2) + (lm1 - 2)) * (kH / 8) + (cw >> 3)) * kTile
-                                    : stash_cta;
+        const bool stashed = !fwd && s >= L - 1;
+        const uint4* st_r = stashed ? stash_at(slot, lm1, cw) : stash_cta;
         uint4 dn0 = make_uint4(0u, 0u, 0u, 0u), dn1 = dn0;  // the next chunk's stash
         if (stashed) {
           dn0 = st_r[0];
@@ -838,7 +852,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         const uint32_t t_acc = t_lane + (uint32_t)(slot * kH) + c0;  // the slot's accumulator
         if (s < L - 2) {
           // middle forward layer l = s + 2: h_l -> A, 2 s'(z_l) -> stash
-          uint4* st_g = fwd ? stash_cta : stash_cta + ((size_t)(slot * (L - 2) + s) * (kH / 8) + (c0 >> 3)) * kTile;
+          uint4* st_g = fwd ? stash_cta : stash_at(slot, s + 2, c0);
           const float sc8 = kF8 ? tw.fp8_scale[s] : 1.f;  // FP8: the layer's weight scale
           const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + s * (kH / 2) + (c0 >> 1));
           // two 16-column chunks are loaded at once, so the second load's
@@ -923,26 +937,15 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
           // FP8: acc = (64 / s_rev) (W^T / 2) g, so acc * s_rev is the next
           // operand already carrying its x64
           const float sc8 = kF8 ? tw.fp8_scale[L - 1 + (2 * L - 3 - s)] : 1.f;
-          const uint32_t* aiw = aiw_base + slot * kEpiWarps * 32;
-          const uint4 pt = pt_base[slot * kTile];
 #pragma unroll
           for (int cc = 0; cc < 64; cc += 16) {
             uint32_t v[16], d2[8];
             ptx::tmem_ld16(t_acc + cc, v);
-            if (stashed) {
-              d2[0] = dn0.x; d2[1] = dn0.y; d2[2] = dn0.z; d2[3] = dn0.w;
-              d2[4] = dn1.x; d2[5] = dn1.y; d2[6] = dn1.z; d2[7] = dn1.w;
-              if (cc + 16 < 64) {
-                dn0 = st_r[((cc + 16) / 8) * kTile];
-                dn1 = st_r[((cc + 16) / 8 + 1) * kTile];
-              }
-            } else {
-              // 2 s'(z_1) recomputed from A_i + W_1p p
-#pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                uint32_t hh;
-                silu2(first_layer_u2(s_w1p[(c0 + cc) / 2 + i], aiw[cc / 2 + i], pt.x, pt.y, pt.z), hh, d2[i]);
-              }
+            d2[0] = dn0.x; d2[1] = dn0.y; d2[2] = dn0.z; d2[3] = dn0.w;
+            d2[4] = dn1.x; d2[5] = dn1.y; d2[6] = dn1.z; d2[7] = dn1.w;
+            if (cc + 16 < 64) {
+              dn0 = st_r[((cc + 16) / 8) * kTile];
+              dn1 = st_r[((cc + 16) / 8 + 1) * kTile];
             }
             ptx::tmem_wait_ld();
             uint32_t o[8];
@@ -1127,8 +1130,8 @@ uint16_t to_bits(float x, bool f16) {
 
 int tc_tile_pairs() { return kTile; }
 
-// [slot][layer 2..L-1][8-column chunk][row] of 16 bytes per CTA
-static size_t stash_bytes_per_cta(int L) { return L > 2 ? (size_t)kSlots * (L - 2) * (kH / 8) * kTile * 16 : 0; }
+// [slot][layer 1..L-1][8-column chunk][row] of 16 bytes per CTA
+static size_t stash_bytes_per_cta(int L) { return L >= 2 ? (size_t)kSlots * (L - 1) * (kH / 8) * kTile * 16 : 0; }
 
 size_t tc_stash_bytes(int L, int num_sms) { return stash_bytes_per_cta(L) * (size_t)(num_sms > 1 ? num_sms : 2); }
 

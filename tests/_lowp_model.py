@@ -58,7 +58,7 @@ def _silu_f16(u):
 
 
 def _silu_bf16(u):
-    """The BF16-operand epilogue of the hidden layers 2..L: t and 1 + t in FP16,
+    """The BF16-operand epilogue of the hidden layers 1..L: t and 1 + t in FP16,
     s(z) = u (1 + t) exact (the product of two FP16 values, formed in FP32), and
     2 s'(z) = (1 + t) + (1 + t)(u - u t) by FP16 multiply-adds."""
     t = round_f16(np.tanh(u))
@@ -94,7 +94,7 @@ def lowp_eval(n_dof, H, L, weights, q_rows, p_rows, shift_rows=None, fmt="bf16")
     u1 = round_f16(0.5 * A)
     for d in range(3):
         u1 = round_f16(w1h[None, :, d] * p16[:, d:d + 1] + u1)
-    h1, s2_1 = _silu_f16(u1)
+    h1, s2_1 = silu(u1)
     h = R(h1)
     stash = {}
     for l in range(1, L - 1):  # middle layers 2..L-1 (0-based index l)

@@ -82,7 +82,7 @@ def test_noalloc_rejects_requests_beyond_its_array():
     g = lib()
     shape, w = small_net()
     net = g.create_net(9, 256, 4, w, "bf16")
-    q = to_dev(torch, random_traj(70000, 9, 3))  # 70000 x 256 floats of first-layer terms > 64 MiB
+    q = to_dev(torch, random_traj(70000, 9, 3))  # 70000 x 256 floats of terms + the stash > 96 MiB
     p = to_dev(torch, synth.uniform_points(synth.SplitMix64(4), 10, [0, 0, 0], [1, 1, 1]))
     raw = g._lib.load()
     cost = torch.empty(70000, device="cuda")
