@@ -103,15 +103,16 @@ constexpr int kOffWo = kOffW1p + (kH / 2) * 16;                 // [H] fp32 w_o
 constexpr int kOffWoh = kOffWo + kH * 4;                        // [H/2] f16x2 w_o / 2
 constexpr int kOffAiw = kOffWoh + (kH / 2) * 4;                 // [2 slots][16 warps][32] f16x2 A_i / 2
 constexpr int kOffPt = kOffAiw + kSlots * kEpiWarps * 32 * 4;   // [2 slots][128 rows] uint4: the row's point, packed
-constexpr int kOffTrig = kOffPt + kSlots * kTile * 16;          // [2 slots][16 warps][24] sin, cos
-constexpr int kOffF = kOffTrig + kSlots * kEpiWarps * 24 * 4;   // [2 slots][2 tiles][4][128] f partials
+constexpr int kOffTrig = kOffPt + kSlots * kTile * 16;          // [2 slots][2 tiles][16 warps][24] sin, cos
+constexpr int kOffTinfo = kOffTrig + kSlots * 2 * kEpiWarps * 24 * 4;  // [2 slots][2 tiles][16 warps] int4 tile
+constexpr int kOffF = kOffTinfo + kSlots * 2 * kEpiWarps * 16;  // [2 slots][2 tiles][4][128] f partials
 constexpr int kOffPart = kOffF + kSlots * 2 * 4 * kTile * 4;    // 4 partial records
 constexpr int kOffBar = kOffPart + 4 * (int)sizeof(Partial);
 constexpr int kNumBars = 2 * kStages + 16;
 constexpr int kOffSlot = kOffBar + kNumBars * 8;
 constexpr int kSmemBytes = kOffSlot + 16 + 1024;                // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024 - 64, "shared memory budget");
-static_assert(kOffPt % 16 == 0 && kOffBar % 8 == 0, "alignment");
+static_assert(kOffPt % 16 == 0 && kOffTinfo % 16 == 0 && kOffBar % 8 == 0, "alignment");
 
 // barrier indices
 constexpr int B_FULL0 = 0;              // + stage: both CTAs' slabs landed (used in the even CTA)
@@ -716,7 +717,11 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     const uint32_t rbase = (row >> 3) * 1024 + (row & 7) * 128;
     const int r7 = row & 7;
     uint32_t* aiw_base = reinterpret_cast<uint32_t*>(gbase + kOffAiw) + e * 32;  // + slot * kEpiWarps * 32
-    float* trig_base = reinterpret_cast<float*>(gbase + kOffTrig) + e * 24;     // + slot * kEpiWarps * 24
+    // per slot and tile parity (the slot's next tile is loaded while the output
+    // stage of the current one is still to come): this warp's sin / cos and its
+    // copy of the tile's (waypoint, first list position, length)
+    float* trig_base = reinterpret_cast<float*>(gbase + kOffTrig) + e * 24;     // + (2 slot + par) * kEpiWarps * 24
+    int4* tinfo_base = reinterpret_cast<int4*>(gbase + kOffTinfo) + e;           // + (2 slot + par) * kEpiWarps
     uint4* pt_base = reinterpret_cast<uint4*>(gbase + kOffPt) + row;            // + slot * kTile
     // global stash of 2 s'(z_l), layers 1..L-1 (index l - 1):
     // [slot][layer][8-column chunk][row], 16 bytes
@@ -727,9 +732,6 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
     uint32_t acc_n0 = 0, acc_n1 = 0;       // ACC completions consumed per slot
     uint32_t n_out = 0;                    // output stages done (partial records)
     bool ok = true;
-    // per slot: the tile in flight (waypoint, first list position, length);
-    // scalars, selected by slot (a runtime-indexed array would live in local memory)
-    int wp0 = 0, wp1 = 0, start0 = 0, start1 = 0, len0 = 0, len1 = 0;
 
     // byte offset (within an A buffer) of columns c0 + 8 q .. c0 + 8 q + 7 of this row
     auto aoff = [&](int c0, int q) -> uint32_t {
@@ -763,14 +765,15 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       }
     };
     // tile `it` (local index) into slot it & 1: its waypoint's A_i / 2 for this
-    // warp's columns, its sin / cos, and this row's point
+    // warp's columns and this row's point (read by its first layer), its sin /
+    // cos and its list range (read by its output stage, by tile parity)
     auto load_tile = [&](int it) {
       const int sl = it & 1;
+      const int tp = 2 * sl + ((it >> 1) & 1);
       const int t = 2 * (cluster + it * nclusters) + (int)rank;
       int wp = 0, start = 0, len = 0;
       if (t < ntiles) tile_lookup(w, t, wp, start, len);  // else: the odd CTA's half of the last pair tile
-      if (sl) { wp1 = wp; start1 = start; len1 = len; }
-      else { wp0 = wp; start0 = start; len0 = len; }
+      if (lane == 0) tinfo_base[tp * kEpiWarps] = make_int4(wp, start, len, 0);
       float px = 0.f, py = 0.f, pz = 0.f;
       if (row < len) {
         int j;
@@ -782,7 +785,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       }
       const float* Ai = w.A + (size_t)wp * kH + cw;
       uint32_t* aiw = aiw_base + sl * kEpiWarps * 32;
-      float* trigw = trig_base + sl * kEpiWarps * 24;
+      float* trigw = trig_base + tp * kEpiWarps * 24;
       __syncwarp();
       // (the four warps of a row quad store the same point: each reads back its own store)
       pt_base[sl * kTile] = make_uint4(ptx::pack_f16x2(px, px), ptx::pack_f16x2(py, py), ptx::pack_f16x2(pz, pz), 0u);
@@ -966,11 +969,16 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
         }
         // (forward-only: the last step produces no operand, so no MMA waits for it)
         if (!(fwd && s == n_steps - 1)) arrive_lead(B_ED0 + 2 * slot + hg);
+        // after the tile's last reverse step: fetch the slot's next tile, whose
+        // first layer the tail writes as soon as the Jacobian chain has read the
+        // A buffer (this step has slack; the tail does not)
+        if (!fwd && s == n_steps - 1 && it + kSlots < my_tiles) load_tile(it + kSlots);
         continue;
       }
 
       // ---- tail item of the slot's tile -------------------------------------------
-      const int cur_wp = slot ? wp1 : wp0, cur_start = slot ? start1 : start0, cur_len = slot ? len1 : len0;
+      const int4 ti = tinfo_base[(2 * slot + (jl & 1)) * kEpiWarps];
+      const int cur_wp = ti.x, cur_start = ti.y, cur_len = ti.z;
       const bool more = it + kSlots < my_tiles;
       if (fwd) {
         // the next tile of the slot can start at once: the last step's MMAs have
@@ -1004,7 +1012,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       }
       float trs[3], trc[3];
       {
-        const float* tr = trig_base + slot * kEpiWarps * 24;
+        const float* tr = trig_base + (2 * slot + (jl & 1)) * kEpiWarps * 24;
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
           const int a = kq + 4 * m - 2;
@@ -1016,10 +1024,7 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
       // the slot's next tile: its first layer goes into the A buffer (free: the
       // Jacobian chain has completed) and its first MMAs into the accumulator
       // (free: the Jacobian columns were just read, ordered by the arrival)
-      if (more) {
-        load_tile(it + kSlots);
-        first_layer(slot);
-      }
+      if (more) first_layer(slot);  // its inputs were loaded after the last reverse step
       // output stage, shared by all 16 warps
       if (!wait_epi_warp(bar(base, B_FD0 + slot), (uint32_t)jl & 1u, abort_flag, tw.err)) { ok = false; break; }
       const float* sf = s_f + (2 * slot + (jl & 1)) * 4 * kTile;
