@@ -64,6 +64,9 @@ struct GemmArgs {
 
 __device__ __forceinline__ uint32_t bar(uint32_t base, int i) { return base + kOffBar + 8 * i; }
 
+// sigma(z) of the BF16 products' epilogues (s(z), s'(z) and s''(z) all use it)
+__device__ __forceinline__ float fast_sigmoid(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
+
 __device__ __forceinline__ bool wait_bounded(uint32_t b, uint32_t parity, volatile int* abort_flag, int* err) {
   if (ptx::mbar_try_wait(b, parity)) return true;
   const long long t0 = clock64();
@@ -235,11 +238,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
             if (ep.add_in) v += tile[lane * 33 + j];
             if (ep.acc_out) tile2[lane * 33 + j] = raw;  // (this thread's own element, read above)
           } else if (silu) {
-            // h = s(z), z = acc + b, with the arithmetic of the element-wise
-            // kernel of the generic path (expf, an exactly rounded reciprocal
-            // equal to 1 / x): the same activations and s' to the bit
+            // h = s(z), z = acc + b; the sigmoid from the fast exponential and
+            // division intrinsics (a few ulp in FP32, far below the BF16
+            // rounding of every product operand), the same as for s'' below
             const float z = v + __ldg(ep.bias + min(nb + j, a.N - 1));
-            const float sg = __frcp_rn(1.f + expf(-z));
+            const float sg = fast_sigmoid(z);
             v = z * sg;
             tile2[lane * 33 + j] = sg * (1.f + z * (1.f - sg));
           }
@@ -277,7 +280,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const float z = __uint_as_float(u[j]) + __ldg(ep.bias + min(nb + j, a.N - 1));
-            const float sg = __frcp_rn(1.f + expf(-z));
+            const float sg = fast_sigmoid(z);
             tile2[lane * 33 + j] = sg * (1.f - sg) * (2.f + z * (1.f - 2.f * sg));
           }
           __syncwarp();
