@@ -11,7 +11,7 @@
 // A CTA pair (cluster of 2) computes one 256 x 128 tile of C with
 // tcgen05.mma.cta_group::2 (M = 256, N = 128, K = 16 per instruction): each
 // CTA holds 128 rows of A and 64 rows of B per stage and its own 128 x 128
-// FP32 accumulator in TMEM, which four epilogue warps read back with
+// FP32 accumulator in TMEM, which eight epilogue warps read back with
 // tcgen05.ld and store (or add) to C.  72 KB of shared memory (a 3-stage
 // ring, reused by the epilogue) and 128 TMEM columns per CTA, so three CTAs
 // share an SM and their epilogues overlap each other's main loops (measured
@@ -214,6 +214,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
       for (int c0 = 64 * ch; c0 < 64 * ch + 64; c0 += 32) {
         const int nb = n0 + c0;  // first column of the block
         if (nb >= a.N) break;
+        // the block's 32 biases, one per lane, handed to every lane by shuffles
+        const float bias_l = silu ? __ldg(ep.bias + min(nb + lane, a.N - 1)) : 0.f;
         if (ep.mode == kEpiMul) {
           // the factor block (and the added block) come in coalesced (lane = column)
 #pragma unroll 4
@@ -241,7 +243,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
             // h = s(z), z = acc + b; the sigmoid from the fast exponential and
             // division intrinsics (a few ulp in FP32, far below the BF16
             // rounding of every product operand), the same as for s'' below
-            const float z = v + __ldg(ep.bias + min(nb + j, a.N - 1));
+            const float z = v + __shfl_sync(0xffffffffu, bias_l, j);
             const float sg = fast_sigmoid(z);
             v = z * sg;
             tile2[lane * 33 + j] = sg * (1.f + z * (1.f - sg));
@@ -279,7 +281,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
           __syncwarp();
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const float z = __uint_as_float(u[j]) + __ldg(ep.bias + min(nb + j, a.N - 1));
+            const float z = __uint_as_float(u[j]) + __shfl_sync(0xffffffffu, bias_l, j);
             const float sg = fast_sigmoid(z);
             tile2[lane * 33 + j] = sg * (1.f - sg) * (2.f + z * (1.f - 2.f * sg));
           }
