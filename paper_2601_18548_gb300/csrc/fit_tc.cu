@@ -46,8 +46,8 @@ constexpr int B_FULL0 = 0, B_EMPTY0 = kStages, B_ACC = 2 * kStages;
 constexpr int kNumBars = 2 * kStages + 1;
 constexpr int kOffSlot = kOffBar + kNumBars * 8;
 constexpr int kSmemBytes = kOffSlot + 16 + 1024;  // + alignment slack
-// the epilogue's two 33 x 32 float tiles per epilogue warp reuse the idle ring
-static_assert(8 * 2 * 33 * 32 * 4 <= kStages * kStageBytes, "epilogue tiles fit in the ring");
+// the epilogue's two 32 x 36 float tiles per epilogue warp reuse the idle ring
+static_assert(8 * 2 * 36 * 32 * 4 <= kStages * kStageBytes, "epilogue tiles fit in the ring");
 constexpr long long kWaitCycles = 2000000000LL;   // ~1 s
 
 struct GemmArgs {
@@ -66,6 +66,12 @@ __device__ __forceinline__ uint32_t bar(uint32_t base, int i) { return base + kO
 
 // sigma(z) of the BF16 products' epilogues (s(z), s'(z) and s''(z) all use it)
 __device__ __forceinline__ float fast_sigmoid(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
+
+// Rows of p (leading dimension ld elements of eb bytes) all start on an
+// `align`-byte boundary (or p is absent).
+__device__ __forceinline__ bool rows_aligned(const void* p, long long ld, int eb, int align) {
+  return p == nullptr || ((reinterpret_cast<uintptr_t>(p) % align) == 0 && (ld * eb) % align == 0);
+}
 
 __device__ __forceinline__ bool wait_bounded(uint32_t b, uint32_t parity, volatile int* abort_flag, int* err) {
   if (ptx::mbar_try_wait(b, parity)) return true;
@@ -196,111 +202,210 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
     if (ok) {
       ptx::tc_fence_after();
       // Each 32 x 32 block (lane = row after tcgen05.ld) is transposed through
-      // shared memory, so that each store instruction writes 32 consecutive
-      // values of one row (one 128-byte line of FP32) instead of one value in
-      // 32 rows.  The operand ring is idle once the accumulator is complete
-      // (every MMA, and so every TMA load, has finished): each warp uses two
-      // 33 x 32 float tiles of it (row stride 33: conflict-free both ways), one
-      // for the result and one for s'(z) or the incoming factor.
-      float* tile = reinterpret_cast<float*>(gbase) + (warp - 2) * (2 * 32 * 33);
-      float* tile2 = tile + 32 * 33;
+      // shared memory, so that global stores run along rows.  The operand ring
+      // is idle once the accumulator is complete (every MMA, and so every TMA
+      // load, has finished): each warp uses two 32 x 36 float tiles of it (row
+      // stride 36 = 144 bytes: 16-byte accesses of a row by the 32 lanes and of
+      // 4 rows x 8 column quads by a warp are both conflict-free), one for the
+      // result and one for s'(z) or the incoming factor.  Where the block lies
+      // inside the matrix and every output row is 16-byte aligned, lane
+      // (rg, ck) = (lane / 8, lane mod 8) moves columns 4 ck .. 4 ck + 3 of rows
+      // 4 r + rg with 16-byte accesses (a warp covers 4 rows x 128 bytes per
+      // instruction); otherwise lane = column, one element per access.
+      constexpr int kTs = 36;
+      float* tile = reinterpret_cast<float*>(gbase) + (warp - 2) * (2 * 32 * kTs);
+      float* tile2 = tile + 32 * kTs;
       const int row0 = tm * 2 * kRowsA + (int)rank * kRowsA + q * 32;
       float* cz = a.C ? a.C + (long long)blockIdx.y * a.zstride : nullptr;
       const int n0 = tn * kTileN;
       const GemmEpilogue& ep = a.ep;
       const bool silu = ep.mode == kEpiBiasSilu;
       const bool mul = ep.mode == kEpiMul;
+      const bool vec = rows_aligned(cz, a.ldc, 4, 16) && rows_aligned(ep.s_in, ep.ld_s, 4, 16) &&
+                       rows_aligned(ep.add_in, ep.ld_s, 4, 16) && rows_aligned(ep.s_out, ep.ld_s, 4, 16) &&
+                       rows_aligned(ep.acc_out, ep.ld_s, 4, 16) && rows_aligned(ep.s2_out, ep.ld_s, 4, 16) &&
+                       rows_aligned(ep.img, ep.ld_img, 2, 8) && rows_aligned(ep.colsum, ep.ld_colsum, 4, 16);
+      const int rg = lane >> 3, ck = lane & 7;
 #pragma unroll 1
       for (int c0 = 64 * ch; c0 < 64 * ch + 64; c0 += 32) {
         const int nb = n0 + c0;  // first column of the block
         if (nb >= a.N) break;
+        const bool vb = vec && nb + 32 <= a.N;
         // the block's 32 biases, one per lane, handed to every lane by shuffles
         const float bias_l = silu ? __ldg(ep.bias + min(nb + lane, a.N - 1)) : 0.f;
-        if (ep.mode == kEpiMul) {
-          // the factor block (and the added block) come in coalesced (lane = column)
+        if (mul) {
+          // the factor block (and the added block) come in along rows
+          if (vb) {
 #pragma unroll 4
-          for (int r = 0; r < 32; ++r) {
-            const int rr = row0 + r, n = nb + lane;
-            const bool ok_rc = rr < a.M && n < a.N;
-            tile2[r * 33 + lane] = ok_rc ? ep.s_in[(long long)rr * ep.ld_s + n] : 0.f;
-            if (ep.add_in) tile[r * 33 + lane] = ok_rc ? ep.add_in[(long long)rr * ep.ld_s + n] : 0.f;
+            for (int r4 = 0; r4 < 8; ++r4) {
+              const int r = 4 * r4 + rg, rr = row0 + r;
+              const long long o = (long long)rr * ep.ld_s + nb + 4 * ck;
+              const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+              *reinterpret_cast<float4*>(tile2 + r * kTs + 4 * ck) =
+                  rr < a.M ? *reinterpret_cast<const float4*>(ep.s_in + o) : z4;
+              if (ep.add_in)
+                *reinterpret_cast<float4*>(tile + r * kTs + 4 * ck) =
+                    rr < a.M ? *reinterpret_cast<const float4*>(ep.add_in + o) : z4;
+            }
+          } else {
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r) {
+              const int rr = row0 + r, n = nb + lane;
+              const bool ok_rc = rr < a.M && n < a.N;
+              tile2[r * kTs + lane] = ok_rc ? ep.s_in[(long long)rr * ep.ld_s + n] : 0.f;
+              if (ep.add_in) tile[r * kTs + lane] = ok_rc ? ep.add_in[(long long)rr * ep.ld_s + n] : 0.f;
+            }
           }
           __syncwarp();
         }
         uint32_t u[32];
         ptx::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, u);
         ptx::tmem_wait_ld();
-        // this row's 32 results into the tile (s'(z) into the second tile)
+        // this row's 32 results into the tile (s'(z), or the raw accumulator,
+        // into the second tile), four columns per 16-byte access; the
+        // transposed BF16 image straight from registers: for each column the 32
+        // lanes write 32 consecutive rows (64 contiguous bytes)
+        const bool row_ok = row0 + lane < a.M;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          float v = __uint_as_float(u[j]);
-          if (ep.mode == kEpiMul) {
-            const float raw = v;
-            v *= tile2[lane * 33 + j];
-            if (ep.add_in) v += tile[lane * 33 + j];
-            if (ep.acc_out) tile2[lane * 33 + j] = raw;  // (this thread's own element, read above)
-          } else if (silu) {
-            // h = s(z), z = acc + b; the sigmoid from the fast exponential and
-            // division intrinsics (a few ulp in FP32, far below the BF16
-            // rounding of every product operand), the same as for s'' below
-            const float z = v + __shfl_sync(0xffffffffu, bias_l, j);
-            const float sg = fast_sigmoid(z);
-            v = z * sg;
-            tile2[lane * 33 + j] = sg * (1.f + z * (1.f - sg));
+        for (int j4 = 0; j4 < 8; ++j4) {
+          float4 f4 = make_float4(0.f, 0.f, 0.f, 0.f), a4 = f4;
+          if (mul) {
+            f4 = *reinterpret_cast<const float4*>(tile2 + lane * kTs + 4 * j4);
+            if (ep.add_in) a4 = *reinterpret_cast<const float4*>(tile + lane * kTs + 4 * j4);
           }
-          tile[lane * 33 + j] = v;
+          const float fj[4] = {f4.x, f4.y, f4.z, f4.w}, aj[4] = {a4.x, a4.y, a4.z, a4.w};
+          float vv[4], ww[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int j = 4 * j4 + t;
+            float v = __uint_as_float(u[j]);
+            float w2 = 0.f;
+            if (mul) {
+              w2 = v;  // the raw accumulator, for acc_out
+              v *= fj[t];
+              if (ep.add_in) v += aj[t];
+            } else if (silu) {
+              // h = s(z), z = acc + b; the sigmoid from the fast exponential and
+              // division intrinsics (a few ulp in FP32, far below the BF16
+              // rounding of every product operand), the same as for s'' below
+              const float z = v + __shfl_sync(0xffffffffu, bias_l, j);
+              const float sg = fast_sigmoid(z);
+              v = z * sg;
+              w2 = sg * (1.f + z * (1.f - sg));
+            }
+            vv[t] = v;
+            ww[t] = w2;
+            if (ep.imgT && row_ok && nb + j < a.N)
+              ep.imgT[(long long)(nb + j) * ep.ld_imgT + row0 + lane] = __float2bfloat16_rn(v);
+          }
+          *reinterpret_cast<float4*>(tile + lane * kTs + 4 * j4) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+          if (silu || (mul && ep.acc_out))
+            *reinterpret_cast<float4*>(tile2 + lane * kTs + 4 * j4) = make_float4(ww[0], ww[1], ww[2], ww[3]);
         }
         __syncwarp();
-        // row-major outputs, lane = column: C (or C += for split partials),
-        // s'(z), the BF16 image and the column sums
-        const int n = nb + lane;
-        if (n < a.N) {
-          float cs = 0.f;
-#pragma unroll 4
-          for (int r = 0; r < 32; ++r) {
-            const int rr = row0 + r;
+        // row-major outputs: C (or C += for split partials), s'(z) or the raw
+        // accumulator, the BF16 image and the column sums
+        if (vb) {
+          float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+          for (int r4 = 0; r4 < 8; ++r4) {
+            const int r = 4 * r4 + rg, rr = row0 + r;
             if (rr < a.M) {
-              const float x = tile[r * 33 + lane];
+              const int n = nb + 4 * ck;
+              const float4 x = *reinterpret_cast<const float4*>(tile + r * kTs + 4 * ck);
               if (cz) {
-                float* c = cz + (long long)rr * a.ldc + n;
-                *c = a.accumulate ? *c + x : x;
+                float4* c = reinterpret_cast<float4*>(cz + (long long)rr * a.ldc + n);
+                if (a.accumulate) {
+                  const float4 o = *c;
+                  *c = make_float4(o.x + x.x, o.y + x.y, o.z + x.z, o.w + x.w);
+                } else {
+                  *c = x;
+                }
               }
-              if (silu && ep.s_out) ep.s_out[(long long)rr * ep.ld_s + n] = tile2[r * 33 + lane];
-              if (mul && ep.acc_out) ep.acc_out[(long long)rr * ep.ld_s + n] = tile2[r * 33 + lane];
-              if (ep.img) ep.img[(long long)rr * ep.ld_img + n] = __float2bfloat16_rn(x);
-              cs += x;
+              if ((silu && ep.s_out) || (mul && ep.acc_out)) {
+                float* dst = silu ? ep.s_out : ep.acc_out;
+                *reinterpret_cast<float4*>(dst + (long long)rr * ep.ld_s + n) =
+                    *reinterpret_cast<const float4*>(tile2 + r * kTs + 4 * ck);
+              }
+              if (ep.img) {
+                const __nv_bfloat162 lo = __floats2bfloat162_rn(x.x, x.y), hi = __floats2bfloat162_rn(x.z, x.w);
+                uint2 pk;
+                pk.x = *reinterpret_cast<const uint32_t*>(&lo);
+                pk.y = *reinterpret_cast<const uint32_t*>(&hi);
+                *reinterpret_cast<uint2*>(ep.img + (long long)rr * ep.ld_img + n) = pk;
+              }
+              cs.x += x.x;
+              cs.y += x.y;
+              cs.z += x.z;
+              cs.w += x.w;
             }
           }
-          // column sums of this block's rows, summed later over the row blocks
-          // in a fixed order (blocks past the last row hold no rows)
-          if (ep.colsum && row0 < a.M) ep.colsum[(long long)(row0 >> 5) * ep.ld_colsum + n] = cs;
-        }
-        if (silu && ep.s2_out) {
-          // s''(z) for the second-order products: recomputed from the accumulators
-          // still in registers, then stored row by row like s'(z)
-          __syncwarp();
+          // column sums of this block's rows (the four row groups added in a
+          // fixed order), summed later over the row blocks in a fixed order
+          // (blocks past the last row hold no rows)
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float z = __uint_as_float(u[j]) + __shfl_sync(0xffffffffu, bias_l, j);
-            const float sg = fast_sigmoid(z);
-            tile2[lane * 33 + j] = sg * (1.f - sg) * (2.f + z * (1.f - 2.f * sg));
+          for (int o = 8; o <= 16; o <<= 1) {
+            cs.x += __shfl_xor_sync(0xffffffffu, cs.x, o);
+            cs.y += __shfl_xor_sync(0xffffffffu, cs.y, o);
+            cs.z += __shfl_xor_sync(0xffffffffu, cs.z, o);
+            cs.w += __shfl_xor_sync(0xffffffffu, cs.w, o);
           }
-          __syncwarp();
+          if (ep.colsum && row0 < a.M && rg == 0)
+            *reinterpret_cast<float4*>(ep.colsum + (long long)(row0 >> 5) * ep.ld_colsum + nb + 4 * ck) = cs;
+        } else {
+          const int n = nb + lane;
           if (n < a.N) {
+            float cs = 0.f;
 #pragma unroll 4
             for (int r = 0; r < 32; ++r) {
               const int rr = row0 + r;
-              if (rr < a.M) ep.s2_out[(long long)rr * ep.ld_s + n] = tile2[r * 33 + lane];
+              if (rr < a.M) {
+                const float x = tile[r * kTs + lane];
+                if (cz) {
+                  float* c = cz + (long long)rr * a.ldc + n;
+                  *c = a.accumulate ? *c + x : x;
+                }
+                if (silu && ep.s_out) ep.s_out[(long long)rr * ep.ld_s + n] = tile2[r * kTs + lane];
+                if (mul && ep.acc_out) ep.acc_out[(long long)rr * ep.ld_s + n] = tile2[r * kTs + lane];
+                if (ep.img) ep.img[(long long)rr * ep.ld_img + n] = __float2bfloat16_rn(x);
+                cs += x;
+              }
             }
+            if (ep.colsum && row0 < a.M) ep.colsum[(long long)(row0 >> 5) * ep.ld_colsum + n] = cs;
           }
         }
-        if (ep.imgT && row0 + lane < a.M) {
-          // transposed BF16 image: for each column the 32 lanes write 32
-          // consecutive rows (64 contiguous bytes)
+        if (silu && ep.s2_out) {
+          // s''(z) for the second-order products: recomputed from the accumulators
+          // still in registers, then stored along rows like s'(z)
+          __syncwarp();
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4) {
+            float ww[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const int j = 4 * j4 + t;
+              const float z = __uint_as_float(u[j]) + __shfl_sync(0xffffffffu, bias_l, j);
+              const float sg = fast_sigmoid(z);
+              ww[t] = sg * (1.f - sg) * (2.f + z * (1.f - 2.f * sg));
+            }
+            *reinterpret_cast<float4*>(tile2 + lane * kTs + 4 * j4) = make_float4(ww[0], ww[1], ww[2], ww[3]);
+          }
+          __syncwarp();
+          if (vb) {
+#pragma unroll 2
+            for (int r4 = 0; r4 < 8; ++r4) {
+              const int r = 4 * r4 + rg, rr = row0 + r;
+              if (rr < a.M)
+                *reinterpret_cast<float4*>(ep.s2_out + (long long)rr * ep.ld_s + nb + 4 * ck) =
+                    *reinterpret_cast<const float4*>(tile2 + r * kTs + 4 * ck);
+            }
+          } else if (nb + lane < a.N) {
 #pragma unroll 4
-          for (int j = 0; j < 32; ++j)
-            if (nb + j < a.N)
-              ep.imgT[(long long)(nb + j) * ep.ld_imgT + row0 + lane] = __float2bfloat16_rn(tile[lane * 33 + j]);
+            for (int r = 0; r < 32; ++r) {
+              const int rr = row0 + r;
+              if (rr < a.M) ep.s2_out[(long long)rr * ep.ld_s + nb + lane] = tile2[r * kTs + lane];
+            }
+          }
         }
         __syncwarp();
       }
