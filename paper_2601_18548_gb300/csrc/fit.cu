@@ -116,14 +116,19 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const float* __restr
 // C = sum over z of the partial tiles, in increasing z.
 __global__ void sum_partials_kernel(const float* __restrict__ P, int splits, int M, int N, int ldp,
                                     float* __restrict__ C, int ldc, int accumulate) {
-  const long long total = (long long)M * N;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int m = (int)(e / N), n = (int)(e - (long long)m * N);
-    float s = 0.f;
-    for (int z = 0; z < splits; ++z) s += P[((long long)z * M + m) * ldp + n];
-    C[(long long)m * ldc + n] = accumulate ? C[(long long)m * ldc + n] + s : s;
-  }
+  // grid: x over columns, y over rows (grid-strided), so no index division
+  for (int m = blockIdx.y; m < M; m += gridDim.y)
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+      float s = 0.f;
+      for (int z = 0; z < splits; ++z) s += P[((long long)z * M + m) * ldp + n];
+      C[(long long)m * ldc + n] = accumulate ? C[(long long)m * ldc + n] + s : s;
+    }
+}
+
+// launch shape of sum_partials_kernel for an M x N result
+dim3 partials_grid(int M, int N) {
+  const int gx = (N + 255) / 256, gy = M;
+  return dim3((unsigned)(gx < 1 ? 1 : (gx < 64 ? gx : 64)), (unsigned)(gy < 1 ? 1 : (gy < 65535 ? gy : 65535)));
 }
 
 // out[c] = sum_b X[b, c] w_b (w NULL: 1) over the rows of one of `chunks`
@@ -312,8 +317,7 @@ cudaError_t gemm(const float* A, long long sam, long long sak, const float* B, l
     gemm_kernel<<<grid, kGemmThreads, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, kc, accumulate ? 1 : 0);
   } else {
     gemm_kernel<<<grid, kGemmThreads, 0, s>>>(A, sam, sak, B, sbk, sbn, partials, N, M, N, K, kc, 0);
-    sum_partials_kernel<<<grid1((long long)M * N), 256, 0, s>>>(partials, splits, M, N, N, C, ldc,
-                                                                accumulate ? 1 : 0);
+    sum_partials_kernel<<<partials_grid(M, N), 256, 0, s>>>(partials, splits, M, N, N, C, ldc, accumulate ? 1 : 0);
   }
   return cudaGetLastError();
 }
@@ -325,7 +329,7 @@ cudaError_t colsum(const float* X, int rows, int C, const float* w, float* out, 
   while (chunks > 1 && (size_t)chunks * C > pfl) --chunks;
   dim3 grid((C + 255) / 256, chunks);
   colsum_kernel<<<grid, 256, 0, s>>>(X, rows, C, w, chunks, partials);
-  sum_partials_kernel<<<grid1(C), 256, 0, s>>>(partials, chunks, 1, C, C, out, C, accumulate ? 1 : 0);
+  sum_partials_kernel<<<partials_grid(1, C), 256, 0, s>>>(partials, chunks, 1, C, C, out, C, accumulate ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -435,8 +439,8 @@ struct Ctx {
       e = tc_gemm_bf16(A, lda, B, ldb, M, N, K, partials, N, (long long)M * N, (int)splits, (int)per, false, err, s,
                        &enc_fail);
       if (e == cudaSuccess && !enc_fail)
-        sum_partials_kernel<<<grid1((long long)M * N), 256, 0, s>>>(partials, (int)splits, M, N, N, C, ldc,
-                                                                    accumulate ? 1 : 0);
+        sum_partials_kernel<<<partials_grid(M, N), 256, 0, s>>>(partials, (int)splits, M, N, N, C, ldc,
+                                                                accumulate ? 1 : 0);
     }
     if (enc_fail) return cudaErrorInvalidValue;
     return e != cudaSuccess ? e : cudaGetLastError();
