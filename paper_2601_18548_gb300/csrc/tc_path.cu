@@ -860,17 +860,16 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
           uint4* st_g = fwd ? stash_cta : stash_at(slot, s + 2, c0);
           const float sc8 = kF8 ? tw.fp8_scale[s] : 1.f;  // FP8: the layer's weight scale
           const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + s * (kH / 2) + (c0 >> 1));
-          // two 16-column chunks are loaded at once, so the second load's
-          // latency hides behind the first chunk's arithmetic
+          // 32 columns per TMEM load (one instruction, one wait), arithmetic in
+          // 16-column chunks
 #pragma unroll 1
           for (int cp = 0; cp < 64; cp += 32) {
-            uint32_t va[16], vb[16];
-            ptx::tmem_ld16(t_acc + cp, va);
-            ptx::tmem_ld16(t_acc + cp + 16, vb);
+            uint32_t vab[32];
+            ptx::tmem_ld32(t_acc + cp, vab);
             ptx::tmem_wait_ld();
 #pragma unroll
             for (int cc = cp; cc < cp + 32; cc += 16) {
-              const uint32_t* v = (cc - cp) ? vb : va;
+              const uint32_t* v = vab + (cc - cp);
               const uint4 b0 = bh4[cc / 8], b1 = bh4[cc / 8 + 1];
               const uint32_t bh[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
               uint32_t o[8], st2[8];
