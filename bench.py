@@ -873,16 +873,21 @@ def run_fit(args):
     target = torch.zeros(B, device="cuda")
 
     def step():
+        if prec == "bf16":
+            # the forward keeps its tape; the VJP runs the reverse sweep from it
+            f, tape = g.fit_forward_tape((n, H, L), w, q, p, precision=prec)
+            gf = (2.0 / B) * (f - target)
+            return g.fit_vjp_tape((n, H, L), w, q, p, gf, tape, want_dq=False, precision=prec)
         f = g.fit_forward((n, H, L), w, q, p, precision=prec)
         gf = (2.0 / B) * (f - target)
         return g.fit_vjp((n, H, L), w, q, p, gf, want_dq=False, precision=prec)
     ms = _time_events(step, reps=args.steps if args.steps < 20 else 10)
     d_in = 3 + 2 + 2 * (n - 2)
-    # GEMM FLOPs: forward (d_in H + (L-1) H^2 + H) x 2 per sample, twice (the
-    # forward and the forward inside the VJP), weight gradients the same
+    # GEMM FLOPs: forward (d_in H + (L-1) H^2 + H) x 2 per sample (twice with
+    # FP32, whose VJP recomputes the forward), weight gradients the same
     # again, back-products (L-1) H^2 x 2
     fwd = 2 * (d_in * H + (L - 1) * H * H + H)
-    flops = B * (2 * fwd + fwd + 2 * (L - 1) * H * H)
+    flops = B * ((1 if prec == "bf16" else 2) * fwd + fwd + 2 * (L - 1) * H * H)
     if prec == "fp32":
         fma = measure_fp32_fma_peak(g, torch)
         peak, bound = fma["tflops"], "alu"
@@ -895,7 +900,9 @@ def run_fit(args):
     line = {"metric": "differentiable fit training step", "unit": "samples/s", "value": B / (ms / 1e3),
             "n_gpus": 1, "dtype": "bf16" if prec == "bf16" else "f32", "data": "synthetic",
             "config": {"net": "10-DOF 5 x 512 SiLU", "batch": B, "loss": "distance (Table I)",
-                       "operands": "BF16, FP32 accumulation and master weights" if prec == "bf16" else "FP32"},
+                       "operands": "BF16, FP32 accumulation and master weights" if prec == "bf16" else "FP32",
+                       "backward": ("from the forward's tape (gcdf_fit_forward_tape / gcdf_fit_vjp_tape)"
+                                    if prec == "bf16" else "recomputes the forward (gcdf_fit_vjp)")},
             "ms_per_step": ms,
             "roofline": {"bound": bound, "achieved": flops / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                          "frac": flops / (ms / 1e3) / 1e12 / peak, "peak_source": src,

@@ -373,6 +373,28 @@ GCDF_API int gcdf_fit_value_grad(const gcdf_fit_desc *desc, const float *weights
 GCDF_API int gcdf_fit_vjp2(const gcdf_fit_desc *desc, const float *weights, const float *q, const float *p,
                            int batch, const float *g_f, const float *G_q, float *dweights, gcdf_stream_t stream);
 
+/* A training step that computes f and then its weight gradient can keep what
+ * the reverse sweep of gcdf_fit_vjp needs instead of recomputing the forward
+ * pass (BF16 precision only): the transposed BF16 images of the input
+ * encoding and of h_1 .. h_{L-1}, s'(z_1) .. s'(z_L) and h_L in FP32, in a
+ * caller-owned DEVICE buffer (the "tape").
+ * gcdf_fit_tape_bytes: *bytes = the tape size for `batch` samples (0 for
+ *   batch 0).  Errors: EINVAL (bad shape, FP32 precision, bytes NULL).
+ * gcdf_fit_forward_tape: gcdf_fit_forward that also fills the tape (tape 256-
+ *   byte aligned, at least gcdf_fit_tape_bytes long; EINVAL otherwise).
+ * gcdf_fit_vjp_tape: gcdf_fit_vjp from a tape filled by gcdf_fit_forward_tape
+ *   with the SAME desc, weights, q, p and batch (nothing checks that; another
+ *   tape gives the gradient of that other forward pass).  The tape is only
+ *   read.  Results equal gcdf_fit_vjp's bit for bit; the forward pass's
+ *   products are not repeated.  Temporaries: the delta images and the weight
+ *   images (about 4 batch x hidden BF16 values) and the partials array. */
+GCDF_API int gcdf_fit_tape_bytes(const gcdf_fit_desc *desc, int batch, size_t *bytes);
+GCDF_API int gcdf_fit_forward_tape(const gcdf_fit_desc *desc, const float *weights, const float *q, const float *p,
+                                   int batch, float *f, void *tape, size_t tape_bytes, gcdf_stream_t stream);
+GCDF_API int gcdf_fit_vjp_tape(const gcdf_fit_desc *desc, const float *weights, const float *q, const float *p,
+                               int batch, const float *g_f, const void *tape, size_t tape_bytes, float *dweights,
+                               float *dq, gcdf_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Trajectory optimisation with the GCDF collision cost (Sec. IV-A).
  *

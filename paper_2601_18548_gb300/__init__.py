@@ -407,6 +407,40 @@ def fit_vjp2(shape, weights, q, p, g_f, G_q, stream=None, precision="fp32"):
     return dw
 
 
+def fit_tape_bytes(shape, batch: int, precision="bf16") -> int:
+    """gcdf_fit_tape_bytes: device bytes of the tape of a BF16 forward pass."""
+    d = _fit_desc(shape, precision)
+    n = ctypes.c_size_t(0)
+    _lib.check(_lib.load().gcdf_fit_tape_bytes(ctypes.byref(d), int(batch), ctypes.byref(n)))
+    return int(n.value)
+
+
+def fit_forward_tape(shape, weights, q, p, stream=None, precision="bf16"):
+    """gcdf_fit_forward_tape: (f (B,), tape) — the tape (a uint8 CUDA tensor)
+    holds what fit_vjp_tape needs for the same weights, q and p."""
+    d = _fit_desc(shape, precision)
+    B = int(q.shape[0])
+    f = torch.empty(B, device=q.device, dtype=torch.float32)
+    tape = torch.empty(max(fit_tape_bytes(shape, B, precision), 1), device=q.device, dtype=torch.uint8)
+    _lib.check(_lib.load().gcdf_fit_forward_tape(ctypes.byref(d), _ptr(weights, name="weights"), _ptr(q, name="q"),
+                                                 _ptr(p, name="p"), B, _ptr(f, name="f"), _ptr(tape, torch.uint8, name="tape"),
+                                                 tape.numel(), _stream(stream)))
+    return f, tape
+
+
+def fit_vjp_tape(shape, weights, q, p, g_f, tape, want_dq=True, stream=None, precision="bf16"):
+    """gcdf_fit_vjp_tape: fit_vjp from the tape of fit_forward_tape (same
+    weights, q and p), without repeating the forward pass."""
+    d = _fit_desc(shape, precision)
+    dw = torch.empty_like(weights)
+    dq = torch.empty_like(q) if want_dq else None
+    _lib.check(_lib.load().gcdf_fit_vjp_tape(ctypes.byref(d), _ptr(weights, name="weights"), _ptr(q, name="q"),
+                                             _ptr(p, name="p"), int(q.shape[0]), _ptr(g_f.contiguous(), name="g_f"),
+                                             _ptr(tape, torch.uint8, name="tape"), tape.numel(), _ptr(dw, name="dweights"),
+                                             None if dq is None else _ptr(dq, name="dq"), _stream(stream)))
+    return dw, dq
+
+
 def fit_device_status() -> int:
     """gcdf_fit_device_status: synchronise; the fit kernels' status word since
     the last call (0 = every tensor-core wait completed), then clear it."""
@@ -417,19 +451,31 @@ def fit_device_status() -> int:
 
 class FieldFunction(torch.autograd.Function):
     """f(q_b, p_b; weights) as an autograd.Function: the forward and both
-    vector-Jacobian products (weights and q) run in libgcdf's kernels."""
+    vector-Jacobian products (weights and q) run in libgcdf's kernels.  With
+    BF16 products the forward keeps its tape for the backward (autograd's
+    version check on the saved weights and q guards against in-place changes
+    in between); with FP32 the backward recomputes the forward."""
 
     @staticmethod
     def forward(ctx, weights, q, p, shape, precision):
         ctx.save_for_backward(weights, q, p)
         ctx.shape, ctx.precision = shape, precision
+        if precision == "bf16":
+            f, ctx.tape = fit_forward_tape(shape, weights.detach(), q.detach(), p, precision=precision)
+            return f
+        ctx.tape = None
         return fit_forward(shape, weights.detach(), q.detach(), p, precision=precision)
 
     @staticmethod
     def backward(ctx, g_f):
         weights, q, p = ctx.saved_tensors
-        dw, dq = fit_vjp(ctx.shape, weights.detach(), q.detach(), p, g_f.detach().float(),
-                         want_dq=ctx.needs_input_grad[1], precision=ctx.precision)
+        if ctx.tape is not None:
+            dw, dq = fit_vjp_tape(ctx.shape, weights.detach(), q.detach(), p, g_f.detach().float(), ctx.tape,
+                                  want_dq=ctx.needs_input_grad[1], precision=ctx.precision)
+            ctx.tape = None
+        else:
+            dw, dq = fit_vjp(ctx.shape, weights.detach(), q.detach(), p, g_f.detach().float(),
+                             want_dq=ctx.needs_input_grad[1], precision=ctx.precision)
         return dw, dq, None, None, None
 
 

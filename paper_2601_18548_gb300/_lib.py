@@ -82,6 +82,10 @@ SIGNATURES = {
     "gcdf_fit_vjp": (_i, [ctypes.POINTER(FitDesc), _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp]),
     "gcdf_fit_value_grad": (_i, [ctypes.POINTER(FitDesc), _vp, _vp, _vp, _i, _vp, _vp, _vp]),
     "gcdf_fit_vjp2": (_i, [ctypes.POINTER(FitDesc), _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp]),
+    "gcdf_fit_tape_bytes": (_i, [ctypes.POINTER(FitDesc), _i, ctypes.POINTER(ctypes.c_size_t)]),
+    "gcdf_fit_forward_tape": (_i, [ctypes.POINTER(FitDesc), _vp, _vp, _vp, _i, _vp, _vp, ctypes.c_size_t, _vp]),
+    "gcdf_fit_vjp_tape": (_i, [ctypes.POINTER(FitDesc), _vp, _vp, _vp, _i, _vp, _vp, ctypes.c_size_t, _vp, _vp,
+                               _vp]),
     "gcdf_plan_solve": (_i, [_vp, ctypes.POINTER(PlanProblem), _i, ctypes.POINTER(PlanParams), _vp, _vp, _vp, _vp]),
     "gcdf_server_create": (_i, [ctypes.POINTER(ServerDesc), ctypes.POINTER(_vp)]),
     "gcdf_plan_submit": (_i, [_vp, ctypes.POINTER(PlanRequest), ctypes.POINTER(ctypes.c_uint64)]),

@@ -965,6 +965,64 @@ int vjp2_bf16(const Shape& sh, const float* w, const float* q, const float* p, i
 
 using namespace gcdf;
 
+
+// The tape of a BF16 forward pass: what the reverse sweep of gcdf_fit_vjp reads
+// (the transposed image of v and of h_1 .. h_{L-1}, s'(z_1) .. s'(z_L) and
+// h_L in FP32), each part 256-byte aligned.
+struct TapeLayout {
+  size_t xc, hc, ss, hl, total;
+};
+size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+TapeLayout tape_layout(const Shape& sh, int B) {
+  TapeLayout t{};
+  const size_t ldb = (size_t)pad8(B);
+  t.xc = up256((size_t)sh.d_in * ldb * sizeof(__nv_bfloat16));
+  t.hc = up256((size_t)sh.H * ldb * sizeof(__nv_bfloat16));
+  t.ss = up256((size_t)B * sh.H * sizeof(float));
+  t.hl = t.ss;
+  t.total = t.xc + (size_t)(sh.L - 1) * t.hc + (size_t)sh.L * t.ss + t.hl;
+  return t;
+}
+// Point the tape-held buffers of a BF16 pass into `tape`.
+void tape_carve(const Shape& sh, int B, void* tape, Bf16Fwd& bf, float** Ss, float** HL) {
+  const TapeLayout t = tape_layout(sh, B);
+  unsigned char* c = static_cast<unsigned char*>(tape);
+  bf.Xc = reinterpret_cast<__nv_bfloat16*>(c);
+  c += t.xc;
+  for (int l = 1; l < sh.L; ++l) {
+    bf.Hc[l] = reinterpret_cast<__nv_bfloat16*>(c);
+    c += t.hc;
+  }
+  for (int l = 1; l <= sh.L; ++l) {
+    Ss[l - 1] = reinterpret_cast<float*>(c);
+    c += t.ss;
+  }
+  *HL = reinterpret_cast<float*>(c);
+}
+// Buffers of a BF16 pass that are not on the tape: the row images (v, h_l)
+// and the weight images (fwd: W_l for the layer products; rev: W_l^T for the
+// back products).
+cudaError_t alloc_bf16_work(Ws& ws, const Shape& sh, int B, bool fwd, bool rev, Bf16Fwd& bf) {
+  cudaError_t e;
+  bf.ldx = pad8(sh.d_in);
+  bf.ldb = pad8(B);
+  if (fwd) {
+    if ((e = ws.get(&bf.Xr, (size_t)B * bf.ldx))) return e;
+    for (int l = 1; l < sh.L; ++l) {
+      if (l <= 2) {
+        if ((e = ws.get(&bf.Hr[l], (size_t)B * sh.H))) return e;
+      } else {
+        bf.Hr[l] = bf.Hr[l - 2];
+      }
+    }
+  }
+  for (int l = 1; l <= sh.L; ++l) {
+    if (fwd && (e = ws.get(&bf.Wr[l], (size_t)sh.H * pad8(sh.fan_in(l))))) return e;
+    if (rev && (e = ws.get(&bf.Wt[l], (size_t)sh.fan_in(l) * sh.H))) return e;
+  }
+  return cudaSuccess;
+}
+
 extern "C" {
 
 int gcdf_fit_device_status(int* status) {
@@ -1256,6 +1314,100 @@ int gcdf_fit_vjp2(const gcdf_fit_desc* desc, const float* weights, const float* 
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit vjp2 launch: %s", cudaGetErrorString(e));
+  clear_error();
+  return GCDF_OK;
+}
+
+
+int gcdf_fit_tape_bytes(const gcdf_fit_desc* desc, int batch, size_t* bytes) {
+  Shape sh;
+  if (!bytes) return set_error(GCDF_EINVAL, "bytes is NULL");
+  // shape checks only (no data pointer is read)
+  alignas(16) static const float none[4] = {0.f, 0.f, 0.f, 0.f};
+  int rc = check(desc, none, none, none, batch, sh);
+  if (rc) return rc;
+  if (!sh.bf16) return set_error(GCDF_EINVAL, "the tape is kept by the BF16 path only");
+  *bytes = batch > 0 ? tape_layout(sh, batch).total : 0;
+  clear_error();
+  return GCDF_OK;
+}
+
+int gcdf_fit_forward_tape(const gcdf_fit_desc* desc, const float* weights, const float* q, const float* p, int batch,
+                          float* f, void* tape, size_t tape_bytes, gcdf_stream_t stream) {
+  Shape sh;
+  int rc = check(desc, weights, q, p, batch, sh);
+  if (rc) return rc;
+  if (!sh.bf16) return set_error(GCDF_EINVAL, "the tape is kept by the BF16 path only");
+  if (batch == 0) { clear_error(); return GCDF_OK; }
+  if (!f || !al16(f)) return set_error(GCDF_EINVAL, "f NULL or not 16-byte aligned");
+  if (!tape || (reinterpret_cast<uintptr_t>(tape) & 255) != 0)
+    return set_error(GCDF_EINVAL, "tape NULL or not 256-byte aligned");
+  if (tape_bytes < tape_layout(sh, batch).total)
+    return set_error(GCDF_EINVAL, "tape of %zu bytes, %zu needed", tape_bytes, tape_layout(sh, batch).total);
+  cudaStream_t s = (cudaStream_t)stream;
+  Ws ws(s);
+  Bf16Fwd bf;
+  float* Ss[17];
+  float* HL = nullptr;
+  Ctx cx;
+  cudaError_t e;
+  tape_carve(sh, batch, tape, bf, Ss, &HL);
+  if ((e = alloc_bf16_work(ws, sh, batch, true, false, bf)))
+    return set_error(GCDF_ENOMEM, "temporaries: %s", cudaGetErrorString(e));
+  if ((rc = make_ctx_images(cx, s, nullptr, 0))) return rc;
+  if ((rc = forward_bf16(sh, weights, q, p, batch, bf, Ss, HL, f, cx))) return rc;
+  clear_error();
+  return GCDF_OK;
+}
+
+int gcdf_fit_vjp_tape(const gcdf_fit_desc* desc, const float* weights, const float* q, const float* p, int batch,
+                      const float* g_f, const void* tape, size_t tape_bytes, float* dweights, float* dq,
+                      gcdf_stream_t stream) {
+  Shape sh;
+  int rc = check(desc, weights, q, p, batch, sh);
+  if (rc) return rc;
+  if (!sh.bf16) return set_error(GCDF_EINVAL, "the tape is kept by the BF16 path only");
+  if (!dweights || !al16(dweights)) return set_error(GCDF_EINVAL, "dweights NULL or not 16-byte aligned");
+  if (dq && !al16(dq)) return set_error(GCDF_EINVAL, "dq not 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (batch == 0) {
+    if ((e = cudaMemsetAsync(dweights, 0, sh.total * sizeof(float), s)))
+      return set_error(GCDF_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    clear_error();
+    return GCDF_OK;
+  }
+  if (!g_f || !al16(g_f)) return set_error(GCDF_EINVAL, "g_f NULL or not 16-byte aligned");
+  if (!tape || (reinterpret_cast<uintptr_t>(tape) & 255) != 0)
+    return set_error(GCDF_EINVAL, "tape NULL or not 256-byte aligned");
+  if (tape_bytes < tape_layout(sh, batch).total)
+    return set_error(GCDF_EINVAL, "tape of %zu bytes, %zu needed", tape_bytes, tape_layout(sh, batch).total);
+  Ws ws(s);
+  Bf16Fwd bf;
+  float* Ss[17];
+  float *HL = nullptr, *dv = nullptr, *partials = nullptr;
+  const size_t pfl = (size_t)64 * sh.H * (sh.H > sh.d_in ? sh.H : sh.d_in);
+  Ctx cx;
+  tape_carve(sh, batch, const_cast<void*>(tape), bf, Ss, &HL);
+  if ((e = alloc_bf16_work(ws, sh, batch, false, true, bf)) || (e = ws.get(&partials, pfl)) ||
+      (dq && (e = ws.get(&dv, (size_t)batch * sh.d_in))))
+    return set_error(GCDF_ENOMEM, "temporaries: %s", cudaGetErrorString(e));
+  if ((rc = make_ctx_images(cx, s, partials, pfl))) return rc;
+  // the transposed weight images of the back products (the tape holds the
+  // activations, not the weights)
+  for (int l = 1; l <= sh.L; ++l) {
+    const int K = sh.fan_in(l);
+    if ((e = cx.image(weights + sh.off(l), 1, K, K, sh.H, bf.Wt[l], sh.H)))
+      return set_error(GCDF_ECUDA, "weight image: %s", cudaGetErrorString(e));
+  }
+  float* dwo = dweights + sh.off_out;
+  if ((e = colsum(HL, batch, sh.H, g_f, dwo, partials, pfl, s)) ||
+      (e = colsum(g_f, batch, 1, nullptr, dwo + sh.H, partials, pfl, s)))
+    return set_error(GCDF_ECUDA, "colsum: %s", cudaGetErrorString(e));
+  if ((rc = reverse_bf16(sh, batch, bf, Ss, g_f, weights + sh.off_out, true, dweights, dv, ws, cx))) return rc;
+  if (dq) dq_kernel<<<grid1(batch), 256, 0, s>>>(q, dv, batch, sh.n, sh.d_in, dq);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(GCDF_ECUDA, "fit backward launch: %s", cudaGetErrorString(e));
   clear_error();
   return GCDF_OK;
 }

@@ -66,6 +66,24 @@ def test_fit_argument_errors_without_gpu():
     assert lib.gcdf_fit_device_status(None) == g._lib.GCDF_EINVAL
     with pytest.raises(ValueError):
         g._fit_desc((9, 256, 4), "fp16")
+    # the tape: BF16 only, a size output, an aligned and large enough buffer
+    n = ctypes.c_size_t(0)
+    fp32 = g._lib.FitDesc(9, 256, 4, g._lib.GCDF_FP32)
+    assert lib.gcdf_fit_tape_bytes(ctypes.byref(fp32), 1000, ctypes.byref(n)) == g._lib.GCDF_EINVAL
+    assert lib.gcdf_fit_tape_bytes(ctypes.byref(d), 1000, None) == g._lib.GCDF_EINVAL
+    assert lib.gcdf_fit_tape_bytes(ctypes.byref(d), 1000, ctypes.byref(n)) == g._lib.GCDF_OK
+    # transposed images of v (d_in = 19 rows) and h_1..h_3 (row length: the batch padded to a
+    # multiple of 8), s' of 4 layers and h_L, each part rounded up to 256 bytes
+    expect = sum(((b + 255) // 256) * 256 for b in [19 * 1000 * 2] + [256 * 1000 * 2] * 3 + [1000 * 256 * 4] * 5)
+    assert n.value == expect
+    assert lib.gcdf_fit_tape_bytes(ctypes.byref(d), 0, ctypes.byref(n)) == g._lib.GCDF_OK and n.value == 0
+    fake = ctypes.c_void_p(1 << 20)  # aligned, never dereferenced
+    rc = lib.gcdf_fit_forward_tape(ctypes.byref(d), fake, fake, fake, 1000, fake, None, 1 << 30, None)
+    assert rc == g._lib.GCDF_EINVAL and "tape" in g.last_error()
+    rc = lib.gcdf_fit_forward_tape(ctypes.byref(d), fake, fake, fake, 1000, fake, fake, 100, None)
+    assert rc == g._lib.GCDF_EINVAL and "needed" in g.last_error()
+    rc = lib.gcdf_fit_vjp_tape(ctypes.byref(fp32), fake, fake, fake, 1000, fake, fake, 1 << 30, fake, None, None)
+    assert rc == g._lib.GCDF_EINVAL
 
 
 def test_host_side_argument_checks_without_gpu():

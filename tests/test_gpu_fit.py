@@ -254,6 +254,34 @@ def test_bf16_is_deterministic_and_reduces_to_the_first_order_vjp():
     assert g.fit_device_status() == 0
 
 
+@pytest.mark.parametrize("n,H,L,B", [(10, 512, 5, 8192), (3, 96, 2, 333), (12, 64, 1, 5000)])
+def test_bf16_tape_gives_the_vjp_bit_for_bit(n, H, L, B):
+    """gcdf_fit_forward_tape / gcdf_fit_vjp_tape: the same f as gcdf_fit_forward
+    and the same weight and configuration gradients as gcdf_fit_vjp, to the
+    bit, without repeating the forward; a second backward from the same tape
+    gives the same again (the tape is only read).  The autograd Function uses
+    the tape with BF16 products."""
+    torch = need_gpu()
+    g = lib()
+    _, w = small_net(n, hidden=H, n_layers=L)
+    q, p = _batch(n, B, 23)
+    wd, qd, pd = to_dev(torch, np.asarray(w, np.float32)), to_dev(torch, q), to_dev(torch, p)
+    gf = to_dev(torch, np.random.default_rng(5).normal(size=B).astype(np.float32))
+    f, tape = g.fit_forward_tape((n, H, L), wd, qd, pd, precision="bf16")
+    assert tape.numel() == g.fit_tape_bytes((n, H, L), B)
+    assert torch.equal(f, g.fit_forward((n, H, L), wd, qd, pd, precision="bf16"))
+    a = g.fit_vjp((n, H, L), wd, qd, pd, gf, precision="bf16")
+    for _ in range(2):
+        b = g.fit_vjp_tape((n, H, L), wd, qd, pd, gf, tape, precision="bf16")
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    wr = wd.clone().requires_grad_(True)
+    qr = qd.clone().requires_grad_(True)
+    fa = g.field(wr, qr, pd, (n, H, L), precision="bf16")
+    (fa * gf).sum().backward()
+    assert torch.equal(fa.detach(), f) and torch.equal(wr.grad, a[0]) and torch.equal(qr.grad, a[1])
+    assert g.fit_device_status() == 0
+
+
 def test_bf16_full_batch_samples_match_the_oracle():
     """The training-step size (10-DOF 5 x 512, batch 65,536): f and grad_q f of
     sampled rows against the oracle, the weight gradient against the FP32 path."""
