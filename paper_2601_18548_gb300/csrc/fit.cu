@@ -586,6 +586,53 @@ __global__ void encode_bf16_kernel(const float* __restrict__ q, const float* __r
 // delta_L = g w_o * s'(z_L) (g NULL: 1) straight into its BF16 images: row-major
 // Dr (B x H) and transposed Dc (H x ldc, NULL: not written), with the column
 // sums of every 32-row block in cs (NULL: none).  Block (32, 8) per 32 x 32 tile.
+// seed_images_kernel over 32 x 128 blocks: lane tx handles columns c0 + tx + 32 k
+// (k = 0..3) of rows ty, ty + 8, .. (four coalesced loads and stores per row
+// and warp instruction), 16 elements per thread; the same arithmetic and the
+// same column-sum order as seed_images_kernel.
+__global__ void seed_images_wide_kernel(const float* __restrict__ g, const float* __restrict__ wo,
+                                        const float* __restrict__ S, int B, int H, __nv_bfloat16* __restrict__ Dr,
+                                        __nv_bfloat16* __restrict__ Dc, long long ldc, float* __restrict__ cs) {
+  __shared__ float t[32][129];
+  const long long r0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 128;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float wk[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) wk[k] = c0 + tx + 32 * k < H ? wo[c0 + tx + 32 * k] : 0.f;
+  for (int i = ty; i < 32; i += 8) {
+    const long long r = r0 + i;
+    const float gr = (r < B && g) ? g[r] : 1.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = c0 + tx + 32 * k;
+      float d = 0.f;
+      if (r < B && c < H) {
+        d = gr * wk[k] * S[r * H + c];
+        Dr[r * H + c] = __float2bfloat16_rn(d);
+      }
+      t[i][tx + 32 * k] = d;
+    }
+  }
+  __syncthreads();
+  if (cs && ty < 4) {
+    const int col = ty * 32 + tx, c = c0 + col;
+    if (c < H) {
+      float sum = 0.f;
+      for (int i = 0; i < 32; ++i)
+        if (r0 + i < B) sum += t[i][col];
+      cs[(long long)blockIdx.x * H + c] = sum;
+    }
+  }
+  if (Dc) {
+    const long long r = r0 + tx;
+    for (int cc = ty; cc < 128; cc += 8) {
+      const int c = c0 + cc;
+      if (c < H && r < B) Dc[(long long)c * ldc + r] = __float2bfloat16_rn(t[tx][cc]);
+    }
+  }
+}
+
 __global__ void seed_images_kernel(const float* __restrict__ g, const float* __restrict__ wo,
                                    const float* __restrict__ S, int B, int H, __nv_bfloat16* __restrict__ Dr,
                                    __nv_bfloat16* __restrict__ Dc, long long ldc, float* __restrict__ cs) {
@@ -812,9 +859,10 @@ int reverse_bf16(const Shape& sh, int B, Bf16Fwd& bf, float** Ss, const float* g
   if (with_grads && (e = ws.get(&cs, (size_t)nblk * H))) return set_error(GCDF_ENOMEM, "cudaMallocAsync");
   // delta_L straight into its images and column sums
   {
-    dim3 grid((unsigned)nblk, (unsigned)((H + 31) / 32));
-    seed_images_kernel<<<grid, dim3(32, 8), 0, s>>>(g, wo, Ss[sh.L - 1], B, H, Dr[0], with_grads ? Dc[0] : nullptr,
-                                                    bf.ldb, with_grads ? cs : nullptr);
+    dim3 grid((unsigned)nblk, (unsigned)((H + 127) / 128));
+    seed_images_wide_kernel<<<grid, dim3(32, 8), 0, s>>>(g, wo, Ss[sh.L - 1], B, H, Dr[0],
+                                                         with_grads ? Dc[0] : nullptr, bf.ldb,
+                                                         with_grads ? cs : nullptr);
   }
   int cur = 0;
   for (int l = sh.L; l >= 1; --l) {
