@@ -144,6 +144,19 @@ __global__ void colsum_kernel(const float* __restrict__ X, int rows, int C, cons
   partial[(long long)blockIdx.y * C + c] = s;
 }
 
+// out[c] (= or +=) the sum of partial[k, c] over the chunks k, one warp per
+// column: lane-strided sums, then a fixed butterfly (deterministic).
+__global__ void colsum_finish_kernel(const float* __restrict__ partial, int chunks, int C, float* __restrict__ out,
+                                     int accumulate) {
+  const int c = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= C) return;
+  float s = 0.f;
+  for (int k = lane; k < chunks; k += 32) s += partial[(long long)k * C + c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[c] = accumulate ? out[c] + s : s;
+}
+
 // f_b = X[b, :] . v + *c0, one warp per row (lane-strided sums, fixed butterfly).
 __global__ void rowdot_kernel(const float* __restrict__ X, int rows, int C, const float* __restrict__ v,
                               const float* __restrict__ c0, float* __restrict__ f) {
@@ -325,11 +338,15 @@ cudaError_t gemm(const float* A, long long sam, long long sak, const float* B, l
 // out (C) = X^T w over the batch (w NULL: column sums), in a fixed order.
 cudaError_t colsum(const float* X, int rows, int C, const float* w, float* out, float* partials, size_t pfl,
                    cudaStream_t s, bool accumulate = false) {
-  int chunks = 64;
+  // enough row chunks that no thread walks more than ~128 rows (up to 1,024
+  // chunks and the partials array), then one warp per column over the chunks
+  int chunks = (rows + 127) / 128;
+  if (chunks > 1024) chunks = 1024;
+  if (chunks < 1) chunks = 1;
   while (chunks > 1 && (size_t)chunks * C > pfl) --chunks;
   dim3 grid((C + 255) / 256, chunks);
   colsum_kernel<<<grid, 256, 0, s>>>(X, rows, C, w, chunks, partials);
-  sum_partials_kernel<<<partials_grid(1, C), 256, 0, s>>>(partials, chunks, 1, C, C, out, C, accumulate ? 1 : 0);
+  colsum_finish_kernel<<<(unsigned)((C + 7) / 8), 256, 0, s>>>(partials, chunks, C, out, accumulate ? 1 : 0);
   return cudaGetLastError();
 }
 
