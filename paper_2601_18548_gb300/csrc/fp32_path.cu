@@ -19,7 +19,8 @@
 // Activations live in shared memory feature-major, act[c][pair] (row stride
 // TP + 4 floats); weight rows stream through a double-buffered shared chunk of
 // KC rows with cp.async.  The weight images are pre-permuted on the host so a
-// thread's 8 features are 8 consecutive floats of a row (two 16-byte loads).
+// thread's 8 features are two 16-byte pieces of a row, at 4 fg and H / 2 + 4 fg:
+// the 8 feature groups of a warp read each half as 128 contiguous bytes.
 // s'(z_l) of layers 2..L-1 stays in shared memory for the reverse sweep;
 // s'(z_1) is recomputed from A_i + W_1p p_j, which costs three FMAs.
 #include "gcdf_internal.cuh"
@@ -189,13 +190,13 @@ fp32_fused_kernel(const WorkDesc w, const Fp32Weights fw) {
           const bool more = (cnext != 0) || (t + (int)gridDim.x < w.n_tiles);
           if (more) load_chunk<H, KC>(wbuf + ((gchunk + 1) & 1) * KC * H, chunk_src<H, KC>(fw, cnext));
         }
-        const float* wb = wbuf + (gchunk & 1) * KC * H + 8 * fg;
+        const float* wb = wbuf + (gchunk & 1) * KC * H + 4 * fg;  // features f < 4; f >= 4 at + H / 2
         const float* ab = act + (size_t)(part * KC) * C::AS + 4 * pg;
 #pragma unroll 8
         for (int kk = 0; kk < KC; ++kk) {
           const float4 a = *reinterpret_cast<const float4*>(ab + (size_t)kk * C::AS);
           const float4 w0 = *reinterpret_cast<const float4*>(wb + (size_t)kk * H);
-          const float4 w1 = *reinterpret_cast<const float4*>(wb + (size_t)kk * H + 4);
+          const float4 w1 = *reinterpret_cast<const float4*>(wb + (size_t)kk * H + H / 2);
           const float av[4] = {a.x, a.y, a.z, a.w};
           const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll

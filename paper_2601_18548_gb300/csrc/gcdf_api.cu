@@ -88,10 +88,19 @@ int dev_alloc_copy(T** dst, const T* src, size_t count) {
   return GCDF_OK;
 }
 
-// Column permutation of the FP32 path: feature c = fg + G f  ->  column 8 fg + f.
+// Column permutation of the FP32 path's biases and w_o: feature c = fg + G f
+// -> column 8 fg + f (a thread's 8 features are 8 consecutive floats).
 inline int perm_col(int c, int H) {
   const int G = H / 8;
   return (c % G) * 8 + c / G;
+}
+// Column permutation of its weight images: feature c = fg + G f -> column
+// 4 fg + f (f < 4) or H / 2 + 4 fg + f - 4, so that the 8 feature groups of a
+// warp read their first and their second four features of a row as two
+// contiguous 128-byte pieces.
+inline int perm_wcol(int c, int H) {
+  const int G = H / 8, fg = c % G, f = c / G;
+  return f < 4 ? 4 * fg + f : H / 2 + 4 * fg + f - 4;
 }
 
 int build_fp32_images(gcdf_net* net, const float* w) {
@@ -105,8 +114,8 @@ int build_fp32_images(gcdf_net* net, const float* w) {
     for (int o = 0; o < H; ++o) {
       for (int i = 0; i < H; ++i) {
         const float v = W[(size_t)o * H + i];
-        BF[(size_t)l * H * H + (size_t)i * H + perm_col(o, H)] = v;  // row = input, col = output
-        BB[(size_t)l * H * H + (size_t)o * H + perm_col(i, H)] = v;  // row = output, col = input
+        BF[(size_t)l * H * H + (size_t)i * H + perm_wcol(o, H)] = v;  // row = input, col = output
+        BB[(size_t)l * H * H + (size_t)o * H + perm_wcol(i, H)] = v;  // row = output, col = input
       }
       bias[(size_t)l * H + perm_col(o, H)] = b[o];
     }
