@@ -187,6 +187,31 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
     // rows of the CTA's 128) and columns [64 ch, 64 ch + 64) of the tile, ch = (w - 2) / 4
     const int q = warp & 3;
     const int ch = (warp - 2) >> 2;
+    // the biases of the warp's two 32-column blocks, one per lane, fetched
+    // while the main loop runs (handed to every lane by shuffles later)
+    float bias_b0 = 0.f, bias_b1 = 0.f;
+    if (a.ep.mode == kEpiBiasSilu) {
+      const int nb0 = tn * kTileN + 64 * ch;
+      if (nb0 < a.N) bias_b0 = __ldg(a.ep.bias + min(nb0 + lane, a.N - 1));
+      if (nb0 + 32 < a.N) bias_b1 = __ldg(a.ep.bias + min(nb0 + 32 + lane, a.N - 1));
+    }
+    // the factor (and added) rows of the warp's 32 rows x 64 columns pulled into
+    // L2 while the main loop runs: one 128-byte line per row and block
+    if (a.ep.mode == kEpiMul) {
+      const int nb0 = tn * kTileN + 64 * ch;
+      const int rr = tm * 2 * kRowsA + (int)rank * kRowsA + q * 32 + lane;
+      if (rr < a.M) {
+#pragma unroll
+        for (int bk = 0; bk < 2; ++bk) {
+          const int n = nb0 + 32 * bk;
+          if (n < a.N) {
+            const long long o = (long long)rr * a.ep.ld_s + n;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.ep.s_in + o));
+            if (a.ep.add_in) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.ep.add_in + o));
+          }
+        }
+      }
+    }
     bool ok = true;
     {
       const long long t0 = clock64();
@@ -231,8 +256,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
         const int nb = n0 + c0;  // first column of the block
         if (nb >= a.N) break;
         const bool vb = vec && nb + 32 <= a.N;
-        // the block's 32 biases, one per lane, handed to every lane by shuffles
-        const float bias_l = silu ? __ldg(ep.bias + min(nb + lane, a.N - 1)) : 0.f;
+        const float bias_l = c0 == 64 * ch ? bias_b0 : bias_b1;
         if (mul) {
           // the factor block (and the added block) come in along rows
           if (vb) {

@@ -105,9 +105,9 @@ fp32_fused_kernel(const WorkDesc w, const Fp32Weights fw) {
   float* pts = smem + lay.pts;
 
   const int tid = threadIdx.x;
-  // A warp covers 4 pair groups x 8 feature groups, so its weight reads touch
-  // 8 distinct 32-byte rows (broadcast to the 4 pair groups) and its
-  // activation reads 4 distinct 16-byte rows.
+  // A warp covers 4 pair groups x 8 feature groups, so each of its two weight
+  // reads per K step covers 128 contiguous bytes (broadcast to the 4 pair
+  // groups) and its activation read 4 distinct 16-byte pieces.
   const int warp = tid >> 5, lane = tid & 31;
   const int pg = (warp / (C::G / 8)) * 4 + (lane >> 3);
   const int fg = (warp % (C::G / 8)) * 8 + (lane & 7);
