@@ -120,6 +120,7 @@ __global__ void sum_partials_kernel(const float* __restrict__ P, int splits, int
   for (int m = blockIdx.y; m < M; m += gridDim.y)
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
       float s = 0.f;
+#pragma unroll 8
       for (int z = 0; z < splits; ++z) s += P[((long long)z * M + m) * ldp + n];
       C[(long long)m * ldc + n] = accumulate ? C[(long long)m * ldc + n] + s : s;
     }
@@ -140,6 +141,7 @@ __global__ void colsum_kernel(const float* __restrict__ X, int rows, int C, cons
   const int per = (rows + chunks - 1) / chunks;
   const int r0 = blockIdx.y * per, r1 = min(rows, r0 + per);
   float s = 0.f;
+#pragma unroll 8
   for (int b = r0; b < r1; ++b) s = fmaf(X[(long long)b * C + c], w ? w[b] : 1.f, s);
   partial[(long long)blockIdx.y * C + c] = s;
 }
@@ -338,9 +340,9 @@ cudaError_t gemm(const float* A, long long sam, long long sak, const float* B, l
 // out (C) = X^T w over the batch (w NULL: column sums), in a fixed order.
 cudaError_t colsum(const float* X, int rows, int C, const float* w, float* out, float* partials, size_t pfl,
                    cudaStream_t s, bool accumulate = false) {
-  // enough row chunks that no thread walks more than ~128 rows (up to 1,024
+  // enough row chunks that no thread walks more than ~32 rows (up to 1,024
   // chunks and the partials array), then one warp per column over the chunks
-  int chunks = (rows + 127) / 128;
+  int chunks = (rows + 31) / 32;
   if (chunks > 1024) chunks = 1024;
   if (chunks < 1) chunks = 1;
   while (chunks > 1 && (size_t)chunks * C > pfl) --chunks;
