@@ -382,6 +382,71 @@ __global__ void transpose_bf16_kernel(const float* __restrict__ X, long long row
 
 long long pad8(long long x) { return (x + 7) / 8 * 8; }
 
+// The BF16 weight images of every layer in one launch: W_l (H x K_l, row stride
+// K_l) rounded row by row into Wr[l] (row stride pad8(K_l)) and transposed into
+// Wt[l] (K_l x H), either absent per layer.  32 x 32 tiles of all layers in one
+// grid (tile0: the first tile of each layer), block 32 x 8.
+struct WeightImages {
+  const float* W[16];
+  __nv_bfloat16* Wr[16];
+  __nv_bfloat16* Wt[16];
+  int K[16];
+  int tile0[17];
+  int H, L;
+};
+
+__global__ void weight_images_kernel(const WeightImages a) {
+  __shared__ float t[32][33];
+  int l = 0;
+  while (l + 1 < a.L && (int)blockIdx.x >= a.tile0[l + 1]) ++l;
+  const int K = a.K[l], H = a.H;
+  const int tile = (int)blockIdx.x - a.tile0[l];
+  const int tcols = (K + 31) / 32;
+  const int r0 = (tile / tcols) * 32, c0 = (tile % tcols) * 32;  // rows over H, columns over K
+  const float* W = a.W[l];
+  __nv_bfloat16* Wr = a.Wr[l];
+  const long long ldr = (K + 7) / 8 * 8;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    const bool in = r < H && c < K;
+    const float v = in ? W[(long long)r * K + c] : 0.f;
+    t[i][threadIdx.x] = v;
+    if (in && Wr) Wr[(long long)r * ldr + c] = __float2bfloat16_rn(v);
+  }
+  __nv_bfloat16* Wt = a.Wt[l];
+  if (Wt) {  // the same for the whole block
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+      const int c = c0 + i, r = r0 + threadIdx.x;
+      if (c < K && r < H) Wt[(long long)c * H + r] = __float2bfloat16_rn(t[threadIdx.x][i]);
+    }
+  }
+}
+
+// One launch of weight_images_kernel for layers 1..L of the flat weights w
+// (layer l at w_off[l], fan-in K[l]); Wr / Wt indexed by layer, entries may be
+// NULL (the arrays themselves too).
+cudaError_t weight_images(const float* w, const long long* w_off, const int* K, int L, int H,
+                          __nv_bfloat16* const* Wr, __nv_bfloat16* const* Wt, cudaStream_t s) {
+  if (L < 1 || L > 16) return cudaErrorInvalidValue;
+  WeightImages a{};
+  a.H = H;
+  a.L = L;
+  int tiles = 0;
+  for (int l = 1; l <= L; ++l) {
+    a.W[l - 1] = w + w_off[l];
+    a.Wr[l - 1] = Wr ? Wr[l] : nullptr;
+    a.Wt[l - 1] = Wt ? Wt[l] : nullptr;
+    a.K[l - 1] = K[l];
+    a.tile0[l - 1] = tiles;
+    tiles += ((H + 31) / 32) * ((K[l] + 31) / 32);
+  }
+  a.tile0[L] = tiles;
+  if (tiles == 0) return cudaSuccess;
+  weight_images_kernel<<<tiles, dim3(32, 8), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 // The products of one call: FP32 SIMT GEMMs, or the BF16 tensor-core GEMM on
 // K-major BF16 images of both operands (an operand whose K index is already the
 // contiguous one is rounded row by row, the other one is transposed).
@@ -827,13 +892,19 @@ int forward_bf16(const Shape& sh, const float* w, const float* q, const float* p
   const cudaStream_t s = cx.s;
   cudaError_t e;
   encode_bf16_kernel<<<grid1(B), 256, 0, s>>>(q, p, B, sh.n, sh.d_in, bf.Xr, bf.ldx, bf.Xc, bf.ldb);
+  {
+    long long offs[17];
+    int fan[17];
+    for (int l = 1; l <= sh.L; ++l) {
+      offs[l] = (long long)sh.off(l);
+      fan[l] = sh.fan_in(l);
+    }
+    if ((e = weight_images(w, offs, fan, sh.L, sh.H, bf.Wr, bf.Wt, s)))
+      return set_error(GCDF_ECUDA, "weight images: %s", cudaGetErrorString(e));
+  }
   for (int l = 1; l <= sh.L; ++l) {
     const int K = sh.fan_in(l);
     const float* W = w + sh.off(l);
-    if ((e = cx.image(W, K, 1, sh.H, K, bf.Wr[l], pad8(K))))
-      return set_error(GCDF_ECUDA, "weight image: %s", cudaGetErrorString(e));
-    if (bf.Wt[l] && (e = cx.image(W, 1, K, K, sh.H, bf.Wt[l], sh.H)))
-      return set_error(GCDF_ECUDA, "weight image: %s", cudaGetErrorString(e));
     GemmEpilogue ep{};
     ep.mode = kEpiBiasSilu;
     ep.bias = W + (size_t)sh.H * K;
@@ -1462,10 +1533,15 @@ int gcdf_fit_vjp_tape(const gcdf_fit_desc* desc, const float* weights, const flo
   if ((rc = make_ctx_images(cx, s, partials, pfl))) return rc;
   // the transposed weight images of the back products (the tape holds the
   // activations, not the weights)
-  for (int l = 1; l <= sh.L; ++l) {
-    const int K = sh.fan_in(l);
-    if ((e = cx.image(weights + sh.off(l), 1, K, K, sh.H, bf.Wt[l], sh.H)))
-      return set_error(GCDF_ECUDA, "weight image: %s", cudaGetErrorString(e));
+  {
+    long long offs[17];
+    int fan[17];
+    for (int l = 1; l <= sh.L; ++l) {
+      offs[l] = (long long)sh.off(l);
+      fan[l] = sh.fan_in(l);
+    }
+    if ((e = weight_images(weights, offs, fan, sh.L, sh.H, nullptr, bf.Wt, s)))
+      return set_error(GCDF_ECUDA, "weight images: %s", cudaGetErrorString(e));
   }
   float* dwo = dweights + sh.off_out;
   if ((e = colsum(HL, batch, sh.H, g_f, dwo, partials, pfl, s)) ||
