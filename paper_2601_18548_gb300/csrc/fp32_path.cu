@@ -15,12 +15,12 @@
 //
 // Layout.  A tile is TP = 8192 / H pairs of one waypoint.  256 threads; thread
 // (pg, fg) owns pairs 4pg..4pg+3 and features fg + G f (f = 0..7, G = H / 8);
-// a warp spans 4 pair groups and 8 feature groups.
+// a warp spans 2 pair groups and 16 feature groups (4 and 8 for H = 64).
 // Activations live in shared memory feature-major, act[c][pair] (row stride
 // TP + 4 floats); weight rows stream through a double-buffered shared chunk of
 // KC rows with cp.async.  The weight images are pre-permuted on the host so a
 // thread's 8 features are two 16-byte pieces of a row, at 4 fg and H / 2 + 4 fg:
-// the 8 feature groups of a warp read each half as 128 contiguous bytes.
+// the feature groups of a warp read each half as one contiguous piece.
 // s'(z_l) of layers 2..L-1 stays in shared memory for the reverse sweep;
 // s'(z_1) is recomputed from A_i + W_1p p_j, which costs three FMAs.
 #include "gcdf_internal.cuh"
@@ -105,15 +105,19 @@ fp32_fused_kernel(const WorkDesc w, const Fp32Weights fw) {
   float* pts = smem + lay.pts;
 
   const int tid = threadIdx.x;
-  // A warp covers 4 pair groups x 8 feature groups, so each of its two weight
-  // reads per K step covers 128 contiguous bytes (broadcast to the 4 pair
-  // groups) and its activation read 4 distinct 16-byte pieces.  Lanes run over
-  // the pair groups first (lane = 4 fg + pg within the warp): each 8-lane
-  // phase of a 16-byte shared load then holds 2 weight and 4 activation
-  // pieces, which measured 2.6 % faster than one pair group per phase.
+  // A warp covers WP pair groups x WF feature groups (2 x 16 where the tile
+  // allows it, else 4 x 8), lanes running over the pair groups first
+  // (lane = WP fg + pg within the warp): each of its two weight reads per K
+  // step covers WF x 16 contiguous bytes, each read by WP lanes, and its
+  // activation read WP distinct 16-byte pieces.  Against 4 x 8 with one pair
+  // group per 8-lane phase this measured 1.1 % (2 x 16) and 2.6 % (4 x 8,
+  // pair groups first) faster, the fully unrolled K chunk 3.4 % on top.
   const int warp = tid >> 5, lane = tid & 31;
-  const int pg = (warp / (C::G / 8)) * 4 + (lane & 3);
-  const int fg = (warp % (C::G / 8)) * 8 + (lane >> 2);
+  constexpr int WF = C::G % 16 == 0 && C::PG % 2 == 0 ? 16 : 8;  // feature groups per warp
+  constexpr int WP = 32 / WF;                                     // pair groups per warp
+  static_assert(C::PG % WP == 0 && C::G % WF == 0, "warp tiling");
+  const int pg = (warp / (C::G / WF)) * WP + (lane % WP);
+  const int fg = (warp % (C::G / WF)) * WF + (lane / WP);
   const int L = fw.L;
   // value-only query (no gradient output): the forward layers alone
   const bool fwd_only = (w.mode == kQuery && w.g_out == nullptr);
@@ -195,7 +199,7 @@ fp32_fused_kernel(const WorkDesc w, const Fp32Weights fw) {
         }
         const float* wb = wbuf + (gchunk & 1) * KC * H + 4 * fg;  // features f < 4; f >= 4 at + H / 2
         const float* ab = act + (size_t)(part * KC) * C::AS + 4 * pg;
-#pragma unroll 8
+#pragma unroll
         for (int kk = 0; kk < KC; ++kk) {
           const float4 a = *reinterpret_cast<const float4*>(ab + (size_t)kk * C::AS);
           const float4 w0 = *reinterpret_cast<const float4*>(wb + (size_t)kk * H);
