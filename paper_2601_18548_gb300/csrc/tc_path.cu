@@ -862,7 +862,10 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
           const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + s * (kH / 2) + (c0 >> 1));
           // 32 columns per TMEM load (one instruction, one wait), arithmetic in
           // 16-column chunks
-#pragma unroll 1
+          // both 32-column halves in one trip for BF16 operands (0.6 % faster;
+          // with the first layer unrolled as well it was 0.6 % slower)
+          constexpr int kMidUnroll = kFmt == 0 ? 2 : 1;
+#pragma unroll kMidUnroll
           for (int cp = 0; cp < 64; cp += 32) {
             uint32_t vab[32];
             ptx::tmem_ld32(t_acc + cp, vab);
@@ -898,7 +901,9 @@ tc_fused_kernel(const WorkDesc w, const __grid_constant__ CUtensorMap map_w,
           fpart = 0.f;
           const float sc8 = kF8 ? tw.fp8_scale[L - 2] : 1.f;
           const uint4* bh4 = reinterpret_cast<const uint4*>(s_biasH + (L - 2) * (kH / 2) + (c0 >> 1));
-#pragma unroll 1
+          // two chunks per trip for BF16 operands (0.4 % faster; FP16 0.6 % slower)
+          constexpr int kLastUnroll = kFmt == 0 ? 2 : 1;
+#pragma unroll kLastUnroll
           for (int cc = 0; cc < 64; cc += 16) {
             uint32_t v[16];
             ptx::tmem_ld16(t_acc + cc, v);
