@@ -49,12 +49,16 @@ constexpr int kBM = 128, kBN = 128, kBK = 8, kGemmThreads = 256;
 // C[m, n] (row-major, ldc) = sum_k A(m, k) B(k, n) over k in this block's
 // chunk [z kc, min(K, (z + 1) kc)); with z > 0 chunks the block writes its
 // partial tile to C + z M ldc.
-__global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const float* __restrict__ A, long long sam, long long sak,
+__global__ void __launch_bounds__(kGemmThreads, 2) gemm_kernel(const float* __restrict__ A, long long sam, long long sak,
                                                             const float* __restrict__ B, long long sbk,
                                                             long long sbn, float* __restrict__ C, int ldc, int M,
                                                             int N, int K, int kc, int accumulate) {
-  __shared__ __align__(16) float As[kBK][kBM];
-  __shared__ __align__(16) float Bs[kBK][kBN];
+  // two shared buffers: the next K block's elements are fetched into registers
+  // before this block's products and stored to the other buffer after them,
+  // so one barrier per K block separates the two (same summation order as a
+  // single buffer)
+  __shared__ __align__(16) float As[2][kBK][kBM];
+  __shared__ __align__(16) float Bs[2][kBK][kBN];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
   const int k_lo = blockIdx.z * kc, k_hi = min(K, k_lo + kc);
@@ -64,30 +68,53 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const float* __restr
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
   const bool a_kfast = (sak == 1), b_nfast = (sbn == 1);
-  for (int k0 = k_lo; k0 < k_hi; k0 += kBK) {
+  constexpr int kRA = (kBK * kBM) / kGemmThreads, kRB = (kBK * kBN) / kGemmThreads;
+  float ra[kRA], rb[kRB];
+  auto fetch = [&](int k0) {
 #pragma unroll
-    for (int r = 0; r < (kBK * kBM) / kGemmThreads; ++r) {
+    for (int r = 0; r < kRA; ++r) {
       const int e = threadIdx.x + r * kGemmThreads;
       const int mm = a_kfast ? e / kBK : e % kBM;
       const int kk = a_kfast ? e % kBK : e / kBM;
       const int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < M && k < k_hi) ? A[(long long)m * sam + (long long)k * sak] : 0.f;
+      ra[r] = (m < M && k < k_hi) ? A[(long long)m * sam + (long long)k * sak] : 0.f;
     }
 #pragma unroll
-    for (int r = 0; r < (kBK * kBN) / kGemmThreads; ++r) {
+    for (int r = 0; r < kRB; ++r) {
       const int e = threadIdx.x + r * kGemmThreads;
       const int nn = b_nfast ? e % kBN : e / kBK;
       const int kk = b_nfast ? e / kBN : e % kBK;
       const int n = n0 + nn, k = k0 + kk;
-      Bs[kk][nn] = (n < N && k < k_hi) ? B[(long long)k * sbk + (long long)n * sbn] : 0.f;
+      rb[r] = (n < N && k < k_hi) ? B[(long long)k * sbk + (long long)n * sbn] : 0.f;
     }
-    __syncthreads();
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < kRA; ++r) {
+      const int e = threadIdx.x + r * kGemmThreads;
+      As[buf][a_kfast ? e % kBK : e / kBM][a_kfast ? e / kBK : e % kBM] = ra[r];
+    }
+#pragma unroll
+    for (int r = 0; r < kRB; ++r) {
+      const int e = threadIdx.x + r * kGemmThreads;
+      Bs[buf][b_nfast ? e / kBN : e % kBK][b_nfast ? e % kBN : e / kBK] = rb[r];
+    }
+  };
+  if (k_lo < k_hi) {
+    fetch(k_lo);
+    stash(0);
+  }
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = k_lo; k0 < k_hi; k0 += kBK) {
+    const bool more = k0 + kBK < k_hi;
+    if (more) fetch(k0 + kBK);
 #pragma unroll
     for (int kk = 0; kk < kBK; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
-      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
       const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -95,7 +122,9 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const float* __restr
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
+    if (more) stash(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
   float* Cz = C + (long long)blockIdx.z * M * ldc;
 #pragma unroll
