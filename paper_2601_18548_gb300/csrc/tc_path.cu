@@ -17,20 +17,20 @@
 // CTA that reloads the whole network for each tile).
 //
 // Two tiles in flight per CTA pair ("slots" 0 and 1).  Each H x H product of
-// the forward pass or the reverse sweep ("a step") is two MMA chains of N = 128
-// output columns ("halves" a and b), each D (TMEM, FP32) = A (shared, 16-bit,
-// 128 pairs x 256 per CTA) x B (shared, 16-bit weight rows, 64 per CTA).  The
-// tensor core alternates between the slots: while it computes a step of one
-// slot, the epilogue turns the other slot's last step into that slot's next
-// operand, so neither waits for the other as long as an epilogue step is
+// the forward pass or the reverse sweep ("a step") is one MMA chain of N = 256
+// output columns, D (TMEM, FP32) = A (shared, 16-bit, 128 pairs x 256 per CTA)
+// x B (shared, 16-bit weight rows, 128 per CTA), so a step reads its A operand
+// once.  The tensor core alternates between the slots: while it computes a step
+// of one slot, the epilogue turns the other slot's last step into that slot's
+// next operand, so neither waits for the other as long as an epilogue step is
 // shorter than a step of MMAs.  Each slot has one A buffer (its step's
 // epilogue writes the next operand into it once the step's MMAs have read it)
 // and one 256-column accumulator.  Weights stream through a ring of 16 KB
-// stages (K = 128 of one chain) loaded by TMA in the order the MMAs consume
-// them; both CTAs' loads of a stage complete on one barrier of the even CTA,
-// and the even CTA's commit releases the stage in both.  The reverse operands
-// are stored copies of W_l^T scaled by 1/2 (exact), so both directions are
-// K-major.
+// stages (one K = 64 slab: each CTA's 128 weight rows as two 64-row boxes)
+// loaded by TMA in the order the MMAs consume them; both CTAs' loads of a stage
+// complete on one barrier of the even CTA, and the even CTA's commit releases
+// the stage in both.  The reverse operands are stored copies of W_l^T scaled
+// by 1/2 (exact), so both directions are K-major.
 //
 // Epilogue arithmetic (packed FP16 pairs):
 //   u = z / 2 = acc / 2 + b / 2,  t = tanh(u),  s(z) = z sigma(z) = u (1 + t),
@@ -45,23 +45,25 @@
 // f = w_o . s(z_L) accumulates in FP32.
 //
 // TMEM columns (512, allocated for the CTA pair): slot s's accumulator is
-// [256 s, 256 s + 256), half a first; the input-Jacobian chain (N = 32) of a
-// slot writes the first 32 columns of its half b after the last reverse step
-// has been read.
+// [256 s, 256 s + 256), columns [0, 128) ("half a") first; the input-Jacobian
+// chain (N = 32) of a slot writes the first 32 columns of its half b after the
+// last reverse step has been read.
 //
-// Tile boundary: the tail of a slot's tile reads the Jacobian and writes the
-// next tile's first layer into the slot's A buffer before its output stage
-// (chain rule, reduction), so the slot's next chains can start early; slot 0
-// runs one item ahead of slot 1.
+// Tile boundary: the slot's next tile's inputs are fetched after its last
+// reverse step; the tail reads the Jacobian and writes the next tile's first
+// layer into the slot's A buffer before its output stage (chain rule,
+// reduction), so the slot's next chain can start early; slot 0 runs one item
+// ahead of slot 1.
 //
 // Warp roles (608 threads per CTA): warp 0 issues TMA loads, warp 1 allocates
 // TMEM and (even CTA) issues the pair's MMAs, warp 18 merges each tile's four
 // row-quad partial records into the tile's record, warps 2..17 are the
 // epilogue: thread = one pair row (TMEM lane) and 64 columns; the 8 warps of
 // columns [0, 128) and the 8 of [128, 256) each signal their half to the MMA
-// issuer with one arrival per warp (the next step's first K = 128 stage needs
-// only half a).  The input-Jacobian operand W_1q^T streams through the same
-// ring as the weights.
+// issuer with one arrival per warp; the next chain starts once both halves of
+// both CTAs have arrived (its first MMA overwrites the whole accumulator).
+// The input-Jacobian operand W_1q^T streams through the same ring as the
+// weights.
 //
 // Every cross-warp and cross-CTA handoff is an mbarrier and every wait on one
 // is bounded (about a second).  On expiry the kernel records an error in a
@@ -80,8 +82,8 @@ namespace {
 
 constexpr int kTile = 128;             // pairs per CTA tile; a CTA pair shares each MMA (M = 256)
 constexpr int kH = 256;                // hidden width handled by this kernel
-constexpr int kHalf = 128;             // output columns per MMA chain
-constexpr int kRowsCta = kHalf / 2;    // weight rows of a chain held by each CTA of the pair
+constexpr int kHalf = 128;             // accumulator columns per half (one CTA's share of a step's weight rows)
+constexpr int kRowsCta = kHalf / 2;    // weight rows per TMA box (two boxes per CTA and stage)
 constexpr int kSlots = 2;              // tiles in flight per CTA pair
 constexpr int kStages = 4;             // weight ring depth
 constexpr int kSlabBytes = kRowsCta * 128;  // 64 rows x 64 16-bit values (one K = 64 slab)
@@ -117,7 +119,7 @@ static_assert(kOffPt % 16 == 0 && kOffTinfo % 16 == 0 && kOffBar % 8 == 0, "alig
 // barrier indices
 constexpr int B_FULL0 = 0;              // + stage: both CTAs' slabs landed (used in the even CTA)
 constexpr int B_EMPTY0 = kStages;       // + stage: its MMAs completed (commit to both CTAs)
-constexpr int B_ACC0 = 2 * kStages;     // + slot: the slot's step complete, both chains (commit to both CTAs)
+constexpr int B_ACC0 = 2 * kStages;     // + slot: the slot's step complete (commit to both CTAs)
 constexpr int B_ACCJ0 = 2 * kStages + 2;  // + slot: input-Jacobian chain complete (commit to both CTAs)
 constexpr int B_FD0 = 2 * kStages + 4;  // + slot: f partials written (512 arrivals)
 constexpr int B_ED0 = 2 * kStages + 6;  // + 2 slot + half: epilogues of both CTAs done (even CTA, 16 warp arrivals)
